@@ -1,0 +1,260 @@
+"""Plain FP64 CPU oracle of the EIS-inversion grid search.  TEST INFRASTRUCTURE.
+
+What it computes (arXiv 2207.14507):
+
+* noise residual W(I) = I - F(I)                                   (Sec. 2.2)
+  with F a 3x3 local Wiener filter (the workloads replace the wavelet
+  denoiser of Sec. 2.2 by a 3x3 Wiener filter), weighted by the frame
+  intensity, R = I * W(I), the fingerprint-matching term of Eq. 2/3;
+* fingerprint term K0 = K - mean(K)                                 (Eq. 1, 3)
+* inverse similarity warp of R, bilinear, zero outside the frame    (Eq. 4, Sec. 3.2)
+* circular cross-correlation over all shifts, C(d) = sum_x X(x) K0(x + d)
+* PCE with an 11x11 cyclic exclusion around the signed peak         (Eq. 3)
+* exhaustive search over the (lambda, theta) grid, arg-max PCE      (Sec. 3.2, Eq. 8)
+
+Everything is float64 NumPy, written as the plain definition; the only library
+primitives are numpy's FFTs (for the correlation) and array arithmetic.
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this module.  It shares no code with the CUDA path, and the CUDA path
+never calls it.
+
+Parity pins (see tests/test_oracle_pins.py): brute-force direct correlation on
+32x32 and 30x40; closed-form warps (identity, 90-degree rotation, 2x zoom);
+PCE of a delta-plus-constant surface and of a brute-force masked surface;
+invariance of the PCE to global gain and to a common cyclic shift; Wiener
+residual against scipy's reference filter in the interior and against
+scipy.ndimage's replicate-padded moments; planted-transform recovery.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
+    "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
+    "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
+]
+
+# Eq. 3: the exclusion neighbourhood D around the correlation peak is 11 x 11, cyclic.
+EXCLUSION = 11
+
+
+# ----------------------------------------------------------------------------- residual (Sec. 2.2)
+
+def local_moments_3x3(I: np.ndarray):
+    """3x3 local mean and population variance, borders replicated."""
+    I = np.asarray(I, dtype=np.float64)
+    H, W = I.shape
+    P = np.pad(I, 1, mode="edge")
+    s1 = np.zeros((H, W))
+    s2 = np.zeros((H, W))
+    for dy in range(3):
+        for dx in range(3):
+            v = P[dy:dy + H, dx:dx + W]
+            s1 += v
+            s2 += v * v
+    mu = s1 / 9.0
+    var = s2 / 9.0 - mu * mu
+    return mu, var
+
+
+def wiener_residual(I: np.ndarray):
+    """W(I) = I - Wiener3x3(I) with the noise power nu^2 = mean of the local variances.
+
+    Wiener3x3(I) = mu + (I - mu) * max(var - nu^2, 0) / max(var, nu^2); where both
+    var and nu^2 are zero the window is constant, I == mu and W = 0.
+    Returns (W, nu^2).
+    """
+    I = np.asarray(I, dtype=np.float64)
+    mu, var = local_moments_3x3(I)
+    nu2 = float(var.mean())
+    den = np.maximum(var, nu2)
+    safe = np.where(den > 0, den, 1.0)
+    gain = np.where(den > 0, np.maximum(var - nu2, 0.0) / safe, 1.0)
+    wien = mu + (I - mu) * gain
+    return I - wien, nu2
+
+
+def prnu_residual(frame: np.ndarray, weight_by_intensity: bool = True, normalise: bool = False):
+    """Residual fed to the matcher: R = I * W(I) (default) or W(I).
+
+    With ``normalise`` R is multiplied by s = 1 / RMS(R) (s = 1 when R == 0).
+    Returns (R, s).
+    """
+    I = np.asarray(frame, dtype=np.float64)
+    Wr, _ = wiener_residual(I)
+    R = I * Wr if weight_by_intensity else Wr
+    s = 1.0
+    if normalise:
+        ms = float(np.mean(R * R))
+        s = 1.0 / np.sqrt(ms) if ms > 0 else 1.0
+        R = R * s
+    return R, s
+
+
+def fingerprint_term(K: np.ndarray) -> np.ndarray:
+    """K0 = K - mean(K): the mean-removed fingerprint of the NCC (Eq. 1)."""
+    K = np.asarray(K, dtype=np.float64)
+    return K - K.mean()
+
+
+# ----------------------------------------------------------------------------- candidates (Sec. 3.2)
+
+def _f32(x) -> float:
+    return float(np.float32(x))
+
+
+def grid_lambda(lam0: float, dlam: float, i: int) -> float:
+    """Scale node i: lam0 + i*dlam from float32 descriptor fields, evaluated in
+    float64 and rounded to float32 (the value both sides search)."""
+    return _f32(_f32(lam0) + i * _f32(dlam))
+
+
+def grid_theta(th0: float, dth: float, j: int) -> float:
+    return _f32(_f32(th0) + j * _f32(dth))
+
+
+def candidate_list(grid, window=None):
+    """(index, lambda, theta_deg) of every candidate, lambda-major, index = i*nth + j.
+
+    ``window`` = (lam_lo, lam_hi, th_lo, th_hi), inclusive; None = full grid.
+    """
+    lo_i, hi_i, lo_j, hi_j = (0, grid.nlam - 1, 0, grid.nth - 1) if window is None else window
+    out = []
+    for i in range(lo_i, hi_i + 1):
+        for j in range(lo_j, hi_j + 1):
+            out.append((i * grid.nth + j, grid_lambda(grid.lam0, grid.dlam, i),
+                        grid_theta(grid.th0_deg, grid.dth_deg, j)))
+    return out
+
+
+# ----------------------------------------------------------------------------- warp (Eq. 4)
+
+def warp_matrix(lam: float, theta_deg: float) -> np.ndarray:
+    """A = Rot(-theta) / lambda, so that q = c + A (p - c) maps a corrected pixel p
+    to the stabilised frame.  Eq. 4 restricted as in Sec. 3.2: t11 = t22 = scale,
+    t12 = -t21 = rotation, no projective terms; the translation is left to the
+    correlation peak.  Rot acts on (x = column, y = row)."""
+    th = np.deg2rad(theta_deg)
+    c, s = np.cos(th), np.sin(th)
+    return np.array([[c, s], [-s, c]]) / lam
+
+
+def inverse_warp(R: np.ndarray, lam: float, theta_deg: float) -> np.ndarray:
+    """X(p) = bilinear(R, q), q = c + A (p - c), c = ((W-1)/2, (H-1)/2).
+
+    Each of the four bilinear taps that falls outside the frame contributes 0.
+    """
+    R = np.asarray(R, dtype=np.float64)
+    H, W = R.shape
+    cy, cx = (H - 1) / 2.0, (W - 1) / 2.0
+    A = warp_matrix(lam, theta_deg)
+    yy, xx = np.meshgrid(np.arange(H) - cy, np.arange(W) - cx, indexing="ij")
+    qx = cx + A[0, 0] * xx + A[0, 1] * yy
+    qy = cy + A[1, 0] * xx + A[1, 1] * yy
+    x0 = np.floor(qx)
+    y0 = np.floor(qy)
+    fx = qx - x0
+    fy = qy - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    X = np.zeros((H, W))
+    for oy, wy in ((0, 1.0 - fy), (1, fy)):
+        for ox, wx in ((0, 1.0 - fx), (1, fx)):
+            yi = y0 + oy
+            xi = x0 + ox
+            ok = (yi >= 0) & (yi < H) & (xi >= 0) & (xi < W)
+            vals = np.zeros((H, W))
+            vals[ok] = R[yi[ok], xi[ok]]
+            X += wy * wx * vals
+    return X
+
+
+# ----------------------------------------------------------------------------- correlation and PCE (Eq. 1, 3)
+
+def xcorr(X: np.ndarray, K0: np.ndarray, K0_spectrum: np.ndarray | None = None) -> np.ndarray:
+    """Circular cross-correlation over all shifts, C(d) = sum_x X(x) K0((x + d) mod (H, W)).
+
+    The NCC normalisation of Eq. 1 is a constant over d and cancels in the PCE,
+    so it is left out here (see ``ncc_peak``).
+    """
+    H, W = X.shape
+    FK = np.fft.rfft2(K0) if K0_spectrum is None else K0_spectrum
+    return np.fft.irfft2(np.conj(np.fft.rfft2(X)) * FK, s=(H, W))
+
+
+def pce(C: np.ndarray, exclusion: int = EXCLUSION):
+    """Peak-to-correlation energy, Eq. 3.
+
+    The peak is the signed maximum of C (first in row-major order on ties); the
+    energy is the mean of C^2 over all shifts outside the cyclic
+    exclusion x exclusion window centred on the peak.  PCE = sgn(C*) C*^2 / E,
+    with E == 0 giving 0 for a zero peak and +-inf otherwise.
+    Returns dict(pce, dy, dx, peak, py, px) with the shift in [-H/2, H/2) x [-W/2, W/2).
+    """
+    C = np.asarray(C, dtype=np.float64)
+    H, W = C.shape
+    flat = int(np.argmax(C))
+    py, px = divmod(flat, W)
+    peak = float(C[py, px])
+    h = exclusion // 2
+    mask = np.ones((H, W), dtype=bool)
+    mask[np.ix_((py + np.arange(-h, h + 1)) % H, (px + np.arange(-h, h + 1)) % W)] = False
+    E = float(np.mean(C[mask] ** 2))
+    if E > 0:
+        val = float(np.sign(peak) * peak * peak / E)
+    else:
+        val = 0.0 if peak == 0 else float(np.sign(peak) * np.inf)
+    dy = py if py < H / 2 else py - H
+    dx = px if px < W / 2 else px - W
+    return dict(pce=val, dy=int(dy), dx=int(dx), peak=peak, py=int(py), px=int(px), energy=E)
+
+
+def ncc_peak(X: np.ndarray, K0: np.ndarray, peak: float) -> float:
+    """rho at the peak (Eq. 1): the correlation divided by ||X - mean X|| ||K0 - mean K0||."""
+    Xc = X - X.mean()
+    Kc = K0 - K0.mean()
+    den = np.linalg.norm(Xc) * np.linalg.norm(Kc)
+    return float(peak / den) if den > 0 else 0.0
+
+
+def score(R: np.ndarray, K0: np.ndarray, lam: float, theta_deg: float, K0_spectrum=None):
+    """PCE of one candidate: warp, correlate, Eq. 3."""
+    X = inverse_warp(R, lam, theta_deg)
+    return pce(xcorr(X, K0, K0_spectrum))
+
+
+# ----------------------------------------------------------------------------- search (Sec. 3.2)
+
+def grid_search(residuals, fingerprints, grid, windows=None, on_candidate=None):
+    """Exhaustive search of every frame against every fingerprint.
+
+    residuals: [F, H, W] (R from ``prnu_residual``); fingerprints: list of K0 (mean removed)
+    grid: object with lam0, dlam, nlam, th0_deg, dth_deg, nth
+    windows: None or int [F, 4] inclusive (lam_lo, lam_hi, th_lo, th_hi) per frame.
+    Returns (best, all_pce): best[f][p] = dict(pce, dy, dx, peak, lam, th_deg, cand);
+    all_pce: float64 [F, P, nlam*nth], NaN where a candidate was not evaluated.
+    Ties in PCE go to the lowest candidate index (lambda-major).
+    """
+    F = len(residuals)
+    P = len(fingerprints)
+    all_pce = np.full((F, P, grid.nlam * grid.nth), np.nan)
+    spectra = [np.fft.rfft2(K0) for K0 in fingerprints]
+    best = []
+    for f in range(F):
+        row = []
+        win = None if windows is None else tuple(int(v) for v in windows[f])
+        cands = candidate_list(grid, win)
+        for p in range(P):
+            b = None
+            for idx, lam, th in cands:
+                r = score(residuals[f], fingerprints[p], lam, th, spectra[p])
+                all_pce[f, p, idx] = r["pce"]
+                if on_candidate is not None:
+                    on_candidate(f, p, idx, r)
+                if b is None or r["pce"] > b["pce"]:
+                    b = dict(r, lam=lam, th_deg=th, cand=idx)
+            row.append(b)
+        best.append(row)
+    return best, all_pce

@@ -1,0 +1,332 @@
+"""Pins of the FP64 oracle to facts other than itself (closed forms, brute force,
+library routines, invariants).  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage, signal
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _direct_xcorr(X, K0):
+    """C(d) = sum_x X(x) K0(x + d) by explicit summation over every shift."""
+    H, W = X.shape
+    C = np.empty((H, W))
+    for dy in range(H):
+        for dx in range(W):
+            C[dy, dx] = np.sum(X * np.roll(K0, shift=(-dy, -dx), axis=(0, 1)))
+    return C
+
+
+# ------------------------------------------------------------------ correlation vs brute force
+
+@pytest.mark.parametrize("H,W", [(32, 32), (30, 40), (24, 20), (18, 50)])
+def test_xcorr_equals_direct_correlation(H, W):
+    rng = np.random.default_rng(H * 1000 + W)
+    X = rng.standard_normal((H, W))
+    K0 = rng.standard_normal((H, W))
+    C = oracle.xcorr(X, K0)
+    D = _direct_xcorr(X, K0)
+    assert np.max(np.abs(C - D)) <= 1e-12 * np.max(np.abs(D)) * np.sqrt(H * W)
+
+
+def test_xcorr_tiny_loops():
+    """Pure-Python quadruple loop on a 6x4 case (no numpy reductions)."""
+    rng = np.random.default_rng(7)
+    H, W = 6, 4
+    X = rng.standard_normal((H, W))
+    K0 = rng.standard_normal((H, W))
+    C = oracle.xcorr(X, K0)
+    for dy in range(H):
+        for dx in range(W):
+            s = 0.0
+            for y in range(H):
+                for x in range(W):
+                    s += X[y, x] * K0[(y + dy) % H, (x + dx) % W]
+            assert abs(C[dy, dx] - s) < 1e-12
+
+
+def test_shift_sign_convention():
+    """X(x) = K0(x + s) puts the peak at d = s (the planted stabilisation shift)."""
+    rng = np.random.default_rng(3)
+    K0 = rng.standard_normal((30, 40))
+    X = np.roll(K0, shift=(-7, 11), axis=(0, 1))   # X(x) = K0(x + (7, -11))
+    r = oracle.pce(oracle.xcorr(X, K0))
+    assert (r["dy"], r["dx"]) == (7, -11)
+
+
+# ------------------------------------------------------------------ warp closed forms (Eq. 4)
+
+def test_warp_identity_is_exact():
+    R = np.random.default_rng(0).standard_normal((37, 52))
+    assert np.array_equal(oracle.inverse_warp(R, 1.0, 0.0), R)
+
+
+@pytest.mark.parametrize("n", [17, 31])
+def test_warp_quarter_turn_is_rot90(n):
+    R = np.random.default_rng(n).standard_normal((n, n))
+    X = oracle.inverse_warp(R, 1.0, 90.0)
+    np.testing.assert_allclose(X, np.rot90(R, -1), atol=1e-12, rtol=0)
+    X = oracle.inverse_warp(R, 1.0, -90.0)
+    np.testing.assert_allclose(X, np.rot90(R, 1), atol=1e-12, rtol=0)
+
+
+def test_warp_zoom_half_pixel_averages():
+    """lambda = 2 on odd sizes samples at integers and half-integers around the centre."""
+    H, W = 21, 15
+    R = np.random.default_rng(1).standard_normal((H, W))
+    X = oracle.inverse_warp(R, 2.0, 0.0)
+    cy, cx = (H - 1) // 2, (W - 1) // 2
+    for y in range(H):
+        for x in range(W):
+            qy2, qx2 = 2 * cy + (y - cy), 2 * cx + (x - cx)   # 2*q, integer
+            ys = [qy2 // 2] if qy2 % 2 == 0 else [qy2 // 2, qy2 // 2 + 1]
+            xs = [qx2 // 2] if qx2 % 2 == 0 else [qx2 // 2, qx2 // 2 + 1]
+            expect = np.mean([R[a, b] for a in ys for b in xs])
+            assert abs(X[y, x] - expect) < 1e-13
+
+
+def test_warp_zoom_out_decimates_and_zero_fills():
+    """lambda = 1/2 samples R at c + 2(p - c): integer taps, zero outside the frame."""
+    H, W = 19, 23
+    R = np.random.default_rng(2).standard_normal((H, W)) + 3.0
+    X = oracle.inverse_warp(R, 0.5, 0.0)
+    cy, cx = (H - 1) // 2, (W - 1) // 2
+    for y in range(H):
+        for x in range(W):
+            qy, qx = cy + 2 * (y - cy), cx + 2 * (x - cx)
+            expect = R[qy, qx] if (0 <= qy < H and 0 <= qx < W) else 0.0
+            assert X[y, x] == expect
+
+
+@pytest.mark.parametrize("lam,th", [(1.07, 3.3), (0.93, -4.1), (1.0, 0.25), (1.1, 5.0)])
+def test_warp_reproduces_linear_ramp(lam, th):
+    """Bilinear interpolation is exact on affine fields, so inside the frame
+    X(p) = a*qx + b*qy + c0 with q = c + Rot(-theta)(p - c)/lambda, worked out by
+    hand per component: qx = cx + (cos t (x-cx) + sin t (y-cy))/lam and
+    qy = cy + (-sin t (x-cx) + cos t (y-cy))/lam."""
+    H, W = 40, 56
+    a, b, c0 = 0.37, -1.21, 5.0
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    R = a * xx + b * yy + c0
+    X = oracle.inverse_warp(R, lam, th)
+    cy, cx = (H - 1) / 2, (W - 1) / 2
+    t = np.radians(th)
+    qx = cx + (np.cos(t) * (xx - cx) + np.sin(t) * (yy - cy)) / lam
+    qy = cy + (-np.sin(t) * (xx - cx) + np.cos(t) * (yy - cy)) / lam
+    inside = (qx >= 0) & (qx <= W - 1) & (qy >= 0) & (qy <= H - 1)
+    # the far edge (q == W-1 exactly) is interior too; drop a 1-px band to avoid
+    # the zero tap next to it when q rounds just past the last column
+    inside &= (qx < W - 1 - 1e-9) & (qy < H - 1 - 1e-9)
+    assert inside.sum() > H * W // 2
+    np.testing.assert_allclose(X[inside], (a * qx + b * qy + c0)[inside], atol=1e-10)
+    outside = (qx < -1) | (qx > W) | (qy < -1) | (qy > H)
+    assert np.all(X[outside] == 0)
+
+
+# ------------------------------------------------------------------ PCE (Eq. 3)
+
+def test_pce_golden_closed_forms():
+    d = json.load(open(os.path.join(GOLDEN, "pce_closed_forms.json")))
+    for case in d["cases"]:
+        C = np.full((case["H"], case["W"]), case["b"], dtype=np.float64)
+        for y, x, v in case["points"]:
+            C[y, x] = v
+        r = oracle.pce(C)
+        e = case["expected"]
+        assert r["pce"] == pytest.approx(e["pce"], rel=1e-14), case["name"]
+        assert (r["dy"], r["dx"], r["peak"]) == (e["dy"], e["dx"], e["peak"]), case["name"]
+
+
+def test_pce_matches_explicit_cyclic_mask():
+    """Random surface: energy from a loop that tests cyclic distance explicitly."""
+    consts = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    half = consts["exclusion_window"]["value"] // 2
+    rng = np.random.default_rng(11)
+    for H, W in [(16, 16), (24, 30)]:
+        C = rng.standard_normal((H, W))
+        C[H - 2, 1] = 9.0                       # peak near a corner: window wraps both axes
+        r = oracle.pce(C)
+        py, px = H - 2, 1
+        tot, cnt = 0.0, 0
+        for y in range(H):
+            for x in range(W):
+                ddy = min((y - py) % H, (py - y) % H)
+                ddx = min((x - px) % W, (px - x) % W)
+                if ddy <= half and ddx <= half:
+                    continue
+                tot += C[y, x] ** 2
+                cnt += 1
+        assert cnt == H * W - consts["exclusion_count"]["value"]
+        assert r["pce"] == pytest.approx(81.0 / (tot / cnt), rel=1e-13)
+        assert (r["py"], r["px"]) == (py, px)
+
+
+def test_pce_ties_take_first_row_major():
+    C = np.zeros((16, 20))
+    C[9, 3] = 5.0
+    C[4, 17] = 5.0
+    C[4, 18] = 5.0
+    r = oracle.pce(C)
+    assert (r["py"], r["px"]) == (4, 17)
+
+
+def test_pce_zero_energy_rules():
+    assert oracle.pce(np.zeros((16, 16)))["pce"] == 0.0
+    C = np.zeros((16, 16))
+    C[2, 2] = 3.0
+    assert oracle.pce(C)["pce"] == np.inf
+
+
+# ------------------------------------------------------------------ invariances
+
+def _frame(seed, H=48, W=64):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(16, 240, size=(H, W))
+
+
+def test_pce_invariant_to_global_gain():
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((48, 64))
+    K0 = oracle.fingerprint_term(rng.standard_normal((48, 64)))
+    base = oracle.score(R, K0, 1.03, 1.7)
+    for g in (0.125, 3.0, 1e3):
+        r = oracle.score(R * g, K0 * (1.0 / g + 0.5), 1.03, 1.7)
+        assert r["pce"] == pytest.approx(base["pce"], rel=1e-12)
+        assert (r["dy"], r["dx"]) == (base["dy"], base["dx"])
+
+
+def test_residual_gain_homogeneity():
+    """Frame gain g (before quantisation): W(gI) = g W(I), R(gI) = g^2 R(I), PCE unchanged."""
+    I = _frame(6)
+    K0 = oracle.fingerprint_term(np.random.default_rng(8).standard_normal(I.shape))
+    R1, _ = oracle.prnu_residual(I)
+    R2, _ = oracle.prnu_residual(2.5 * I)
+    np.testing.assert_allclose(R2, 6.25 * R1, rtol=1e-10, atol=1e-10)
+    a = oracle.score(R1, K0, 0.97, -2.0)["pce"]
+    b = oracle.score(R2, K0, 0.97, -2.0)["pce"]
+    assert b == pytest.approx(a, rel=1e-12)
+
+
+def test_pce_invariant_to_common_cyclic_shift():
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((30, 40))
+    K0 = rng.standard_normal((30, 40))
+    X[4, 4] += 30
+    K0[6, 9] += 30
+    a = oracle.pce(oracle.xcorr(X, K0))
+    s = (13, -7)
+    b = oracle.pce(oracle.xcorr(np.roll(X, s, (0, 1)), np.roll(K0, s, (0, 1))))
+    assert b["pce"] == pytest.approx(a["pce"], rel=1e-12)
+    assert (a["dy"], a["dx"]) == (b["dy"], b["dx"])
+
+
+# ------------------------------------------------------------------ residual (Sec. 2.2)
+
+def test_local_moments_match_scipy_nearest():
+    I = _frame(10).round()
+    mu, var = oracle.local_moments_3x3(I)
+    m1 = ndimage.uniform_filter(I, size=3, mode="nearest")
+    m2 = ndimage.uniform_filter(I * I, size=3, mode="nearest")
+    np.testing.assert_allclose(mu, m1, rtol=1e-13)
+    np.testing.assert_allclose(var, m2 - m1 * m1, atol=1e-9)
+
+
+def test_wiener_interior_matches_scipy():
+    """scipy.signal.wiener with the same noise power equals the oracle's filter
+    away from the border (scipy zero-pads, the oracle replicates)."""
+    I = _frame(12).round()
+    Wr, nu2 = oracle.wiener_residual(I)
+    ref = signal.wiener(I, mysize=3, noise=nu2)
+    np.testing.assert_allclose((I - Wr)[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-12, atol=1e-9)
+
+
+def test_wiener_constant_and_flat_frames():
+    I = np.full((20, 30), 117.0)
+    Wr, nu2 = oracle.wiener_residual(I)
+    assert nu2 == 0.0 and np.all(Wr == 0)
+    R, s = oracle.prnu_residual(I, normalise=True)
+    assert s == 1.0 and np.all(R == 0)
+
+
+def test_residual_normalised_rms_is_one():
+    R, s = oracle.prnu_residual(_frame(13), normalise=True)
+    assert np.sqrt(np.mean(R * R)) == pytest.approx(1.0, rel=1e-12)
+    R0, _ = oracle.prnu_residual(_frame(13))
+    np.testing.assert_allclose(R, R0 * s, rtol=1e-14)
+
+
+# ------------------------------------------------------------------ end to end (Sec. 3.2)
+
+def test_candidate_nodes_and_order():
+    g = synth.GRID_C1
+    cl = oracle.candidate_list(g)
+    assert len(cl) == 121 and cl[0][0] == 0 and cl[-1][0] == 120
+    assert cl[5 * 11 + 5][1] == 1.0            # 0.96 + 5*0.008 rounds to exactly 1 in float32
+    assert cl[1][2] == pytest.approx(-0.8, abs=1e-6) and cl[11][1] == pytest.approx(0.968, abs=1e-6)
+    w = oracle.candidate_list(g, (2, 4, 7, 8))
+    assert [c[0] for c in w] == [29, 30, 40, 41, 51, 52]
+
+
+def test_identity_frames_peak_at_zero_shift():
+    """Unstabilised frames: the (1, ~0) candidate wins with its peak at zero shift."""
+    wl = synth.make_workload(1, F=2)
+    wl.planted[:] = (1.0, 0.0, 0.0, 0.0)
+    K = wl.fingerprints[0]
+    frames = synth.make_frames(K, wl.planted, config=1)
+    R = [oracle.prnu_residual(f)[0] for f in frames]
+    best, allp = oracle.grid_search(R, [oracle.fingerprint_term(K)], synth.GRID_C1,
+                                    windows=np.array([[3, 7, 3, 7]] * 2))
+    for f in range(2):
+        b = best[f][0]
+        assert b["cand"] == 5 * 11 + 5 and (b["dy"], b["dx"]) == (0, 0)
+        assert b["pce"] > 1000
+
+
+def test_planted_on_grid_recovery_256():
+    wl = synth.make_workload(1, on_grid=True)
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    R = [oracle.prnu_residual(f)[0] for f in wl.frames]
+    best, allp = oracle.grid_search(R, [K0], wl.grid)
+    for f in range(len(R)):
+        lam, th, sy, sx = wl.planted[f]
+        b = best[f][0]
+        assert b["lam"] == pytest.approx(lam, abs=0) and b["th_deg"] == pytest.approx(th, abs=0)
+        assert (b["dy"], b["dx"]) == (sy, sx)
+        assert b["pce"] > 1000
+    assert not np.isnan(allp).any()
+
+
+def test_planted_on_grid_recovery_1080p_window():
+    """Full-HD frame, 3x3 window around the planted node: the planted node wins."""
+    wl = synth.make_workload(2, F=1, on_grid=True)
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    R = [oracle.prnu_residual(wl.frames[0])[0]]
+    lam, th, sy, sx = wl.planted[0]
+    i = int(round((lam - np.float32(0.9)) / np.float32(0.005)))
+    j = int(round((th + 5.0) / 0.25))
+    win = np.array([[max(i - 1, 0), min(i + 1, 40), max(j - 1, 0), min(j + 1, 40)]])
+    best, _ = oracle.grid_search(R, [K0], wl.grid, windows=win)
+    b = best[0][0]
+    assert b["cand"] == i * 41 + j and (b["dy"], b["dx"]) == (sy, sx)
+
+
+def test_unmatched_fingerprint_scores_low():
+    wl = synth.make_workload(1, F=1, on_grid=True)
+    K_other = synth.fingerprint_field(256, 256, np.random.default_rng(99))
+    R = oracle.prnu_residual(wl.frames[0])[0]
+    lam, th = wl.planted[0, :2]
+    assert oracle.score(R, oracle.fingerprint_term(K_other), lam, th)["pce"] < 60
+
+
+def test_fingerprint_term_makes_correlation_blind_to_offsets():
+    """With K0 = K - mean(K), sum_x (X(x) + c) K0(x + d) = sum_x X(x) K0(x + d)."""
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((24, 30))
+    K0 = oracle.fingerprint_term(rng.standard_normal((24, 30)) + 0.7)
+    np.testing.assert_allclose(oracle.xcorr(X + 42.0, K0), oracle.xcorr(X, K0), atol=1e-9)
