@@ -1,0 +1,236 @@
+/*
+ * prnu.h -- C ABI of libprnu: GPU grid search that inverts electronic image
+ * stabilisation (EIS) before PRNU camera-fingerprint matching, after
+ * "GPU-accelerated SIFT-aided source identification of stabilized videos"
+ * (arXiv 2207.14507).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (PRNU_OK == 0).  Nothing throws
+ *    across the ABI.  On failure, prnu_last_error() gives a thread-local
+ *    message and no output is written.
+ *  - "d_" pointers are device pointers owned by the caller (for example
+ *    allocated by PyTorch); they must stay valid until the work enqueued on
+ *    the given stream has completed.  The library owns only its context, its
+ *    fingerprint-spectrum cache, its scratch workspace and its serving buffers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it in order.  Calls on one context are
+ *    serialised by the library (one workspace per context); work from a call on
+ *    another stream is ordered after the previous call's work by an event.
+ *  - Images are row-major, [rows H][columns W]; a frame batch is [F][H][W].
+ *  - Sizes accepted by the correlation path: H and W even, 16 <= H, W <= 4096,
+ *    and both 5-smooth (only prime factors 2, 3, 5).  Other sizes return
+ *    PRNU_EINVAL.
+ *  - Shifts are cyclic and reported signed: dy in [-H/2, H/2), dx in [-W/2, W/2).
+ */
+#ifndef PRNU_H
+#define PRNU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+    PRNU_OK = 0,
+    PRNU_EINVAL = 1,          /* bad argument (size, pointer, window outside the grid) */
+    PRNU_ENOMEM = 2,          /* allocation failed or the HBM budget would be exceeded */
+    PRNU_ECUDA = 3,           /* a CUDA runtime call failed */
+    PRNU_EAGAIN = 4,          /* not ready yet (query_poll with timeout 0), or queue full */
+    PRNU_ETIMEOUT = 5,        /* query_poll waited timeout_us and the query is not done */
+    PRNU_ENOTFOUND = 6,       /* unknown fingerprint handle or query id */
+    PRNU_EDEVICE_ABORT = 7    /* a bounded device-side wait gave up */
+};
+
+/* storage types of residuals and fingerprint spectra (arithmetic is always FP32) */
+enum { PRNU_F32 = 0, PRNU_F16 = 1, PRNU_BF16 = 2 };
+
+/* prnu_residual flags */
+enum {
+    PRNU_WEIGHT_BY_INTENSITY = 1, /* store R = I * W(I) (the K.I matching term) instead of W(I) */
+    PRNU_NORMALISE = 2            /* scale each frame's R by 1/RMS(R) (s = 1 for R == 0) */
+};
+
+typedef struct prnu_ctx prnu_ctx;
+typedef void* prnu_stream;          /* a cudaStream_t */
+
+/* Search grid: lambda_i = lam0 + i*dlam (0 <= i < nlam), theta_j = th0_deg + j*dth_deg
+ * degrees (0 <= j < nth).  Node values are evaluated in double from these float
+ * fields and rounded to float.  Candidate index = i*nth + j (lambda-major).
+ * Sec. 3.2 ("correction", Eq. 8): exhaustive search over Lambda x Theta. */
+typedef struct {
+    float lam0, dlam;
+    int nlam;
+    float th0_deg, dth_deg;
+    int nth;
+} prnu_grid;
+
+/* Inclusive index window of one frame: lam_lo..lam_hi x th_lo..th_hi. */
+typedef struct {
+    int lam_lo, lam_hi, th_lo, th_hi;
+} prnu_window;
+
+/* Best candidate of one (frame, fingerprint) pair. */
+typedef struct {
+    float lam, th_deg;      /* arg-max scale and rotation (degrees) */
+    int dy, dx;             /* arg-max cyclic shift, signed */
+    double pce;             /* Eq. 3 at the arg-max */
+    float peak;             /* correlation value at the peak, C* = sum_x X(x) K0(x + d*) */
+    int cand_idx;           /* i*nth + j, or -1 when the frame had no candidate */
+} prnu_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the library itself allocates (workspace, spectra cache, serving
+ * buffers); 0 means 90% of the free memory at creation.  *out receives the
+ * context.  Errors: PRNU_EINVAL (NULL out, bad device), PRNU_ECUDA. */
+int prnu_create(prnu_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Wait for outstanding work, stop the serving thread, free everything the
+ * context owns.  NULL is accepted. */
+int prnu_destroy(prnu_ctx* ctx);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* prnu_last_error(void);
+
+/* Number of CUDA kernels this context has launched so far. */
+uint64_t prnu_launch_count(const prnu_ctx* ctx);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Noise residual of F uint8 frames (Sec. 2.2: W(I) = I - F(I)), with F a 3x3
+ * local Wiener filter: local mean mu and population variance s2 over the 3x3
+ * neighbourhood (borders replicated), noise power nu2 = mean of s2 over the
+ * frame, Wiener(I) = mu + (I - mu) max(s2 - nu2, 0) / max(s2, nu2).
+ *  d_frames: device uint8, frame f row y at d_frames + (f*H + y)*pitch, pitch >= W.
+ *  flags:    PRNU_WEIGHT_BY_INTENSITY and/or PRNU_NORMALISE.
+ *  out_dtype: PRNU_F32 | PRNU_F16 | PRNU_BF16; d_out: [F][H][W] of that type.
+ *  d_scale:  [F] float, receives the per-frame scale s (1 without PRNU_NORMALISE);
+ *            may be NULL.
+ * H, W >= 1 (no FFT-size rule here).  F == 0 is a no-op.  Asynchronous. */
+int prnu_residual(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch,
+                  int flags, int out_dtype, void* d_out, float* d_scale, prnu_stream stream);
+
+/* Fingerprint term (Eq. 1-3): cache the 2-D spectrum of K0 = K - mean(K) on the
+ * device, in the library's packed half-spectrum layout, stored as FP32 or FP16
+ * (store_dtype PRNU_F32 | PRNU_F16; PRNU_BF16 is stored as FP16).  d_K: device
+ * float [H][W].  *out_handle receives a reference-counted handle; computing
+ * the same device buffer twice gives two handles.  The spectrum is complete
+ * when the work on `stream` is; later calls on any stream are ordered after it.
+ * Errors: PRNU_EINVAL (size rule), PRNU_ENOMEM (budget). */
+int prnu_fingerprint_term(prnu_ctx* ctx, const float* d_K, int H, int W, int store_dtype,
+                          uint64_t* out_handle, prnu_stream stream);
+
+/* Drop a handle's reference; the cached spectrum is freed with the last one.
+ * Errors: PRNU_ENOTFOUND. */
+int prnu_fingerprint_release(prnu_ctx* ctx, uint64_t handle);
+
+/* EIS inversion grid search (Sec. 3.2 "correction" over one grid level, Eq. 3
+ * scoring, Eq. 4 restricted to scale + rotation).  For every frame f, every
+ * fingerprint p and every candidate (lambda_i, theta_j) in the frame's window:
+ *   X(p) = bilinear(R_f, c + Rot(-theta)(p - c)/lambda), c = ((W-1)/2, (H-1)/2),
+ *          taps outside the frame count 0;
+ *   C(d) = sum_x X(x) K0_p((x + d) mod (H, W))  over all H*W cyclic shifts;
+ *   PCE  = sgn(C*) C*^2 / E, C* = max C (first in row-major order on ties),
+ *          E = mean of C^2 outside the cyclic 11x11 window around the peak
+ *          (E == 0: PCE = 0 for a zero peak, +-inf otherwise);
+ * then keeps, per (f, p), the candidate of largest PCE (ties: lowest index).
+ *  d_resid:  [F][H][W] residuals of type `dtype` (from prnu_residual).
+ *  d_scale:  [F] or NULL; when given, the reported peak is divided by d_scale[f].
+ *  fp_handles: host array [P] of handles of spectra of the same H x W.
+ *  grid:     host pointer.  windows: host array [F] or NULL (= full grid).
+ *  out:      [F*P] results, out[f*P + p]; host or device pointer.  With a host
+ *            pointer the call returns after the stream has finished; with a
+ *            device pointer it is asynchronous.
+ *  d_all_pce: device double [F*P*nlam*nth] or NULL; receives every evaluated
+ *            candidate's PCE at (f*P + p)*nlam*nth + cand_idx, NaN elsewhere.
+ * F == 0 or P == 0 is a no-op.  Errors: PRNU_EINVAL, PRNU_ENOTFOUND, PRNU_ENOMEM. */
+int eis_grid_search(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale,
+                    int F, int H, int W, const uint64_t* fp_handles, int P,
+                    const prnu_grid* grid, const prnu_window* windows,
+                    prnu_result* out, double* d_all_pce, prnu_stream stream);
+
+/* The same search through the plain per-candidate path: one candidate at a
+ * time, each step (warp, row FFT, column FFT, spectrum product, inverse column
+ * FFT, inverse row FFT, PCE) its own launch through full-size FP32
+ * intermediates in device memory.  Same arguments and results as
+ * eis_grid_search (dtype must be PRNU_F32); it exists as the speed baseline. */
+int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale,
+                          int F, int H, int W, const uint64_t* fp_handles, int P,
+                          const prnu_grid* grid, const prnu_window* windows,
+                          prnu_result* out, double* d_all_pce, prnu_stream stream);
+
+/* PCE of one aligned pair (Eq. 3, no warp): d_X device float [H][W] against the
+ * cached fingerprint `fp_handle`.  Host outputs; any of them may be NULL.
+ * Synchronous (waits for `stream`). */
+int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W,
+              double* pce, int* dy, int* dx, float* peak, prnu_stream stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* One forensic query: F frames tested against P fingerprints. */
+typedef struct {
+    const uint8_t* frames;          /* [F][H][W] uint8 (row pitch `pitch`), device or host memory;
+                                       must stay valid until query_poll returns PRNU_OK */
+    int F, H, W;
+    size_t pitch;                   /* bytes between rows (>= W); 0 means W */
+    const uint64_t* fp_handles;     /* [P] spectra handles of size H x W (copied at submit) */
+    int P;
+    prnu_grid grid;
+    const prnu_window* windows;     /* [F] or NULL = full grid (copied at submit) */
+    int dtype;                      /* residual storage type */
+    int flags;                      /* residual flags (PRNU_WEIGHT_BY_INTENSITY, PRNU_NORMALISE) */
+} prnu_query;
+
+/* Hand a query to the context's continuous-batching server.  The descriptor is
+ * copied; *qid receives its id.  The server admits queries in arrival order as
+ * their device memory fits the context's HBM budget, and interleaves the
+ * candidates of all admitted queries in shared launches.
+ * Errors: PRNU_EINVAL, PRNU_ENOTFOUND, PRNU_EAGAIN (queue full), PRNU_ENOMEM
+ * (the query alone exceeds the budget). */
+int query_submit(prnu_ctx* ctx, const prnu_query* q, uint64_t* qid);
+
+/* Wait up to timeout_us microseconds (0 = do not wait, < 0 = forever) for
+ * query `qid`.  PRNU_OK: out[F*P] (host) receives the results and the query is
+ * retired.  PRNU_EAGAIN (timeout 0) / PRNU_ETIMEOUT: not done yet.
+ * PRNU_ENOTFOUND: unknown or already retired id.  Errors inside the server are
+ * reported here (PRNU_ECUDA, PRNU_EDEVICE_ABORT). */
+int query_poll(prnu_ctx* ctx, uint64_t qid, prnu_result* out, int64_t timeout_us);
+
+/* Serving statistics since creation: completed queries, candidates scored,
+ * launches issued by the server, and the peak device bytes admitted. */
+typedef struct {
+    uint64_t queries_done, candidates_done, server_launches;
+    uint64_t admitted_bytes_peak, admitted_bytes_now;
+} prnu_server_stats;
+int prnu_server_stats_get(prnu_ctx* ctx, prnu_server_stats* out);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Launch configuration of the fused path for one frame size and storage type:
+ * columns per column-pass block, row pairs per row block, and candidates per
+ * wave (the number of per-candidate spectra kept in the workspace). */
+typedef struct {
+    int col_width;        /* 4, 8 or 16 */
+    int pairs_per_block;  /* 1, 2 or 4 */
+    int wave;             /* candidates in flight, >= 1 */
+} prnu_tuning;
+
+/* Read / override the configuration used for frames of H x W. */
+int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out);
+int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg);
+
+/* Time the candidate configurations on synthetic data of H x W and `dtype`,
+ * keep the fastest for that size and write it to *best (may be NULL).
+ * `budget_ms` bounds the total measuring time. */
+int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budget_ms, prnu_tuning* best,
+                  prnu_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRNU_H */

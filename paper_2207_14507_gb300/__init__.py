@@ -1,0 +1,264 @@
+"""Python binding of libprnu (ctypes).  Argument marshalling only: every step of
+the search runs in the library's CUDA kernels.  PyTorch supplies device memory
+and streams.
+
+The raw C functions are exposed under their C names on ``lib()``; ``Context``
+wraps the same calls with tensor arguments (same method names).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libprnu.so")
+
+PRNU_OK, PRNU_EINVAL, PRNU_ENOMEM, PRNU_ECUDA, PRNU_EAGAIN, PRNU_ETIMEOUT, PRNU_ENOTFOUND, PRNU_EDEVICE_ABORT = range(8)
+PRNU_F32, PRNU_F16, PRNU_BF16 = 0, 1, 2
+PRNU_WEIGHT_BY_INTENSITY, PRNU_NORMALISE = 1, 2
+STATUS_NAMES = {0: "PRNU_OK", 1: "PRNU_EINVAL", 2: "PRNU_ENOMEM", 3: "PRNU_ECUDA", 4: "PRNU_EAGAIN",
+                5: "PRNU_ETIMEOUT", 6: "PRNU_ENOTFOUND", 7: "PRNU_EDEVICE_ABORT"}
+
+
+class PrnuError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class prnu_grid(C.Structure):
+    _fields_ = [("lam0", C.c_float), ("dlam", C.c_float), ("nlam", C.c_int),
+                ("th0_deg", C.c_float), ("dth_deg", C.c_float), ("nth", C.c_int)]
+
+
+class prnu_window(C.Structure):
+    _fields_ = [("lam_lo", C.c_int), ("lam_hi", C.c_int), ("th_lo", C.c_int), ("th_hi", C.c_int)]
+
+
+class prnu_result(C.Structure):
+    _fields_ = [("lam", C.c_float), ("th_deg", C.c_float), ("dy", C.c_int), ("dx", C.c_int),
+                ("pce", C.c_double), ("peak", C.c_float), ("cand_idx", C.c_int)]
+
+
+class prnu_query(C.Structure):
+    _fields_ = [("frames", C.c_void_p), ("F", C.c_int), ("H", C.c_int), ("W", C.c_int), ("pitch", C.c_size_t),
+                ("fp_handles", C.POINTER(C.c_uint64)), ("P", C.c_int), ("grid", prnu_grid),
+                ("windows", C.POINTER(prnu_window)), ("dtype", C.c_int), ("flags", C.c_int)]
+
+
+class prnu_server_stats(C.Structure):
+    _fields_ = [("queries_done", C.c_uint64), ("candidates_done", C.c_uint64), ("server_launches", C.c_uint64),
+                ("admitted_bytes_peak", C.c_uint64), ("admitted_bytes_now", C.c_uint64)]
+
+
+class prnu_tuning(C.Structure):
+    _fields_ = [("col_width", C.c_int), ("pairs_per_block", C.c_int), ("wave", C.c_int)]
+
+
+RESULT_DTYPE = np.dtype([("lam", "<f4"), ("th_deg", "<f4"), ("dy", "<i4"), ("dx", "<i4"), ("pce", "<f8"),
+                         ("peak", "<f4"), ("cand_idx", "<i4")])
+assert RESULT_DTYPE.itemsize == C.sizeof(prnu_result) == 32
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "prnu_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t]),
+    "prnu_destroy": (C.c_int, [_P]),
+    "prnu_last_error": (C.c_char_p, []),
+    "prnu_launch_count": (C.c_uint64, [_P]),
+    "prnu_residual": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int, C.c_int, _P, _P, _P]),
+    "prnu_fingerprint_term": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), _P]),
+    "prnu_fingerprint_release": (C.c_int, [_P, C.c_uint64]),
+    "eis_grid_search": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int,
+                                  C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
+                                        C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "pce_score": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                            C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
+    "query_submit": (C.c_int, [_P, C.POINTER(prnu_query), C.POINTER(C.c_uint64)]),
+    "query_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
+    "prnu_server_stats_get": (C.c_int, [_P, C.POINTER(prnu_server_stats)]),
+    "prnu_get_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
+    "prnu_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
+    "prnu_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(prnu_tuning), _P]),
+}
+EXPORTED = tuple(_SIGNATURES)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libprnu.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libprnu.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)
+
+
+def _check(code: int, func: str):
+    if code != PRNU_OK:
+        raise PrnuError(code, func, lib().prnu_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def make_grid(g) -> prnu_grid:
+    return prnu_grid(g.lam0, g.dlam, g.nlam, g.th0_deg, g.dth_deg, g.nth)
+
+
+def make_windows(windows):
+    if windows is None:
+        return None
+    w = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 4)
+    arr = (prnu_window * len(w))()
+    for i, (a, b, c, d) in enumerate(w):
+        arr[i] = prnu_window(int(a), int(b), int(c), int(d))
+    return arr
+
+
+class Context:
+    """A libprnu context on one CUDA device (``prnu_create``)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        h = C.c_void_p()
+        _check(lib().prnu_create(C.byref(h), device, hbm_budget_bytes), "prnu_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            _check(lib().prnu_destroy(self.h), "prnu_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def prnu_launch_count(self) -> int:
+        return int(lib().prnu_launch_count(self.h))
+
+    # --------------------------------------------------------------- hot path
+    def prnu_residual(self, frames, out, scale=None, flags=PRNU_WEIGHT_BY_INTENSITY, pitch=0, stream=None):
+        """frames: uint8 CUDA tensor [F, H, W]; out: float32/float16/bfloat16 CUDA tensor [F, H, W]."""
+        import torch
+        F, H, W = frames.shape[-3:]
+        dt = {torch.float32: PRNU_F32, torch.float16: PRNU_F16, torch.bfloat16: PRNU_BF16}[out.dtype]
+        pitch = pitch or (frames.stride(-2) if frames.dim() >= 2 else W)
+        _check(lib().prnu_residual(self.h, _ptr(frames), F, H, W, pitch, flags, dt, _ptr(out), _ptr(scale),
+                                   _stream(stream)), "prnu_residual")
+        return out
+
+    def prnu_fingerprint_term(self, K, store_dtype=PRNU_F32, stream=None) -> int:
+        H, W = K.shape
+        h = C.c_uint64()
+        _check(lib().prnu_fingerprint_term(self.h, _ptr(K), H, W, store_dtype, C.byref(h), _stream(stream)),
+               "prnu_fingerprint_term")
+        return int(h.value)
+
+    def prnu_fingerprint_release(self, handle: int):
+        _check(lib().prnu_fingerprint_release(self.h, handle), "prnu_fingerprint_release")
+
+    def eis_grid_search(self, resid, fp_handles, grid, windows=None, scale=None, out=None, all_pce=None,
+                        stream=None, naive=False):
+        """resid: CUDA tensor [F, H, W] (float32/float16/bfloat16).  Returns a numpy
+        structured array [F, P] of results (RESULT_DTYPE) when ``out`` is None,
+        else fills the CUDA uint8/float tensor ``out`` (F*P*32 bytes)."""
+        import torch
+        F, H, W = resid.shape
+        dt = {torch.float32: PRNU_F32, torch.float16: PRNU_F16, torch.bfloat16: PRNU_BF16}[resid.dtype]
+        P = len(fp_handles)
+        hs = (C.c_uint64 * max(P, 1))(*fp_handles)
+        g = make_grid(grid)
+        w = make_windows(windows)
+        host = out is None
+        if host:
+            res = np.zeros((F, P), dtype=RESULT_DTYPE)
+            optr = C.c_void_p(res.ctypes.data)
+        else:
+            res = out
+            optr = _ptr(out)
+        fn = lib().eis_grid_search_naive if naive else lib().eis_grid_search
+        _check(fn(self.h, _ptr(resid), dt, _ptr(scale), F, H, W, hs, P, C.byref(g), w, optr, _ptr(all_pce),
+                  _stream(stream)), "eis_grid_search_naive" if naive else "eis_grid_search")
+        return res
+
+    def pce_score(self, X, handle: int, stream=None):
+        H, W = X.shape
+        pce, dy, dx, peak = C.c_double(), C.c_int(), C.c_int(), C.c_float()
+        _check(lib().pce_score(self.h, _ptr(X), handle, H, W, C.byref(pce), C.byref(dy), C.byref(dx),
+                               C.byref(peak), _stream(stream)), "pce_score")
+        return dict(pce=pce.value, dy=dy.value, dx=dx.value, peak=peak.value)
+
+    # --------------------------------------------------------------- serving
+    def query_submit(self, frames, fp_handles, grid, windows=None, dtype=PRNU_F16,
+                     flags=PRNU_WEIGHT_BY_INTENSITY | PRNU_NORMALISE) -> int:
+        """frames: uint8 tensor [F, H, W] on the device or in (pinned) host memory;
+        it must stay alive until query_poll returns the results."""
+        F, H, W = frames.shape
+        P = len(fp_handles)
+        hs = (C.c_uint64 * max(P, 1))(*fp_handles)
+        w = make_windows(windows)
+        q = prnu_query(C.c_void_p(frames.data_ptr()), F, H, W, frames.stride(1), hs, P, make_grid(grid),
+                       w, dtype, flags)
+        qid = C.c_uint64()
+        _check(lib().query_submit(self.h, C.byref(q), C.byref(qid)), "query_submit")
+        return int(qid.value)
+
+    def query_poll(self, qid: int, F: int, P: int, timeout_us: int = -1):
+        """Returns the [F, P] results, or None while the query is not done."""
+        res = np.zeros((F, P), dtype=RESULT_DTYPE)
+        code = lib().query_poll(self.h, qid, C.c_void_p(res.ctypes.data), timeout_us)
+        if code in (PRNU_EAGAIN, PRNU_ETIMEOUT):
+            return None
+        _check(code, "query_poll")
+        return res
+
+    def prnu_server_stats_get(self) -> dict:
+        s = prnu_server_stats()
+        _check(lib().prnu_server_stats_get(self.h, C.byref(s)), "prnu_server_stats_get")
+        return {k: int(getattr(s, k)) for k, _ in s._fields_}
+
+    # --------------------------------------------------------------- tuning
+    def prnu_get_tuning(self, H, W) -> dict:
+        t = prnu_tuning()
+        _check(lib().prnu_get_tuning(self.h, H, W, C.byref(t)), "prnu_get_tuning")
+        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave)
+
+    def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave):
+        t = prnu_tuning(col_width, pairs_per_block, wave)
+        _check(lib().prnu_set_tuning(self.h, H, W, C.byref(t)), "prnu_set_tuning")
+
+    def prnu_autotune(self, H, W, dtype=PRNU_F32, budget_ms=2000.0, stream=None) -> dict:
+        t = prnu_tuning()
+        _check(lib().prnu_autotune(self.h, H, W, dtype, budget_ms, C.byref(t), _stream(stream)), "prnu_autotune")
+        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave)

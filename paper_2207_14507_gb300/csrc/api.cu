@@ -1,0 +1,701 @@
+// api.cu -- C ABI of libprnu (see include/prnu.h): context, FFT plans and
+// twiddle table, fingerprint-spectrum cache, work lists and the search driver.
+#include <climits>
+#include <cmath>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+
+#include "internal.h"
+#include "server.h"
+
+namespace prnu {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class Fn>
+int guarded(Fn&& fn) {
+  try {
+    fn();
+    g_last_error.clear();
+    return PRNU_OK;
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return PRNU_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return PRNU_EINVAL;
+  }
+}
+
+const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+
+void plan_search(int n, int maxr, std::vector<int>& cur, std::vector<int>& best) {
+  if (n == 1) {
+    if (best.empty() || cur.size() < best.size() || (cur.size() == best.size() && cur.back() > best.back()))
+      best = cur;
+    return;
+  }
+  if (!best.empty() && cur.size() + 1 > best.size()) return;
+  for (int r : kRadices) {
+    if (r > maxr || n % r) continue;
+    cur.push_back(r);
+    plan_search(n / r, r, cur, best);
+    cur.pop_back();
+  }
+}
+
+int roundup32(int v) { return (v + 31) & ~31; }
+
+}  // namespace
+
+bool is_5smooth(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+FftPlan make_plan(int n, const std::vector<int>& tw_offsets) {
+  FftPlan p{};
+  PRNU_CHECK_ARG(n >= 2 && n <= kMaxFft && is_5smooth(n), "FFT length must be 5-smooth in [2, 4096]");
+  std::vector<int> cur, best;
+  plan_search(n, 16, cur, best);
+  PRNU_CHECK_ARG(!best.empty() && (int)best.size() <= kMaxStages, "no FFT plan");
+  p.n = n;
+  p.nstages = (int)best.size();
+  for (int i = 0; i < p.nstages; ++i) p.radix[i] = best[i];
+  p.min_radix = best.back();
+  p.tw_off = tw_offsets[n];
+  return p;
+}
+
+void row_launch_shape(const FftPlan& p, int* threads, int* maxb) {
+  // one thread per butterfly of the stage with the most butterflies, at most 256
+  const int nb = p.n / p.min_radix;
+  *threads = std::min(256, std::max(32, roundup32(nb)));
+  *maxb = 1;
+}
+
+void col_launch_shape(const FftPlan& p, int lg, int* threads, int* maxb) {
+  const int total = (p.n / p.min_radix) << lg;
+  *threads = std::min(512, std::max(32, roundup32(total)));
+  *maxb = 1;
+}
+
+void validate_shape(int H, int W) {
+  PRNU_CHECK_ARG(H >= 16 && W >= 16 && H <= kMaxFft && W <= kMaxFft, "H and W must lie in [16, 4096]");
+  PRNU_CHECK_ARG(H % 2 == 0 && W % 2 == 0, "H and W must be even");
+  PRNU_CHECK_ARG(is_5smooth(H) && is_5smooth(W), "H and W must be 5-smooth (factors 2, 3, 5 only)");
+}
+
+void* ctx_alloc(prnu_ctx* c, size_t bytes) {
+  if (bytes == 0) return nullptr;
+  if (c->used.load() + bytes > c->budget)
+    throw Error{PRNU_ENOMEM, "HBM budget exceeded (" + std::to_string(c->used.load() + bytes) + " > " +
+                                 std::to_string(c->budget) + " bytes)"};
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{PRNU_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+  }
+  c->used += bytes;
+  return p;
+}
+
+void ctx_free(prnu_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  c->used -= bytes;
+}
+
+void ensure_buf(prnu_ctx* c, DeviceBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return;
+  // the old buffer may still be in use by enqueued work
+  if (b.p) {
+    PRNU_CUDA_TRY(cudaEventSynchronize(c->last_done));
+    ctx_free(c, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = std::max(bytes, (size_t)4096);
+  b.p = ctx_alloc(c, want);
+  b.bytes = want;
+}
+
+Tuning tuning_for(prnu_ctx* c, int H, int W) {
+  auto it = c->tuning.find({H, W});
+  if (it != c->tuning.end()) return it->second;
+  Tuning t;
+  FftPlan pc = make_plan(H, c->tw_off);
+  t.col_log2 = 0;
+  for (int lg = 4; lg >= 0; --lg) {
+    const size_t sm = 2 * (size_t)H * (1u << lg) * sizeof(float2);
+    if (sm <= 112 * 1024) {
+      t.col_log2 = lg;
+      break;
+    }
+  }
+  t.ppb = 2;
+  const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
+  t.wave = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)1 << 30) / per_item));
+  return t;
+}
+
+// Host-side staging of small descriptor arrays through pinned memory.
+struct Stager {
+  prnu_ctx* c;
+  size_t off = 0;
+  std::vector<std::function<void(char*)>> writers;
+  struct Copy {
+    void* dst;
+    size_t off, bytes;
+  };
+  std::vector<Copy> copies;
+  explicit Stager(prnu_ctx* ctx) : c(ctx) {}
+  template <class T>
+  void add(void* dst, const T* src, size_t count) {
+    const size_t bytes = sizeof(T) * count;
+    if (!bytes) return;
+    const size_t o = off;
+    copies.push_back(Copy{dst, o, bytes});
+    writers.push_back([=](char* base) { memcpy(base + o, src, bytes); });
+    off = (off + bytes + 255) & ~(size_t)255;
+  }
+  void flush(cudaStream_t s) {
+    if (copies.empty()) return;
+    PRNU_CUDA_TRY(cudaEventSynchronize(c->stage_free));
+    if (c->h_pinned_bytes < off) {
+      if (c->h_pinned) cudaFreeHost(c->h_pinned);
+      c->h_pinned = nullptr;
+      c->h_pinned_bytes = 0;
+      size_t want = std::max(off, (size_t)1 << 20);
+      PRNU_CUDA_TRY(cudaHostAlloc((void**)&c->h_pinned, want, cudaHostAllocDefault));
+      c->h_pinned_bytes = want;
+    }
+    for (auto& w : writers) w(c->h_pinned);
+    for (auto& cp : copies)
+      PRNU_CUDA_TRY(cudaMemcpyAsync(cp.dst, c->h_pinned + cp.off, cp.bytes, cudaMemcpyHostToDevice, s));
+    PRNU_CUDA_TRY(cudaEventRecord(c->stage_free, s));
+  }
+};
+
+void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call) {
+  PRNU_CHECK_ARG(g.nlam >= 1 && g.nth >= 1, "grid must have nlam >= 1 and nth >= 1");
+  PRNU_CHECK_ARG((long long)g.nlam * g.nth <= (1 << 24), "grid too large");
+  call.items.clear();
+  call.group_start.assign((size_t)F * P + 1, 0);
+  call.cmax = g.nlam * g.nth;
+  std::vector<float> lam(g.nlam), th(g.nth);
+  for (int i = 0; i < g.nlam; ++i) lam[i] = (float)((double)g.lam0 + (double)i * (double)g.dlam);
+  for (int j = 0; j < g.nth; ++j) th[j] = (float)((double)g.th0_deg + (double)j * (double)g.dth_deg);
+  for (int f = 0; f < F; ++f) {
+    int il = 0, ih = g.nlam - 1, jl = 0, jh = g.nth - 1;
+    if (windows) {
+      const prnu_window& w = windows[f];
+      PRNU_CHECK_ARG(w.lam_lo >= 0 && w.lam_lo <= w.lam_hi && w.lam_hi < g.nlam && w.th_lo >= 0 &&
+                         w.th_lo <= w.th_hi && w.th_hi < g.nth,
+                     "window " + std::to_string(f) + " lies outside the grid");
+      il = w.lam_lo; ih = w.lam_hi; jl = w.th_lo; jh = w.th_hi;
+    }
+    for (int p = 0; p < P; ++p) {
+      call.group_start[(size_t)f * P + p] = (int)call.items.size();
+      for (int i = il; i <= ih; ++i) {
+        const double L = (double)lam[i];
+        PRNU_CHECK_ARG(L > 0 && std::isfinite(L), "grid scales must be positive");
+        for (int j = jl; j <= jh; ++j) {
+          const double t = (double)th[j] * 3.14159265358979323846 / 180.0;
+          const double cs = cos(t), sn = sin(t);
+          WorkItem it;
+          it.frame = f;
+          it.fp = p;
+          it.cand = i * g.nth + j;
+          it.group = f * P + p;
+          it.a11 = (float)(cs / L);
+          it.a12 = (float)(sn / L);
+          it.a21 = (float)(-sn / L);
+          it.a22 = (float)(cs / L);
+          it.lam = lam[i];
+          it.th_deg = th[j];
+          call.items.push_back(it);
+        }
+      }
+    }
+  }
+  call.group_start[(size_t)F * P] = (int)call.items.size();
+  PRNU_CHECK_ARG(call.items.size() < (size_t)INT_MAX, "too many candidates");
+}
+
+static std::vector<FpDesc> fp_descs(const SearchCall& call) {
+  std::vector<FpDesc> d;
+  for (auto& f : call.fps) d.push_back(FpDesc{f->d_spec, f->dtype, f->d_scal + 2});
+  return d;
+}
+
+void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, double* d_all, bool naive,
+                    cudaStream_t s) {
+  const int H = call.H, W = call.W, Wh = W / 2;
+  const int n = (int)call.items.size();
+  const int ngroups = (int)call.group_start.size() - 1;
+  const FftPlan prow = make_plan(W, c->tw_off), pcol = make_plan(H, c->tw_off);
+  Tuning tn = tuning_for(c, H, W);
+  int rowT, rowMB;
+  row_launch_shape(prow, &rowT, &rowMB);
+  const int wave = naive ? 1 : std::max(1, std::min(tn.wave, n));
+
+  PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->last_done, 0));
+  for (auto& f : call.fps) PRNU_CUDA_TRY(cudaStreamWaitEvent(s, f->ready, 0));
+  ensure_buf(c, c->ws_items, sizeof(WorkItem) * std::max(n, 1));
+  ensure_buf(c, c->ws_results, sizeof(CandResult) * std::max(n, 1));
+  ensure_buf(c, c->ws_groups, sizeof(int) * (ngroups + 1));
+  ensure_buf(c, c->ws_fpdesc, sizeof(FpDesc) * std::max<size_t>(1, call.fps.size()));
+  ensure_buf(c, c->ws_spec, (size_t)wave * H * Wh * sizeof(float2));
+  ensure_buf(c, c->ws_stats, (size_t)wave * H * sizeof(RowStat));
+  std::vector<FpDesc> fd = fp_descs(call);
+  Stager st(c);
+  st.add(c->ws_items.p, call.items.data(), call.items.size());
+  st.add(c->ws_groups.p, call.group_start.data(), call.group_start.size());
+  st.add(c->ws_fpdesc.p, fd.data(), fd.size());
+  st.flush(s);
+
+  PassArgs a{};
+  a.resid = call.resid;
+  a.rdtype = call.rdtype;
+  a.H = H;
+  a.W = W;
+  a.items = reinterpret_cast<const WorkItem*>(c->ws_items.p);
+  a.spec = reinterpret_cast<float2*>(c->ws_spec.p);
+  a.stats = reinterpret_cast<RowStat*>(c->ws_stats.p);
+  a.results = reinterpret_cast<CandResult*>(c->ws_results.p);
+  a.fps = reinterpret_cast<const FpDesc*>(c->ws_fpdesc.p);
+  a.scale = call.scale;
+  a.tw = c->d_tw;
+  a.prow = prow;
+  a.pcol = pcol;
+  a.pairs_per_block = naive ? 2 : tn.ppb;
+  a.col_log2 = tn.col_log2;
+  a.row_threads = rowT;
+
+  if (!naive) {
+    for (int i0 = 0; i0 < n; i0 += wave) {
+      a.item0 = i0;
+      a.nitems = std::min(wave, n - i0);
+      launch_row_forward(a, true, nullptr, nullptr, s, c->launches);
+      launch_col(a, 0, nullptr, nullptr, nullptr, s, c->launches);
+      launch_row_inverse(a, nullptr, s, c->launches);
+      launch_finalize(a, s, c->launches);
+    }
+  } else {
+    // plain per-candidate path through full-size intermediates
+    PRNU_CHECK_ARG(call.rdtype == kF32, "the per-candidate path takes FP32 residuals");
+    const int nblk = 256;
+    const size_t xbytes = (size_t)H * W * sizeof(float);
+    ensure_buf(c, c->ws_misc, 2 * xbytes + nblk * (sizeof(float) + sizeof(int) + sizeof(double)) + 1024);
+    char* base = reinterpret_cast<char*>(c->ws_misc.p);
+    float* X = reinterpret_cast<float*>(base);
+    float* C = reinterpret_cast<float*>(base + xbytes);
+    double* bsum = reinterpret_cast<double*>(base + 2 * xbytes);
+    float* bmax = reinterpret_cast<float*>(bsum + nblk);
+    int* barg = reinterpret_cast<int*>(bmax + nblk);
+    PassArgs b = a;
+    b.resid = X;
+    b.rdtype = kF32;
+    b.nitems = 1;
+    for (int k = 0; k < n; ++k) {
+      a.item0 = k;
+      a.nitems = 1;
+      b.item0 = k;
+      launch_naive_warp(a, X, s, c->launches);
+      launch_row_forward(b, false, nullptr, nullptr, s, c->launches);
+      launch_col(b, 3, nullptr, nullptr, nullptr, s, c->launches);
+      launch_col(b, 2, nullptr, nullptr, nullptr, s, c->launches);
+      launch_col(b, 4, nullptr, nullptr, nullptr, s, c->launches);
+      launch_row_inverse(b, C, s, c->launches);
+      launch_naive_pce(C, H, W, a.items + k, a.fps, a.scale, a.results + k, bmax, barg, bsum, nblk, s,
+                       c->launches);
+    }
+  }
+  launch_argmax(a.results, a.items, reinterpret_cast<const int*>(c->ws_groups.p), ngroups, d_out, call.scale, H, W,
+                s, c->launches);
+  if (d_all) {
+    PRNU_CUDA_TRY(cudaMemsetAsync(d_all, 0xff, sizeof(double) * (size_t)ngroups * call.cmax, s));
+    launch_scatter_all(a.results, n, call.cmax, d_all, s, c->launches);
+  }
+  PRNU_CUDA_TRY(cudaEventRecord(c->last_done, s));
+}
+
+static bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static std::shared_ptr<Fingerprint> find_fp(prnu_ctx* c, uint64_t h) {
+  auto it = c->fps.find(h);
+  if (it == c->fps.end()) throw Error{PRNU_ENOTFOUND, "unknown fingerprint handle " + std::to_string(h)};
+  return it->second;
+}
+
+static int search_common(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                         const uint64_t* fp_handles, int P, const prnu_grid* grid, const prnu_window* windows,
+                         prnu_result* out, double* d_all_pce, prnu_stream stream, bool naive) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 0 && P >= 0, "F and P must be >= 0");
+    if (F == 0 || P == 0) return;
+    PRNU_CHECK_ARG(d_resid && fp_handles && grid && out, "NULL argument");
+    PRNU_CHECK_ARG(dtype == kF32 || dtype == kF16 || dtype == kBF16, "unknown residual dtype");
+    validate_shape(H, W);
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SearchCall call;
+    call.resid = d_resid;
+    call.rdtype = dtype;
+    call.scale = d_scale;
+    call.F = F;
+    call.H = H;
+    call.W = W;
+    for (int p = 0; p < P; ++p) {
+      auto f = find_fp(ctx, fp_handles[p]);
+      PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs from the frames");
+      call.fps.push_back(f);
+    }
+    build_items(*grid, windows, F, P, call);
+    const bool dev_out = is_device_pointer(out);
+    prnu_result* d_out = out;
+    if (!dev_out) {
+      ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * (size_t)F * P);
+      d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
+    }
+    enqueue_search(ctx, call, d_out, d_all_pce, naive, s);
+    if (!dev_out) {
+      PRNU_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(prnu_result) * (size_t)F * P, cudaMemcpyDeviceToHost, s));
+      PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+}  // namespace prnu
+
+using namespace prnu;
+
+extern "C" {
+
+const char* prnu_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t prnu_launch_count(const prnu_ctx* ctx) { return ctx ? ctx->launches.n.load() : 0; }
+
+int prnu_create(prnu_ctx** out, int device, size_t hbm_budget_bytes) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(out, "NULL out");
+    int ndev = 0;
+    PRNU_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    PRNU_CHECK_ARG(device >= 0 && device < ndev, "no such CUDA device");
+    DeviceGuard dg(device);
+    PRNU_CUDA_TRY(cudaSetDevice(device));
+    std::unique_ptr<prnu_ctx> c(new prnu_ctx());
+    c->device = device;
+    PRNU_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    size_t fr = 0, tot = 0;
+    PRNU_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    // twiddles w_n^k = exp(-2 pi i k / n) for every 5-smooth n <= 4096
+    c->tw_off.assign(kMaxFft + 1, -1);
+    std::vector<float2> tw;
+    for (int n = 1; n <= kMaxFft; ++n) {
+      if (!is_5smooth(n)) continue;
+      c->tw_off[n] = (int)tw.size();
+      for (int k = 0; k < n; ++k) {
+        const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)n;
+        tw.push_back(make_float2((float)cos(a), (float)(-sin(a))));
+      }
+    }
+    const size_t twb = tw.size() * sizeof(float2);
+    c->d_tw = reinterpret_cast<float2*>(ctx_alloc(c.get(), twb));
+    c->tw_bytes = twb;
+    PRNU_CUDA_TRY(cudaMemcpy(c->d_tw, tw.data(), twb, cudaMemcpyHostToDevice));
+    PRNU_CUDA_TRY(cudaEventCreateWithFlags(&c->last_done, cudaEventDisableTiming));
+    PRNU_CUDA_TRY(cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
+    PRNU_CUDA_TRY(cudaEventRecord(c->last_done, 0));
+    PRNU_CUDA_TRY(cudaEventRecord(c->stage_free, 0));
+    set_kernel_attributes();
+    *out = c.release();
+  });
+}
+
+int prnu_destroy(prnu_ctx* ctx) {
+  if (!ctx) return PRNU_OK;
+  return guarded([&] {
+    DeviceGuard dg(ctx->device);
+    ctx->server.reset();
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->fps) {
+      auto& f = kv.second;
+      if (f->refs > 0 && f.use_count() == 1) {
+        ctx_free(ctx, f->d_spec, f->bytes);
+        ctx_free(ctx, f->d_scal, 3 * sizeof(float));
+        cudaEventDestroy(f->ready);
+      }
+    }
+    ctx->fps.clear();
+    for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
+                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid})
+      ctx_free(ctx, b->p, b->bytes);
+    ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    cudaEventDestroy(ctx->last_done);
+    cudaEventDestroy(ctx->stage_free);
+    delete ctx;
+  });
+}
+
+int prnu_residual(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags, int out_dtype,
+                  void* d_out, float* d_scale, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 0, "F must be >= 0");
+    if (F == 0) return;
+    PRNU_CHECK_ARG(d_frames && d_out, "NULL argument");
+    PRNU_CHECK_ARG(H >= 1 && W >= 1 && (long long)H * W <= (1LL << 26), "bad frame size");
+    if (pitch == 0) pitch = (size_t)W;
+    PRNU_CHECK_ARG(pitch >= (size_t)W, "pitch < W");
+    PRNU_CHECK_ARG(out_dtype == kF32 || out_dtype == kF16 || out_dtype == kBF16, "unknown output dtype");
+    PRNU_CHECK_ARG((flags & ~(PRNU_WEIGHT_BY_INTENSITY | PRNU_NORMALISE)) == 0, "unknown flags");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    const size_t np = residual_partials_needed(F, H, W);
+    const size_t need = sizeof(unsigned long long) * F + sizeof(double) * np + sizeof(float) * F + 512;
+    ensure_buf(ctx, ctx->ws_resid, need);
+    char* base = reinterpret_cast<char*>(ctx->ws_resid.p);
+    auto* acc = reinterpret_cast<unsigned long long*>(base);
+    auto* partials = reinterpret_cast<double*>(base + ((sizeof(unsigned long long) * F + 255) & ~(size_t)255));
+    float* scale = d_scale;
+    if (!scale && (flags & PRNU_NORMALISE))
+      scale = reinterpret_cast<float*>(reinterpret_cast<char*>(partials) + ((sizeof(double) * np + 255) & ~(size_t)255));
+    launch_residual(d_frames, F, H, W, pitch, flags, out_dtype, d_out, scale, acc, partials, (int)np, s,
+                    ctx->launches);
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+  });
+}
+
+int prnu_fingerprint_term(prnu_ctx* ctx, const float* d_K, int H, int W, int store_dtype, uint64_t* out_handle,
+                          prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && d_K && out_handle, "NULL argument");
+    validate_shape(H, W);
+    PRNU_CHECK_ARG(store_dtype == kF32 || store_dtype == kF16 || store_dtype == kBF16, "unknown storage dtype");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int Wh = W / 2;
+    const bool half = store_dtype != kF32;
+    auto f = std::make_shared<Fingerprint>();
+    f->H = H;
+    f->W = W;
+    f->dtype = half ? kF16 : kF32;
+    f->bytes = (size_t)H * Wh * (half ? sizeof(__half2) : sizeof(float2));
+    f->d_spec = ctx_alloc(ctx, f->bytes);
+    try {
+      f->d_scal = reinterpret_cast<float*>(ctx_alloc(ctx, 3 * sizeof(float)));
+    } catch (...) {
+      ctx_free(ctx, f->d_spec, f->bytes);
+      throw;
+    }
+    PRNU_CUDA_TRY(cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming));
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    const int nblk = 256;
+    ensure_buf(ctx, ctx->ws_misc, 2 * nblk * sizeof(double));
+    ensure_buf(ctx, ctx->ws_spec, (size_t)H * Wh * sizeof(float2));
+    const FftPlan prow = make_plan(W, ctx->tw_off), pcol = make_plan(H, ctx->tw_off);
+    int rowT, rowMB;
+    row_launch_shape(prow, &rowT, &rowMB);
+    Tuning tn = tuning_for(ctx, H, W);
+    launch_fp_stats(d_K, H, W, reinterpret_cast<double*>(ctx->ws_misc.p), nblk, f->d_scal, f->d_scal + 1,
+                    f->d_scal + 2, half, s, ctx->launches);
+    PassArgs a{};
+    a.resid = d_K;
+    a.rdtype = kF32;
+    a.H = H;
+    a.W = W;
+    a.item0 = 0;
+    a.nitems = 1;
+    a.spec = reinterpret_cast<float2*>(ctx->ws_spec.p);
+    a.tw = ctx->d_tw;
+    a.prow = prow;
+    a.pcol = pcol;
+    a.pairs_per_block = tn.ppb;
+    a.col_log2 = tn.col_log2;
+    a.row_threads = rowT;
+    launch_row_forward(a, false, f->d_scal, nullptr, s, ctx->launches);
+    launch_col(a, 1, half ? nullptr : reinterpret_cast<float2*>(f->d_spec), half ? f->d_spec : nullptr,
+               f->d_scal + 1, s, ctx->launches);
+    PRNU_CUDA_TRY(cudaEventRecord(f->ready, s));
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+    f->refs = 1;
+    const uint64_t h = ctx->next_handle++;
+    ctx->fps[h] = f;
+    *out_handle = h;
+  });
+}
+
+int prnu_fingerprint_release(prnu_ctx* ctx, uint64_t handle) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->fps.find(handle);
+    if (it == ctx->fps.end()) throw Error{PRNU_ENOTFOUND, "unknown fingerprint handle"};
+    auto f = it->second;
+    ctx->fps.erase(it);
+    // freed once no call or query holds it; pending work is ordered by last_done
+    if (f.use_count() == 1) {
+      PRNU_CUDA_TRY(cudaEventSynchronize(ctx->last_done));
+      ctx_free(ctx, f->d_spec, f->bytes);
+      ctx_free(ctx, f->d_scal, 3 * sizeof(float));
+      cudaEventDestroy(f->ready);
+      f->d_spec = nullptr;
+      f->d_scal = nullptr;
+    }
+  });
+}
+
+int eis_grid_search(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                    const uint64_t* fp_handles, int P, const prnu_grid* grid, const prnu_window* windows,
+                    prnu_result* out, double* d_all_pce, prnu_stream stream) {
+  return search_common(ctx, d_resid, dtype, d_scale, F, H, W, fp_handles, P, grid, windows, out, d_all_pce, stream,
+                       false);
+}
+
+int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                          const uint64_t* fp_handles, int P, const prnu_grid* grid, const prnu_window* windows,
+                          prnu_result* out, double* d_all_pce, prnu_stream stream) {
+  return search_common(ctx, d_resid, dtype, d_scale, F, H, W, fp_handles, P, grid, windows, out, d_all_pce, stream,
+                       true);
+}
+
+int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W, double* pce, int* dy, int* dx,
+              float* peak, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && d_X, "NULL argument");
+    validate_shape(H, W);
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto f = find_fp(ctx, fp_handle);
+    PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs");
+    const int Wh = W / 2;
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, f->ready, 0));
+    ensure_buf(ctx, ctx->ws_items, sizeof(WorkItem));
+    ensure_buf(ctx, ctx->ws_results, sizeof(CandResult));
+    ensure_buf(ctx, ctx->ws_fpdesc, sizeof(FpDesc));
+    ensure_buf(ctx, ctx->ws_spec, (size_t)H * Wh * sizeof(float2));
+    ensure_buf(ctx, ctx->ws_stats, (size_t)H * sizeof(RowStat));
+    WorkItem it{};
+    it.a11 = it.a22 = 1.f;
+    it.lam = 1.f;
+    FpDesc fd{f->d_spec, f->dtype, f->d_scal + 2};
+    Stager st(ctx);
+    st.add(ctx->ws_items.p, &it, 1);
+    st.add(ctx->ws_fpdesc.p, &fd, 1);
+    st.flush(s);
+    const FftPlan prow = make_plan(W, ctx->tw_off), pcol = make_plan(H, ctx->tw_off);
+    int rowT, rowMB;
+    row_launch_shape(prow, &rowT, &rowMB);
+    Tuning tn = tuning_for(ctx, H, W);
+    PassArgs a{};
+    a.resid = d_X;
+    a.rdtype = kF32;
+    a.H = H;
+    a.W = W;
+    a.items = reinterpret_cast<const WorkItem*>(ctx->ws_items.p);
+    a.item0 = 0;
+    a.nitems = 1;
+    a.spec = reinterpret_cast<float2*>(ctx->ws_spec.p);
+    a.stats = reinterpret_cast<RowStat*>(ctx->ws_stats.p);
+    a.results = reinterpret_cast<CandResult*>(ctx->ws_results.p);
+    a.fps = reinterpret_cast<const FpDesc*>(ctx->ws_fpdesc.p);
+    a.tw = ctx->d_tw;
+    a.prow = prow;
+    a.pcol = pcol;
+    a.pairs_per_block = tn.ppb;
+    a.col_log2 = tn.col_log2;
+    a.row_threads = rowT;
+    launch_row_forward(a, false, nullptr, nullptr, s, ctx->launches);
+    launch_col(a, 0, nullptr, nullptr, nullptr, s, ctx->launches);
+    launch_row_inverse(a, nullptr, s, ctx->launches);
+    launch_finalize(a, s, ctx->launches);
+    CandResult r{};
+    PRNU_CUDA_TRY(cudaMemcpyAsync(&r, a.results, sizeof(CandResult), cudaMemcpyDeviceToHost, s));
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+    PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+    if (pce) *pce = r.pce;
+    if (dy) *dy = r.py < H / 2 ? r.py : r.py - H;
+    if (dx) *dx = r.px < W / 2 ? r.px : r.px - W;
+    if (peak) *peak = r.peak;
+  });
+}
+
+int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && out, "NULL argument");
+    validate_shape(H, W);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Tuning t = tuning_for(ctx, H, W);
+    out->col_width = 1 << t.col_log2;
+    out->pairs_per_block = t.ppb;
+    out->wave = t.wave;
+  });
+}
+
+int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && cfg, "NULL argument");
+    validate_shape(H, W);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    int lg = -1;
+    for (int k = 0; k <= 4; ++k)
+      if (cfg->col_width == (1 << k)) lg = k;
+    PRNU_CHECK_ARG(lg >= 0, "col_width must be 1, 2, 4, 8 or 16");
+    PRNU_CHECK_ARG(cfg->pairs_per_block == 1 || cfg->pairs_per_block == 2 || cfg->pairs_per_block == 4,
+                   "pairs_per_block must be 1, 2 or 4");
+    PRNU_CHECK_ARG(cfg->wave >= 1, "wave must be >= 1");
+    FftPlan pc = make_plan(H, ctx->tw_off), pr = make_plan(W, ctx->tw_off);
+    int T, mb;
+    col_launch_shape(pc, lg, &T, &mb);
+    PRNU_CHECK_ARG(2 * (size_t)H * (1u << lg) * sizeof(float2) <= 227 * 1024, "column strip exceeds shared memory");
+    row_launch_shape(pr, &T, &mb);
+    PRNU_CHECK_ARG(T * cfg->pairs_per_block <= 512, "row block exceeds 512 threads");
+    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave};
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// common.cuh -- structures shared by the kernels and the host side of libprnu.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace prnu {
+
+enum StoreType { kF32 = 0, kF16 = 1, kBF16 = 2 };
+
+// One candidate of the search: which frame, which fingerprint, which grid
+// node, where its result goes, and the inverse-warp matrix
+// q = c + A (p - c), A = Rot(-theta)/lambda (Eq. 4 restricted to a similarity).
+struct WorkItem {
+  int frame;
+  int fp;        // index into the call's fingerprint table
+  int cand;      // grid index i*nth + j
+  int group;     // (frame, fingerprint) pair index, f*P + p
+  float a11, a12, a21, a22;
+  float lam, th_deg;
+};
+
+// Fingerprint spectrum as the kernels see it.
+struct FpDesc {
+  const void* spec;    // packed [H][W/2] complex, float2 or __half2
+  int dtype;                 // kF32 or kF16
+  const float* inv_scale;    // device scalar: multiply the correlation by it to undo the storage scale
+};
+
+// Per-row statistics of one candidate's correlation surface.
+struct RowStat {
+  float max;
+  int arg;             // column of the first maximum
+  double sumsq;        // sum of C^2 over the row
+};
+
+// Per-candidate score.
+struct CandResult {
+  double pce;
+  float peak;          // C* in the residual's stored units (FFT scale removed)
+  int py, px;          // cyclic peak position
+  int cand;
+  int group;
+  int pad;
+};
+
+// Host-built description of one launch of the fused path.
+struct PassArgs {
+  const void* resid;          // [F][H][W] of `rdtype`
+  int rdtype;
+  int H, W;
+  const WorkItem* items;      // all items of the call
+  int item0;                  // first item of this wave
+  int nitems;                 // items in this wave
+  float2* spec;               // workspace spectra [wave][H][W/2]
+  RowStat* stats;             // [wave][H]
+  CandResult* results;        // [all items]
+  const FpDesc* fps;          // [P]
+  const float* scale;         // [F] or nullptr
+  const float2* tw;           // twiddle table
+  FftPlan prow, pcol;
+  int pairs_per_block;
+  int col_log2;               // columns per column-pass block = 1 << col_log2
+  int row_threads;            // threads per row FFT
+};
+
+// ---------------------------------------------------------------- storage loads / stores
+
+template <int DT>
+__device__ __forceinline__ float load_store_type(const void* p, size_t i) {
+  if constexpr (DT == kF32) {
+    return __ldg(reinterpret_cast<const float*>(p) + i);
+  } else if constexpr (DT == kF16) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(p) + i));
+  } else {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p) + i));
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void store_store_type(void* p, size_t i, float v) {
+  if constexpr (DT == kF32) {
+    reinterpret_cast<float*>(p)[i] = v;
+  } else if constexpr (DT == kF16) {
+    reinterpret_cast<__half*>(p)[i] = __float2half_rn(v);
+  } else {
+    reinterpret_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
+  }
+}
+
+__device__ __forceinline__ float2 load_spec(const void* p, int dtype, size_t i) {
+  if (dtype == kF32) return __ldg(reinterpret_cast<const float2*>(p) + i);
+  __half2 h = reinterpret_cast<const __half2*>(p)[i];
+  return __half22float2(h);
+}
+
+}  // namespace prnu

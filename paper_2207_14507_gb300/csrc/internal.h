@@ -1,0 +1,159 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/prnu.h"
+#include "common.cuh"
+
+namespace prnu {
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+  int code;
+  std::string msg;
+};
+void set_error(const std::string& msg);
+#define PRNU_CUDA_TRY(expr)                                                               \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) throw ::prnu::Error{PRNU_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define PRNU_CHECK_ARG(cond, what)                                                        \
+  do {                                                                                    \
+    if (!(cond)) throw ::prnu::Error{PRNU_EINVAL, what};                                  \
+  } while (0)
+
+// ---------------------------------------------------------------- plans
+
+FftPlan make_plan(int n, const std::vector<int>& tw_offsets);
+bool is_5smooth(int n);
+// threads per row FFT and registers-per-thread class (1, 2 or 4 butterflies)
+void row_launch_shape(const FftPlan& p, int* threads, int* maxb);
+// threads per column block and butterflies per thread for 1 << lg columns
+void col_launch_shape(const FftPlan& p, int lg, int* threads, int* maxb);
+
+// ---------------------------------------------------------------- launchers (search.cu)
+
+// counts every kernel launch
+struct LaunchCounter {
+  std::atomic<uint64_t> n{0};
+};
+
+void launch_row_forward(const PassArgs& a, bool warp, const float* mean_sub, float2* out, cudaStream_t s,
+                        LaunchCounter& lc);
+// mode 0: forward FFT, multiply by the fingerprint, inverse FFT (in place)
+// mode 1: forward FFT only, written to out_f32 / out_f16 scaled by *scale
+// mode 2: multiply only by the fingerprint (packed spectra, in place)  [naive path]
+// mode 3: forward only, in place (float2)                               [naive path]
+// mode 4: inverse only, in place (float2)                               [naive path]
+void launch_col(const PassArgs& a, int mode, float2* out_f32, void* out_f16, const float* scale,
+                cudaStream_t s, LaunchCounter& lc);
+void launch_row_inverse(const PassArgs& a, float* c_out, cudaStream_t s, LaunchCounter& lc);
+void launch_finalize(const PassArgs& a, cudaStream_t s, LaunchCounter& lc);
+void launch_argmax(const CandResult* res, const WorkItem* items, const int* group_start, int ngroups,
+                   prnu_result* out, const float* scale, int H, int W, cudaStream_t s, LaunchCounter& lc);
+void launch_scatter_all(const CandResult* res, int nitems, int cmax, double* all, cudaStream_t s,
+                        LaunchCounter& lc);
+// fingerprint statistics: mean of K and the FP16 storage scale
+void launch_fp_stats(const float* K, int H, int W, double* partials, int nblk, float* mean_out,
+                     float* scale_out, float* inv_scale_out, bool half, cudaStream_t s, LaunchCounter& lc);
+// naive path
+void launch_naive_warp(const PassArgs& a, float* X, cudaStream_t s, LaunchCounter& lc);
+void launch_naive_pce(const float* C, int H, int W, const WorkItem* item, const FpDesc* fps, const float* scale,
+                      CandResult* out, float* blk_max, int* blk_arg, double* blk_sum, int nblk,
+                      cudaStream_t s, LaunchCounter& lc);
+void set_kernel_attributes();
+
+// ---------------------------------------------------------------- launchers (residual.cu)
+
+void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, int flags, int dtype, void* out,
+                     float* scale, unsigned long long* acc, double* partials, int max_partials, cudaStream_t s,
+                     LaunchCounter& lc);
+size_t residual_partials_needed(int F, int H, int W);
+
+// ---------------------------------------------------------------- context
+
+struct Fingerprint {
+  int H = 0, W = 0;
+  int dtype = kF32;
+  void* d_spec = nullptr;
+  float* d_scal = nullptr;   // [mean, scale, inv_scale]
+  size_t bytes = 0;
+  int refs = 0;
+  cudaEvent_t ready = nullptr;
+};
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+class Server;
+
+struct Tuning {
+  int col_log2 = 3;
+  int ppb = 2;
+  int wave = 64;
+};
+
+}  // namespace prnu
+
+struct prnu_ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};
+  std::recursive_mutex mu;
+  std::map<uint64_t, std::shared_ptr<prnu::Fingerprint>> fps;
+  uint64_t next_handle = 1;
+  float2* d_tw = nullptr;
+  std::vector<int> tw_off;   // offset per length, -1 if not 5-smooth
+  prnu::LaunchCounter launches;
+  cudaEvent_t last_done = nullptr;
+  // call workspace
+  prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid;
+  size_t tw_bytes = 0;
+  std::vector<char> h_stage;      // staging for host->device descriptors
+  char* h_pinned = nullptr;
+  size_t h_pinned_bytes = 0;
+  cudaEvent_t stage_free = nullptr;
+  std::map<std::pair<int, int>, prnu::Tuning> tuning;
+  std::unique_ptr<prnu::Server> server;
+};
+
+namespace prnu {
+// allocation helpers that honour the context budget
+void* ctx_alloc(prnu_ctx* c, size_t bytes);
+void ctx_free(prnu_ctx* c, void* p, size_t bytes);
+void ensure_buf(prnu_ctx* c, DeviceBuf& b, size_t bytes);
+Tuning tuning_for(prnu_ctx* c, int H, int W);
+
+// The search engine: enqueue the fused path for a prepared item list.
+struct SearchCall {
+  const void* resid;
+  int rdtype;
+  const float* scale;
+  int F, H, W;
+  std::vector<std::shared_ptr<Fingerprint>> fps;
+  std::vector<WorkItem> items;
+  std::vector<int> group_start;   // [F*P + 1]
+  int cmax;
+};
+void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call);
+void validate_shape(int H, int W);
+// enqueue: results into d_out (device prnu_result [F*P]); optional d_all
+void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, double* d_all, bool naive,
+                    cudaStream_t s);
+
+}  // namespace prnu

@@ -1,0 +1,295 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP32 path PCE relative error <= 1e-3; FP16 storage <= 1e-2; BF16
+storage reported and held to 3e-2; arg-max candidate and shift identical to
+the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-3
+FP16_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def prnu():
+    import paper_2207_14507_gb300 as p
+    p.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(prnu):
+    c = prnu.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    return t if dtype is None else t.to(dtype)
+
+
+# ------------------------------------------------------------------ residual (a1)
+
+@pytest.mark.parametrize("H,W", [(64, 48), (256, 256), (37, 53), (3, 5), (1080, 1920)])
+@pytest.mark.parametrize("weight", [True, False])
+def test_residual_matches_oracle(ctx, prnu, H, W, weight):
+    rng = np.random.default_rng(H * W)
+    frames = rng.integers(0, 256, size=(2, H, W)).astype(np.uint8)
+    frames[1, : H // 2] = 77  # a flat region: local variance 0
+    out = torch.empty((2, H, W), dtype=torch.float32, device=DEV)
+    flags = prnu.PRNU_WEIGHT_BY_INTENSITY if weight else 0
+    ctx.prnu_residual(_t(frames), out, flags=flags)
+    got = out.cpu().numpy()
+    for f in range(2):
+        ref, _ = oracle.prnu_residual(frames[f], weight_by_intensity=weight)
+        scale = np.abs(ref).max() + 1e-30
+        assert np.max(np.abs(got[f] - ref)) <= 2e-6 * scale
+
+
+def test_residual_normalise_and_pitch(ctx, prnu):
+    rng = np.random.default_rng(4)
+    H, W, pitch = 40, 50, 64
+    buf = rng.integers(0, 256, size=(3, H, pitch)).astype(np.uint8)
+    frames = _t(buf)[:, :, :W]          # strided view: pitch 64 bytes per row
+    out = torch.empty((3, H, W), dtype=torch.float32, device=DEV)
+    scale = torch.empty(3, dtype=torch.float32, device=DEV)
+    ctx.prnu_residual(frames, out, scale=scale, flags=prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE,
+                      pitch=pitch)
+    for f in range(3):
+        ref, s = oracle.prnu_residual(buf[f, :, :W], normalise=True)
+        assert scale[f].item() == pytest.approx(s, rel=1e-5)
+        np.testing.assert_allclose(out[f].cpu().numpy(), ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+def test_residual_half_storage(ctx, prnu):
+    frames = np.random.default_rng(5).integers(0, 256, size=(1, 64, 96)).astype(np.uint8)
+    ref, s = oracle.prnu_residual(frames[0], normalise=True)
+    for dt, tol in ((torch.float16, 2 ** -10), (torch.bfloat16, 2 ** -7)):
+        out = torch.empty((1, 64, 96), dtype=dt, device=DEV)
+        ctx.prnu_residual(_t(frames), out, flags=prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE)
+        got = out.float().cpu().numpy()[0]
+        assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3)) <= tol
+
+
+# ------------------------------------------------------------------ pce_score (a2, a4-a6)
+
+@pytest.mark.parametrize("H,W", [(16, 16), (30, 40), (64, 48), (18, 50), (96, 160), (256, 256), (120, 250),
+                                 (720, 1280)])
+def test_pce_score_matches_oracle(ctx, prnu, H, W):
+    rng = np.random.default_rng(H + 7 * W)
+    K = rng.standard_normal((H, W)).astype(np.float32) * 0.02
+    X = rng.standard_normal((H, W)).astype(np.float32)
+    s = (int(rng.integers(-H // 2, H // 2)), int(rng.integers(-W // 2, W // 2)))
+    X += 40.0 * np.roll(K, shift=(-s[0], -s[1]), axis=(0, 1))        # X(x) ~ K(x + s)
+    h = ctx.prnu_fingerprint_term(_t(K))
+    got = ctx.pce_score(_t(X), h)
+    ref = oracle.pce(oracle.xcorr(X.astype(np.float64), oracle.fingerprint_term(K)))
+    ctx.prnu_fingerprint_release(h)
+    assert (got["dy"], got["dx"]) == (ref["dy"], ref["dx"]) == s
+    assert got["pce"] == pytest.approx(ref["pce"], rel=FP32_TOL)
+    assert got["peak"] == pytest.approx(ref["peak"], rel=1e-4)
+
+
+def test_pce_score_peak_in_corner_and_negative_surface(ctx, prnu):
+    H, W = 64, 80
+    rng = np.random.default_rng(12)
+    K = rng.standard_normal((H, W)).astype(np.float32)
+    for s, sign in (((0, 0), 1.0), ((-32, -40), 1.0), ((31, 39), 1.0), ((3, -5), -1.0)):
+        X = (sign * 5.0 * np.roll(K, shift=(-s[0], -s[1]), axis=(0, 1)) + rng.standard_normal((H, W))).astype(np.float32)
+        h = ctx.prnu_fingerprint_term(_t(K))
+        got = ctx.pce_score(_t(X), h)
+        ref = oracle.pce(oracle.xcorr(X.astype(np.float64), oracle.fingerprint_term(K)))
+        ctx.prnu_fingerprint_release(h)
+        assert (got["dy"], got["dx"]) == (ref["dy"], ref["dx"])
+        assert got["pce"] == pytest.approx(ref["pce"], rel=FP32_TOL)
+
+
+def test_pce_zero_frame(ctx, prnu):
+    K = np.random.default_rng(1).standard_normal((32, 32)).astype(np.float32)
+    h = ctx.prnu_fingerprint_term(_t(K))
+    got = ctx.pce_score(torch.zeros((32, 32), device=DEV), h)
+    ctx.prnu_fingerprint_release(h)
+    assert got["pce"] == 0.0 and (got["dy"], got["dx"]) == (0, 0)
+
+
+# ------------------------------------------------------------------ grid search (a3-a8)
+
+def _oracle_search(wl, windows=None, fps=None):
+    R = [oracle.prnu_residual(f)[0] for f in wl.frames]
+    K0s = [oracle.fingerprint_term(K) for K in (fps or wl.fingerprints)]
+    return oracle.grid_search(R, K0s, wl.grid, windows=windows)
+
+
+def _gpu_search(ctx, prnu, wl, windows=None, dtype=torch.float32, fp_dtype=None, naive=False, fps=None,
+                normalise=False):
+    frames = _t(wl.frames)
+    R = torch.empty(frames.shape, dtype=dtype, device=DEV)
+    scale = torch.empty(frames.shape[0], dtype=torch.float32, device=DEV)
+    flags = prnu.PRNU_WEIGHT_BY_INTENSITY | (prnu.PRNU_NORMALISE if normalise else 0)
+    ctx.prnu_residual(frames, R, scale=scale, flags=flags)
+    fpd = fp_dtype if fp_dtype is not None else (prnu.PRNU_F32 if dtype == torch.float32 else prnu.PRNU_F16)
+    hs = [ctx.prnu_fingerprint_term(_t(K), fpd) for K in (fps or wl.fingerprints)]
+    all_pce = torch.empty((len(wl.frames), len(hs), wl.grid.size), dtype=torch.float64, device=DEV)
+    res = ctx.eis_grid_search(R, hs, wl.grid, windows=windows, scale=scale, all_pce=all_pce, naive=naive)
+    torch.cuda.synchronize()
+    for h in hs:
+        ctx.prnu_fingerprint_release(h)
+    return res, all_pce.cpu().numpy()
+
+
+def _assert_all_close(got, ref, tol):
+    mask = ~np.isnan(ref)
+    assert np.array_equal(mask, ~np.isnan(got))
+    rel = np.abs(got[mask] - ref[mask]) / np.maximum(np.abs(ref[mask]), 1e-12)
+    assert rel.max() <= tol, f"max PCE rel err {rel.max():.3g}"
+    return rel.max()
+
+
+def _assert_best_equal(res, best):
+    for f in range(res.shape[0]):
+        for p in range(res.shape[1]):
+            r, b = res[f, p], best[f][p]
+            assert r["cand_idx"] == b["cand"], (f, p, r, b)
+            assert (r["dy"], r["dx"]) == (b["dy"], b["dx"])
+            assert r["lam"] == np.float32(b["lam"]) and r["th_deg"] == np.float32(b["th_deg"])
+            assert r["pce"] == pytest.approx(b["pce"], rel=FP32_TOL)
+
+
+def test_config1_full_grid_every_candidate(ctx, prnu):
+    """256x256, 4 frames, 11x11 grid: all 484 PCEs vs the oracle, and the arg-max."""
+    wl = synth.make_workload(1)
+    res, got = _gpu_search(ctx, prnu, wl)
+    best, ref = _oracle_search(wl)
+    _assert_all_close(got, ref, FP32_TOL)
+    _assert_best_equal(res, best)
+    # peak values are in the residual's units
+    for f in range(4):
+        assert res[f, 0]["peak"] == pytest.approx(best[f][0]["peak"], rel=1e-3)
+
+
+def test_config1_on_grid_planted_recovery(ctx, prnu):
+    wl = synth.make_workload(1, on_grid=True)
+    res, _ = _gpu_search(ctx, prnu, wl)
+    for f in range(4):
+        lam, th, sy, sx = wl.planted[f]
+        r = res[f, 0]
+        assert r["lam"] == np.float32(lam) and r["th_deg"] == np.float32(th)
+        assert (r["dy"], r["dx"]) == (sy, sx)
+
+
+def test_windows_two_fingerprints_ragged(ctx, prnu):
+    """Uneven windows, two fingerprints (one matching), non-square frames."""
+    g = synth.Grid(0.95, 0.01, 11, -2.0, 0.5, 9)
+    wl = synth.make_workload(1, H=160, W=200, F=3, grid=g, on_grid=True)
+    other = synth.fingerprint_field(160, 200, np.random.default_rng(3))
+    fps = [wl.fingerprints[0], other]
+    windows = np.array([[0, 10, 0, 8], [2, 4, 3, 3], [9, 10, 0, 1]], np.int32)
+    res, got = _gpu_search(ctx, prnu, wl, windows=windows, fps=fps)
+    best, ref = _oracle_search(wl, windows=windows, fps=fps)
+    _assert_all_close(got, ref, FP32_TOL)
+    _assert_best_equal(res, best)
+
+
+def test_naive_path_matches_fused_and_oracle(ctx, prnu):
+    wl = synth.make_workload(1, F=2)
+    windows = np.array([[2, 6, 1, 5], [4, 8, 3, 9]], np.int32)
+    res_n, got_n = _gpu_search(ctx, prnu, wl, windows=windows, naive=True)
+    res_f, got_f = _gpu_search(ctx, prnu, wl, windows=windows)
+    best, ref = _oracle_search(wl, windows=windows)
+    _assert_all_close(got_n, ref, FP32_TOL)
+    _assert_best_equal(res_n, best)
+    _assert_all_close(got_f, got_n, 1e-5)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float16, FP16_TOL), (torch.bfloat16, 3e-2)])
+def test_half_storage_precision(ctx, prnu, dtype, tol):
+    """FP16 / BF16 residuals and FP16 fingerprint spectrum, FP32 arithmetic."""
+    wl = synth.make_workload(4, H=240, W=320, F=4, grid=synth.Grid(0.96, 0.02, 5, -2.0, 1.0, 5))
+    res, got = _gpu_search(ctx, prnu, wl, dtype=dtype, normalise=True)
+    R = [oracle.prnu_residual(f, normalise=True)[0] for f in wl.frames]
+    best, ref = oracle.grid_search(R, [oracle.fingerprint_term(wl.fingerprints[0])], wl.grid)
+    err = _assert_all_close(got, ref, tol)
+    print(f"{dtype}: max PCE rel err {err:.3g}")
+    for f in range(4):
+        assert (res[f, 0]["pce"] >= 60) == (best[f][0]["pce"] >= 60)
+        if best[f][0]["pce"] >= 60:
+            assert res[f, 0]["cand_idx"] == best[f][0]["cand"]
+
+
+def test_fullhd_planted_frames_sampled(ctx, prnu):
+    """1080p, full 41x41 grid on planted on-grid frames (the bench's launch
+    configuration); arg-max == planted truth, sampled candidates vs the oracle."""
+    wl = synth.make_workload(2, F=2, on_grid=True)
+    res, got = _gpu_search(ctx, prnu, wl)
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    FK = np.fft.rfft2(K0)
+    g = wl.grid
+    for f in range(2):
+        lam, th, sy, sx = wl.planted[f]
+        r = res[f, 0]
+        assert r["lam"] == np.float32(lam) and r["th_deg"] == np.float32(th)
+        assert (r["dy"], r["dx"]) == (sy, sx)
+        Rf = oracle.prnu_residual(wl.frames[f])[0]
+        cand = int(r["cand_idx"])
+        rng = np.random.default_rng(f)
+        for c in [cand, cand + 1 if cand % 41 < 40 else cand - 1, int(rng.integers(0, g.size))]:
+            i, j = divmod(c, g.nth)
+            o = oracle.score(Rf, K0, g.lam_node(i), g.th_node(j), FK)
+            assert got[f, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL), (f, c)
+
+
+# ------------------------------------------------------------------ edge cases and errors
+
+def test_empty_and_invalid_arguments(ctx, prnu):
+    R = torch.zeros((0, 64, 64), device=DEV)
+    K = torch.zeros((64, 64), device=DEV)
+    h = ctx.prnu_fingerprint_term(K)
+    res = ctx.eis_grid_search(R, [h], synth.GRID_C1)
+    assert res.shape == (0, 1)
+    with pytest.raises(prnu.PrnuError) as e:
+        ctx.prnu_fingerprint_term(torch.zeros((64, 70), device=DEV))     # 70 = 2*5*7
+    assert e.value.code == prnu.PRNU_EINVAL
+    with pytest.raises(prnu.PrnuError) as e:
+        ctx.prnu_fingerprint_term(torch.zeros((14, 64), device=DEV))     # below 16
+    assert e.value.code == prnu.PRNU_EINVAL
+    with pytest.raises(prnu.PrnuError) as e:
+        ctx.eis_grid_search(torch.zeros((1, 64, 64), device=DEV), [h + 999], synth.GRID_C1)
+    assert e.value.code == prnu.PRNU_ENOTFOUND
+    with pytest.raises(prnu.PrnuError) as e:
+        ctx.eis_grid_search(torch.zeros((1, 64, 64), device=DEV), [h], synth.GRID_C1,
+                            windows=np.array([[0, 11, 0, 3]]))
+    assert e.value.code == prnu.PRNU_EINVAL
+    ctx.prnu_fingerprint_release(h)
+    with pytest.raises(prnu.PrnuError) as e:
+        ctx.prnu_fingerprint_release(h)
+    assert e.value.code == prnu.PRNU_ENOTFOUND
+
+
+def test_constant_frames_score_zero(ctx, prnu):
+    frames = torch.full((2, 64, 64), 90, dtype=torch.uint8, device=DEV)
+    R = torch.empty((2, 64, 64), device=DEV)
+    ctx.prnu_residual(frames, R)
+    assert float(R.abs().max()) == 0.0
+    K = torch.from_numpy(np.random.default_rng(0).standard_normal((64, 64)).astype(np.float32)).to(DEV)
+    h = ctx.prnu_fingerprint_term(K)
+    res = ctx.eis_grid_search(R, [h], synth.Grid(0.98, 0.02, 3, -1.0, 1.0, 3))
+    ctx.prnu_fingerprint_release(h)
+    assert np.all(res["pce"] == 0.0) and np.all(res["cand_idx"] == 0)
+
+
+def test_launch_counter_advances(ctx, prnu):
+    n0 = ctx.prnu_launch_count()
+    frames = torch.zeros((1, 32, 32), dtype=torch.uint8, device=DEV)
+    R = torch.empty((1, 32, 32), device=DEV)
+    ctx.prnu_residual(frames, R)
+    assert ctx.prnu_launch_count() > n0
