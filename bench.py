@@ -1,0 +1,381 @@
+"""Benchmark of the EIS-inversion grid search: warp + xcorr + PCE candidates/s at 1080p.
+
+Workload (default): 30 synthetic stabilised frames of 1920x1080 luma, one
+fingerprint, the full 41 x 41 (scale, rotation) grid: 50,430 candidates per
+step.  A step is one pass of the whole hot path: noise residual of the 30
+frames, fingerprint spectrum, grid search, per-frame arg-max.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is device-timed with the frames already
+resident in HBM; `e2e` is the same metric through the C ABI with the frames and
+fingerprint in pinned host memory, host<->device copies inside the timed
+region.  The reference arm (--impl reference) times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "warp+xcorr+PCE candidates/s at 1080p vs HBM roofline; served p50/p99 query latency"
+UNIT = "candidates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=30)
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--no-extras", action="store_true", help="skip the naive-path and CPU-oracle legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- algorithmic bytes
+
+def kernel_bytes(H, W, s_in, s_k):
+    """Algorithmic DRAM bytes per candidate of each kernel of the fused path
+    (packed half spectrum: H x W/2 complex64 = 4*H*W bytes)."""
+    spec = 4 * H * W
+    return {
+        "row_forward": s_in * H * W + spec,                # read residual, write row spectrum
+        "column": spec + s_k * H * W // 2 + spec,          # read, fingerprint spectrum, write
+        "row_inverse": spec + 16 * H,                       # read, per-row stats
+        "finalize": 16 * H + 12 * 4 * W,                    # stats + the window's rows
+        "fused": s_in * H * W + (32 + s_k) * H * W // 2,    # whole path (one pass)
+    }
+
+
+def path_bytes(H, W, s_in, s_k):
+    return s_in * H * W + (32 + s_k) * H * (W // 2)
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2207_14507_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        h.update(n.encode() + open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, H, W, dtype):
+    """DRAM bytes per candidate of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(f"{kernel}:{H}x{W}:{dtype}")
+    if not e or e.get("csrc_digest") != csrc_digest():
+        return None
+    return e.get("dram_bytes_per_candidate")
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        mhz, mx, reasons = [], None, set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+
+def cpu_oracle_sample(wl, target_s, max_cands=200):
+    """Time the FP64 oracle, as it stands, on frame 0 of the workload: its
+    residual once, then candidates spread over the grid until ~target_s."""
+    import oracle
+    g = wl.grid
+    t0 = time.perf_counter()
+    R, _ = oracle.prnu_residual(wl.frames[0])
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    FK = np.fft.rfft2(K0)
+    t_res = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    order = rng.permutation(g.size)
+    n = 0
+    t1 = time.perf_counter()
+    while n < max_cands and (n < 2 or time.perf_counter() - t1 < target_s):
+        i, j = divmod(int(order[n]), g.nth)
+        oracle.score(R, K0, g.lam_node(i), g.th_node(j), FK)
+        n += 1
+    t_c = time.perf_counter() - t1
+    per_cand = t_c / n + t_res / g.size
+    return {"value": 1.0 / per_cand, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"frame 0 of the workload: residual + fingerprint spectrum once, {n} of {g.size} "
+                      f"candidates ({t_c:.1f} s), single process, numpy FFT"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    wl = synth.make_workload(2, F=1)
+    H, W = wl.frames.shape[1:]
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, 0.0, max_cands=1)
+    vals = [cpu_oracle_sample(wl, per_step) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, H, W, 30),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, H, W, F):
+    return {"workload": f"plain-1080p: {F} stabilised frames {W}x{H} luma, 1 fingerprint, full 41x41 "
+                        f"(scale, rotation) grid, residual + fingerprint spectrum + search per step",
+            "frames": F, "H": H, "W": W, "fingerprints": 1, "grid": "41x41",
+            "candidates_per_step": F * 1681, "storage": args.dtype,
+            "l2": "inputs larger than L2 (frames + residuals 311 MB; >16 GB of spectra streamed per step)"}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+
+    wl = synth.make_workload(2, F=args.frames)
+    F, H, W = wl.frames.shape
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    fpd = {"f32": prnu.PRNU_F32, "f16": prnu.PRNU_F16, "bf16": prnu.PRNU_F16}[args.dtype]
+    s_in = 4 if args.dtype == "f32" else 2
+    s_k = 8 if args.dtype == "f32" else 4
+    flags = prnu.PRNU_WEIGHT_BY_INTENSITY | (0 if args.dtype == "f32" else prnu.PRNU_NORMALISE)
+    ncand = F * wl.grid.size
+
+    ctx = prnu.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    frames_d = torch.from_numpy(wl.frames).to(dev)
+    K_d = torch.from_numpy(wl.fingerprints[0]).to(dev)
+    R = torch.empty((F, H, W), dtype=tdt, device=dev)
+    scale = torch.empty(F, dtype=torch.float32, device=dev)
+    out_d = torch.empty((F, 32), dtype=torch.uint8, device=dev)   # prnu_result [F*P]
+
+    def step():
+        ctx.prnu_residual(frames_d, R, scale=scale, flags=flags)
+        h = ctx.prnu_fingerprint_term(K_d, fpd)
+        ctx.eis_grid_search(R, [h], wl.grid, scale=scale, out=out_d)
+        ctx.prnu_fingerprint_release(h)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.prnu_launch_count()
+    with ClockSampler(local) as clk:
+        ctx.prnu_profile_begin()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+        prof = ctx.prnu_profile_end()
+    launches = ctx.prnu_launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ncand * ws / (ms / 1e3)
+
+    # ---- e2e: the same step through the C ABI from pinned host memory
+    frames_h = torch.from_numpy(wl.frames).pin_memory()
+    K_h = torch.from_numpy(wl.fingerprints[0]).pin_memory()
+    fr2 = torch.empty_like(frames_d)
+    K2 = torch.empty_like(K_d)
+
+    def step_e2e():
+        fr2.copy_(frames_h, non_blocking=True)
+        K2.copy_(K_h, non_blocking=True)
+        ctx.prnu_residual(fr2, R, scale=scale, flags=flags)
+        h = ctx.prnu_fingerprint_term(K2, fpd)
+        res = ctx.eis_grid_search(R, [h], wl.grid, scale=scale)      # host results: D2H + sync inside
+        ctx.prnu_fingerprint_release(h)
+        return res
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = step_e2e()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ncand * ws / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(wl.frames.nbytes + wl.fingerprints[0].nbytes),
+           "d2h_bytes_per_step": int(res.nbytes)}
+
+    # ---- roofline of the dominant kernel (event-timed inside the timed region)
+    peak, peak_kind = hbm_peak()
+    kb = kernel_bytes(H, W, s_in, s_k)
+    timed = {k: v for k, v in prof.items() if k in kb}
+    dom = max(timed, key=lambda k: timed[k]["total_ms"])
+    cands_total = ncand * args.steps
+    achieved = kb[dom] * cands_total / (timed[dom]["total_ms"] / 1e3) / 1e9
+    traffic = traffic_for(dom, H, W, args.dtype)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": traffic, "algorithmic_bytes_per_candidate": kb[dom],
+            "share_of_step": round(timed[dom]["total_ms"] / (ms * args.steps), 3)}
+    pb = path_bytes(H, W, s_in, s_k)
+    path_roof = {"bytes_per_candidate": pb, "achieved": round(pb * value / ws / 1e9, 1),
+                 "frac": round(pb * value / ws / 1e9 / peak, 4)}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": round(v["total_ms"] / args.steps, 3)}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": workload_config(args, H, W, F),
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "path_roofline": path_roof,
+        "kernels": kernels, "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not args.no_extras:
+        # plain per-candidate GPU path on the same inputs (a sample of frame 0's grid)
+        if args.dtype == "f32":
+            win = np.array([[18, 22, 18, 22]], np.int32)       # 25 candidates
+            Rn = R[:1].contiguous()
+            h = ctx.prnu_fingerprint_term(K_d, prnu.PRNU_F32)
+            ctx.eis_grid_search(Rn, [h], wl.grid, windows=win, naive=True)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reps = 4
+            for _ in range(reps):
+                ctx.eis_grid_search(Rn, [h], wl.grid, windows=win, naive=True)
+            torch.cuda.synchronize(dev)
+            naive = 25 * reps / (time.perf_counter() - t0)
+            ctx.prnu_fingerprint_release(h)
+            line["naive_baseline"] = {"value": round(naive, 1), "unit": UNIT,
+                                      "speedup": round(value / naive, 2),
+                                      "sample": "frame 0, 5x5 window (25 candidates), FP32, one candidate per launch sequence"}
+        line["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_seconds)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -230,6 +230,23 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg);
 int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budget_ms, prnu_tuning* best,
                   prnu_stream stream);
 
+/* ---------------------------------------------------------------- profiling */
+
+/* Per-kernel timing: while a profile is open, every launch of the context is
+ * bracketed by two CUDA events recorded on its launching stream. */
+typedef struct {
+    char name[32];          /* kernel kind, e.g. "row_forward", "column" */
+    uint64_t launches;
+    double total_ms;        /* sum of the event-measured durations */
+} prnu_kernel_stat;
+
+/* Start recording (clears earlier records). */
+int prnu_profile_begin(prnu_ctx* ctx);
+
+/* Stop recording, wait for the recorded events and aggregate them by kernel
+ * kind into out[0..max) (max >= 1); *n_out receives the number of kinds seen. */
+int prnu_profile_end(prnu_ctx* ctx, prnu_kernel_stat* out, int max, int* n_out);
+
 #ifdef __cplusplus
 }
 #endif

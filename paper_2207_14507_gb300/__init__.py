@@ -57,6 +57,10 @@ class prnu_tuning(C.Structure):
     _fields_ = [("col_width", C.c_int), ("pairs_per_block", C.c_int), ("wave", C.c_int)]
 
 
+class prnu_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
 RESULT_DTYPE = np.dtype([("lam", "<f4"), ("th_deg", "<f4"), ("dy", "<i4"), ("dx", "<i4"), ("pce", "<f8"),
                          ("peak", "<f4"), ("cand_idx", "<i4")])
 assert RESULT_DTYPE.itemsize == C.sizeof(prnu_result) == 32
@@ -82,6 +86,8 @@ _SIGNATURES = {
     "prnu_get_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
     "prnu_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
     "prnu_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(prnu_tuning), _P]),
+    "prnu_profile_begin": (C.c_int, [_P]),
+    "prnu_profile_end": (C.c_int, [_P, C.POINTER(prnu_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
 }
 EXPORTED = tuple(_SIGNATURES)
 
@@ -247,6 +253,17 @@ class Context:
         s = prnu_server_stats()
         _check(lib().prnu_server_stats_get(self.h, C.byref(s)), "prnu_server_stats_get")
         return {k: int(getattr(s, k)) for k, _ in s._fields_}
+
+    # --------------------------------------------------------------- profiling
+    def prnu_profile_begin(self):
+        _check(lib().prnu_profile_begin(self.h), "prnu_profile_begin")
+
+    def prnu_profile_end(self) -> dict:
+        arr = (prnu_kernel_stat * 32)()
+        n = C.c_int()
+        _check(lib().prnu_profile_end(self.h, arr, 32, C.byref(n)), "prnu_profile_end")
+        return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms))
+                for i in range(min(n.value, 32))}
 
     # --------------------------------------------------------------- tuning
     def prnu_get_tuning(self, H, W) -> dict:

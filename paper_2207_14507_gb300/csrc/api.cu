@@ -664,6 +664,57 @@ int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W,
   });
 }
 
+int prnu_profile_begin(prnu_ctx* ctx) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto& lc = ctx->launches;
+    std::lock_guard<std::mutex> lk2(lc.mu);
+    for (auto& r : lc.recs) {
+      lc.pool.push_back(r.a);
+      lc.pool.push_back(r.b);
+    }
+    lc.recs.clear();
+    lc.profiling = true;
+  });
+}
+
+int prnu_profile_end(prnu_ctx* ctx, prnu_kernel_stat* out, int max, int* n_out) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && out && max >= 1, "bad arguments");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto& lc = ctx->launches;
+    std::lock_guard<std::mutex> lk2(lc.mu);
+    lc.profiling = false;
+    std::vector<uint64_t> cnt(kKindCount, 0);
+    std::vector<double> ms(kKindCount, 0.0);
+    for (auto& r : lc.recs) {
+      PRNU_CUDA_TRY(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      PRNU_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+      cnt[r.kind]++;
+      ms[r.kind] += t;
+      lc.pool.push_back(r.a);
+      lc.pool.push_back(r.b);
+    }
+    lc.recs.clear();
+    int k = 0;
+    for (int i = 0; i < kKindCount; ++i) {
+      if (!cnt[i]) continue;
+      if (k < max) {
+        memset(out[k].name, 0, sizeof(out[k].name));
+        strncpy(out[k].name, kKindNames[i], sizeof(out[k].name) - 1);
+        out[k].launches = cnt[i];
+        out[k].total_ms = ms[i];
+      }
+      ++k;
+    }
+    if (n_out) *n_out = k;
+  });
+}
+
 int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
   return guarded([&] {
     PRNU_CHECK_ARG(ctx && out, "NULL argument");

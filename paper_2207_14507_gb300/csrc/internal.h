@@ -45,9 +45,41 @@ void col_launch_shape(const FftPlan& p, int lg, int* threads, int* maxb);
 
 // ---------------------------------------------------------------- launchers (search.cu)
 
-// counts every kernel launch
+// Kernel kinds for per-kernel timing.
+enum KernelKind {
+  kKindResidual = 0, kKindFpSpectrum, kKindRowForward, kKindColumn, kKindRowInverse, kKindFinalize,
+  kKindArgmax, kKindScatter, kKindNaiveWarp, kKindNaivePce, kKindFused, kKindCount
+};
+extern const char* const kKindNames[kKindCount];
+
+// Counts every kernel launch; while profiling, brackets each launch with a
+// pair of CUDA events recorded on the launching stream.
 struct LaunchCounter {
   std::atomic<uint64_t> n{0};
+  bool profiling = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::mutex mu;
+  cudaEvent_t take();
+  void start(int kind, cudaStream_t s);
+  void stop(cudaStream_t s);
+};
+
+// RAII bracket around one launch (or a short fixed sequence of launches).
+struct ProfScope {
+  LaunchCounter& lc;
+  cudaStream_t s;
+  bool on;
+  ProfScope(LaunchCounter& l, int kind, cudaStream_t st) : lc(l), s(st), on(l.profiling) {
+    if (on) lc.start(kind, s);
+  }
+  ~ProfScope() {
+    if (on) lc.stop(s);
+  }
 };
 
 void launch_row_forward(const PassArgs& a, bool warp, const float* mean_sub, float2* out, cudaStream_t s,

@@ -149,6 +149,7 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
   const dim3 b(kBX, kBY);
   const dim3 g((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, F);
   const int weight = (flags & PRNU_WEIGHT_BY_INTENSITY) ? 1 : 0;
+  ProfScope ps(lc, kKindResidual, s);
   PRNU_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * F, s));
   k_resid_moments<<<g, b, 0, s>>>(frames, pitch, H, W, acc);
   PRNU_CUDA_TRY(cudaGetLastError());

@@ -568,6 +568,7 @@ void launch_row_forward(const PassArgs& a, bool warp, const float* mean_sub, flo
   const int ppb = a.pairs_per_block;
   dim3 g((a.H / 2 + ppb - 1) / ppb, a.nitems), b(ppb * T);
   const size_t sm = row_smem_bytes(a.W, ppb);
+  ProfScope ps(lc, kKindRowForward, s);
   if (warp) {
     if (a.rdtype == kF32) k_row_forward<kF32, true><<<g, b, sm, s>>>(a, mean_sub, out);
     else if (a.rdtype == kF16) k_row_forward<kF16, true><<<g, b, sm, s>>>(a, mean_sub, out);
@@ -590,6 +591,7 @@ void launch_col(const PassArgs& a, int mode, float2* out_f32, void* out_f16, con
   dim3 g((Wh + nc - 1) / nc, a.nitems), b(T);
   const size_t sm = 2 * (size_t)a.H * nc * sizeof(float2);
   __half2* o16 = reinterpret_cast<__half2*>(out_f16);
+  ProfScope ps(lc, kKindColumn, s);
   k_col<<<g, b, sm, s>>>(a, mode, out_f32, o16, scale);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -601,6 +603,7 @@ void launch_row_inverse(const PassArgs& a, float* c_out, cudaStream_t s, LaunchC
   const int ppb = a.pairs_per_block;
   dim3 g((a.H / 2 + ppb - 1) / ppb, a.nitems), b(ppb * T);
   const size_t sm = row_smem_bytes(a.W, ppb);
+  ProfScope ps(lc, kKindRowInverse, s);
   k_row_inverse<<<g, b, sm, s>>>(a, c_out);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -611,6 +614,7 @@ void launch_finalize(const PassArgs& a, cudaStream_t s, LaunchCounter& lc) {
   row_launch_shape(a.prow, &T, &maxb);
   dim3 g(a.nitems), b(T);
   const size_t sm = row_smem_bytes(a.W, 1);
+  ProfScope ps(lc, kKindFinalize, s);
   k_finalize<<<g, b, sm, s>>>(a);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -620,6 +624,7 @@ void launch_argmax(const CandResult* res, const WorkItem* items, const int* grou
                    prnu_result* out, const float* /*scale*/, int H, int W, cudaStream_t s, LaunchCounter& lc) {
   if (ngroups <= 0) return;
   const int warps = 8;
+  ProfScope ps(lc, kKindArgmax, s);
   k_argmax<<<(ngroups + warps - 1) / warps, warps * 32, 0, s>>>(res, items, group_start, ngroups, out, H, W);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -627,6 +632,7 @@ void launch_argmax(const CandResult* res, const WorkItem* items, const int* grou
 
 void launch_scatter_all(const CandResult* res, int nitems, int cmax, double* all, cudaStream_t s, LaunchCounter& lc) {
   if (nitems <= 0) return;
+  ProfScope ps(lc, kKindScatter, s);
   k_scatter_all<<<(nitems + 255) / 256, 256, 0, s>>>(res, nitems, cmax, all);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -634,6 +640,7 @@ void launch_scatter_all(const CandResult* res, int nitems, int cmax, double* all
 
 void launch_fp_stats(const float* K, int H, int W, double* partials, int nblk, float* mean_out, float* scale_out,
                      float* inv_scale_out, bool half, cudaStream_t s, LaunchCounter& lc) {
+  ProfScope ps(lc, kKindFpSpectrum, s);
   k_fp_partials<<<nblk, 256, 0, s>>>(K, (size_t)H * W, partials);
   PRNU_LAUNCH_CHECK();
   k_fp_finish<<<1, 32, 0, s>>>(partials, nblk, (size_t)H * W, half ? 1 : 0, mean_out, scale_out, inv_scale_out);
@@ -642,6 +649,7 @@ void launch_fp_stats(const float* K, int H, int W, double* partials, int nblk, f
 }
 
 void launch_naive_warp(const PassArgs& a, float* X, cudaStream_t s, LaunchCounter& lc) {
+  ProfScope ps(lc, kKindNaiveWarp, s);
   k_naive_warp<<<1024, 256, 0, s>>>(a, X);
   PRNU_LAUNCH_CHECK();
   lc.n++;
@@ -650,11 +658,39 @@ void launch_naive_warp(const PassArgs& a, float* X, cudaStream_t s, LaunchCounte
 void launch_naive_pce(const float* C, int H, int W, const WorkItem* item, const FpDesc* fps, const float* scale,
                       CandResult* out, float* bmax, int* barg, double* bsum, int nblk, cudaStream_t s,
                       LaunchCounter& lc) {
+  ProfScope ps(lc, kKindNaivePce, s);
   k_naive_reduce<<<nblk, 256, 0, s>>>(C, (size_t)H * W, bmax, barg, bsum);
   PRNU_LAUNCH_CHECK();
   k_naive_final<<<1, 32, 0, s>>>(C, H, W, item, fps, scale, bmax, barg, bsum, nblk, out);
   PRNU_LAUNCH_CHECK();
   lc.n += 2;
+}
+
+const char* const kKindNames[kKindCount] = {"residual", "fingerprint_spectrum", "row_forward", "column",
+                                             "row_inverse", "finalize", "argmax", "scatter", "naive_warp",
+                                             "naive_pce", "fused"};
+
+cudaEvent_t LaunchCounter::take() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  PRNU_CUDA_TRY(cudaEventCreate(&e));
+  return e;
+}
+
+void LaunchCounter::start(int kind, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(mu);
+  Rec r{kind, take(), take()};
+  PRNU_CUDA_TRY(cudaEventRecord(r.a, s));
+  recs.push_back(r);
+}
+
+void LaunchCounter::stop(cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(mu);
+  if (!recs.empty()) cudaEventRecord(recs.back().b, s);
 }
 
 template <class K>
