@@ -110,7 +110,7 @@ def lib() -> C.CDLL:
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .buildlib import build as _build
     return _build(force=force)
 
 

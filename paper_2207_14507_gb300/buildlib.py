@@ -1,6 +1,6 @@
 """Build libprnu.so in-tree: one nvcc process per translation unit (in parallel), then a link.
 
-Usage: python -m paper_2207_14507_gb300.build [--force]
+Usage: python -m paper_2207_14507_gb300.buildlib [--force]
 """
 from __future__ import annotations
 
