@@ -170,6 +170,25 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
 int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W,
               double* pce, int* dy, int* dx, float* peak, prnu_stream stream);
 
+/* pce_score for callers that cannot allocate device memory (the paper has no
+ * counterpart: this is a deployment variant).  Some callers cannot call
+ * cudaMalloc -- code where the allocator is off limits, such as a real-time
+ * pipeline that fixes its memory at start-up, a host framework that owns every
+ * device allocation, or a process already at its memory budget.  This entry
+ * point needs no context and no fingerprint handle and allocates nothing: it
+ * computes the PCE of d_X (device float [H][W]) against the fingerprint d_K
+ * (device float [H][W], mean removed inside) in a fixed static device scratch
+ * array of about 8.5 MB that every GPU loading the library holds until exit.
+ *  - H*W must not exceed 2^20 pixels (e.g. 1280x720, 1024x1024), with the
+ *    size rule of pce_score; larger frames return PRNU_EINVAL.
+ *  - All calls share the scratch array, which keeps the last call's contents;
+ *    calls whose GPU work overlaps race on it, so order them (one stream).
+ *  - The first call on a device looks up the array's address and sets kernel
+ *    attributes; make it before any stream capture on that device.
+ * Host outputs, any of them may be NULL.  Synchronous (waits for `stream`). */
+int pce_score_noalloc(const float* d_X, const float* d_K, int H, int W,
+                      double* pce, int* dy, int* dx, float* peak, prnu_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* One forensic query: F frames tested against P fingerprints. */

@@ -80,6 +80,8 @@ _SIGNATURES = {
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "pce_score": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                             C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
+    "pce_score_noalloc": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
     "query_submit": (C.c_int, [_P, C.POINTER(prnu_query), C.POINTER(C.c_uint64)]),
     "query_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
     "prnu_server_stats_get": (C.c_int, [_P, C.POINTER(prnu_server_stats)]),
@@ -142,6 +144,17 @@ def make_windows(windows):
     for i, (a, b, c, d) in enumerate(w):
         arr[i] = prnu_window(int(a), int(b), int(c), int(d))
     return arr
+
+
+def pce_score_noalloc(X, K, stream=None) -> dict:
+    """PCE of the aligned pair (X, K) without any device allocation, for callers
+    that cannot allocate (see include/prnu.h).  X, K: float32 CUDA tensors [H, W]
+    with H*W <= 2^20."""
+    H, W = X.shape
+    pce, dy, dx, peak = C.c_double(), C.c_int(), C.c_int(), C.c_float()
+    _check(lib().pce_score_noalloc(_ptr(X), _ptr(K), H, W, C.byref(pce), C.byref(dy), C.byref(dx),
+                                   C.byref(peak), _stream(stream)), "pce_score_noalloc")
+    return dict(pce=pce.value, dy=dy.value, dx=dx.value, peak=peak.value)
 
 
 class Context:
