@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-extras", action="store_true", help="skip the naive-path and CPU-oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--autotune-ms", type=float, default=5000.0,
+                    help="time budget of the library autotuner run before the warm-up (0 = defaults)")
     return ap.parse_args()
 
 
@@ -250,6 +252,9 @@ def run_ours(args):
     scale = torch.empty(F, dtype=torch.float32, device=dev)
     out_d = torch.empty((F, 32), dtype=torch.uint8, device=dev)   # prnu_result [F*P]
 
+    tuning = ctx.prnu_autotune(H, W, fpd, budget_ms=args.autotune_ms) if args.autotune_ms > 0 \
+        else ctx.prnu_get_tuning(H, W)
+
     def step():
         ctx.prnu_residual(frames_d, R, scale=scale, flags=flags)
         h = ctx.prnu_fingerprint_term(K_d, fpd)
@@ -337,7 +342,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": workload_config(args, H, W, F),
+        "config": dict(workload_config(args, H, W, F), tuning=tuning),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "path_roofline": path_roof,
         "kernels": kernels, "clocks": clk.summary(),
     }

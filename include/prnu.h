@@ -230,13 +230,17 @@ int prnu_server_stats_get(prnu_ctx* ctx, prnu_server_stats* out);
 
 /* ---------------------------------------------------------------- tuning */
 
-/* Launch configuration of the fused path for one frame size and storage type:
- * columns per column-pass block, row pairs per row block, and candidates per
- * wave (the number of per-candidate spectra kept in the workspace). */
+/* Launch configuration of the fused path for one frame size: columns per
+ * column-pass block and row pairs per row block of the generic kernels, the
+ * candidates per wave (per-candidate spectra kept in the workspace), and which
+ * compile-time-planned column kernel to use where the size has them
+ * (1920x1080, 1280x720, 3840x2160, 256x256). */
 typedef struct {
     int col_width;        /* 4, 8 or 16 */
     int pairs_per_block;  /* 1, 2 or 4 */
     int wave;             /* candidates in flight, >= 1 */
+    int variant;          /* compile-time-planned column kernel variant for this size
+                             (0.. n-1), or -1 for the generic runtime-plan kernels */
 } prnu_tuning;
 
 /* Read / override the configuration used for frames of H x W. */

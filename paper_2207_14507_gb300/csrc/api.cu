@@ -10,6 +10,7 @@
 #include <functional>
 
 #include "internal.h"
+#include "search_fixed.h"
 #include "server.h"
 
 namespace prnu {
@@ -299,12 +300,18 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.row_threads = rowT;
 
   if (!naive) {
+    const FixedShape* fs = tn.variant >= 0 ? find_fixed(H, W) : nullptr;
+    if (fs && (H / 2) % fs->ppb != 0) fs = nullptr;
     for (int i0 = 0; i0 < n; i0 += wave) {
       a.item0 = i0;
       a.nitems = std::min(wave, n - i0);
-      launch_row_forward(a, true, nullptr, nullptr, s, c->launches);
-      launch_col(a, 0, nullptr, nullptr, nullptr, s, c->launches);
-      launch_row_inverse(a, nullptr, s, c->launches);
+      if (fs) {
+        launch_fixed_wave(a, *fs, tn.variant, s, c->launches);
+      } else {
+        launch_row_forward(a, true, nullptr, nullptr, s, c->launches);
+        launch_col(a, 0, nullptr, nullptr, nullptr, s, c->launches);
+        launch_row_inverse(a, nullptr, s, c->launches);
+      }
       launch_finalize(a, s, c->launches);
     }
   } else {
@@ -724,6 +731,7 @@ int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
     out->col_width = 1 << t.col_log2;
     out->pairs_per_block = t.ppb;
     out->wave = t.wave;
+    out->variant = t.variant;
   });
 }
 
@@ -745,7 +753,10 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
     PRNU_CHECK_ARG(2 * (size_t)H * (1u << lg) * sizeof(float2) <= 227 * 1024, "column strip exceeds shared memory");
     row_launch_shape(pr, &T, &mb);
     PRNU_CHECK_ARG(T * cfg->pairs_per_block <= 512, "row block exceeds 512 threads");
-    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave};
+    const FixedShape* fs = find_fixed(H, W);
+    PRNU_CHECK_ARG(cfg->variant >= -1 && cfg->variant < (fs ? (int)fs->cols.size() : 0),
+                   "variant out of range for this frame size (-1 = generic kernels)");
+    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant};
   });
 }
 

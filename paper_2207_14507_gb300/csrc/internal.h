@@ -107,6 +107,23 @@ void launch_naive_pce(const float* C, int H, int W, const WorkItem* item, const 
                       cudaStream_t s, LaunchCounter& lc);
 void set_kernel_attributes();
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// minus the kernel's static shared memory (asking for more is rejected and
+// leaves the 48 KB default in place).
+template <class K>
+inline void allow_max_dynamic_smem(K k) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, (const void*)k) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers (residual.cu)
 
 void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, int flags, int dtype, void* out,
@@ -134,9 +151,10 @@ struct DeviceBuf {
 class Server;
 
 struct Tuning {
-  int col_log2 = 3;
-  int ppb = 2;
-  int wave = 64;
+  int col_log2 = 3;   // generic kernels: columns per column-pass block = 1 << col_log2
+  int ppb = 2;        // generic kernels: row pairs per row block
+  int wave = 64;      // candidates in flight
+  int variant = 0;    // compile-time-planned column variant; -1 = generic kernels only
 };
 
 }  // namespace prnu

@@ -557,7 +557,7 @@ __global__ void k_naive_final(const float* __restrict__ C, int H, int W, const W
 #define PRNU_LAUNCH_CHECK()                                                                 \
   do {                                                                                      \
     cudaError_t e_ = cudaGetLastError();                                                    \
-    if (e_ != cudaSuccess) throw Error{PRNU_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+    if (e_ != cudaSuccess) throw Error{PRNU_ECUDA, std::string(__func__) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
 void launch_row_forward(const PassArgs& a, bool warp, const float* mean_sub, float2* out, cudaStream_t s,
@@ -695,7 +695,7 @@ void LaunchCounter::stop(cudaStream_t s) {
 
 template <class K>
 static void allow_smem(K k) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  allow_max_dynamic_smem(k);
 }
 
 void set_kernel_attributes() {

@@ -14,7 +14,4 @@ extern "C" {
 int query_submit(prnu_ctx*, const prnu_query*, uint64_t*) { prnu::set_error("serving not built"); return PRNU_EINVAL; }
 int query_poll(prnu_ctx*, uint64_t, prnu_result*, int64_t) { prnu::set_error("serving not built"); return PRNU_EINVAL; }
 int prnu_server_stats_get(prnu_ctx*, prnu_server_stats* out) { if (out) *out = prnu_server_stats{}; return PRNU_OK; }
-int prnu_autotune(prnu_ctx* ctx, int H, int W, int, double, prnu_tuning* best, prnu_stream) {
-  return prnu_get_tuning(ctx, H, W, best ? best : nullptr);
-}
 }

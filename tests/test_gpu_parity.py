@@ -248,6 +248,45 @@ def test_fullhd_planted_frames_sampled(ctx, prnu):
             assert got[f, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL), (f, c)
 
 
+FIXED_SHAPES = [(256, 256, 2), (720, 1280, 3), (1080, 1920, 4), (2160, 3840, 3)]
+
+
+@pytest.mark.parametrize("H,W,nvar", FIXED_SHAPES)
+def test_fixed_plan_kernels_match_generic_and_oracle(ctx, prnu, H, W, nvar):
+    """Every compile-time-planned column variant of each instantiated frame size
+    gives the generic kernels' PCEs (1e-5) and the oracle's (1e-3)."""
+    g = synth.Grid(0.98, 0.01, 5, -1.0, 0.5, 5)
+    wl = synth.make_workload(2, H=H, W=W, F=1, grid=g, on_grid=True, s_max=16)
+    win = np.array([[1, 3, 1, 3]], np.int32)
+    t0 = ctx.prnu_get_tuning(H, W)
+    try:
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 4, -1)
+        res_g, got_g = _gpu_search(ctx, prnu, wl, windows=win)
+        for v in range(nvar):
+            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 4, v)
+            res_f, got_f = _gpu_search(ctx, prnu, wl, windows=win)
+            _assert_all_close(got_f, got_g, 1e-5)
+            assert res_f[0, 0]["cand_idx"] == res_g[0, 0]["cand_idx"]
+            assert (res_f[0, 0]["dy"], res_f[0, 0]["dx"]) == (res_g[0, 0]["dy"], res_g[0, 0]["dx"])
+    finally:
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"])
+    R = oracle.prnu_residual(wl.frames[0])[0]
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    FK = np.fft.rfft2(K0)
+    for c in (int(res_g[0, 0]["cand_idx"]), 2 * 5 + 1):
+        i, j = divmod(c, g.nth)
+        o = oracle.score(R, K0, g.lam_node(i), g.th_node(j), FK)
+        assert got_g[0, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL)
+
+
+def test_tuning_rejects_bad_variants(ctx, prnu):
+    t = ctx.prnu_get_tuning(1080, 1920)
+    with pytest.raises(prnu.PrnuError):
+        ctx.prnu_set_tuning(1080, 1920, t["col_width"], t["pairs_per_block"], t["wave"], 99)
+    with pytest.raises(prnu.PrnuError):
+        ctx.prnu_set_tuning(160, 200, 8, 2, 4, 0)    # no compile-time kernels for 160x200
+
+
 # ------------------------------------------------------------------ edge cases and errors
 
 def test_empty_and_invalid_arguments(ctx, prnu):
@@ -293,3 +332,14 @@ def test_launch_counter_advances(ctx, prnu):
     R = torch.empty((1, 32, 32), device=DEV)
     ctx.prnu_residual(frames, R)
     assert ctx.prnu_launch_count() > n0
+
+
+def test_autotune_picks_a_valid_configuration(ctx, prnu):
+    t = ctx.prnu_autotune(256, 256, prnu.PRNU_F32, budget_ms=3000.0)
+    assert t["variant"] in (-1, 0, 1) and t["wave"] >= 1
+    assert ctx.prnu_get_tuning(256, 256) == t
+    wl = synth.make_workload(1, F=1, on_grid=True)
+    res, got = _gpu_search(ctx, prnu, wl)
+    best, ref = _oracle_search(wl)
+    _assert_all_close(got, ref, FP32_TOL)
+    _assert_best_equal(res, best)
