@@ -220,6 +220,11 @@ int query_submit(prnu_ctx* ctx, const prnu_query* q, uint64_t* qid);
  * reported here (PRNU_ECUDA, PRNU_EDEVICE_ABORT). */
 int query_poll(prnu_ctx* ctx, uint64_t qid, prnu_result* out, int64_t timeout_us);
 
+/* Latency of a finished query (kept for the last 100000 queries): time from
+ * query_submit to admission (queued_ms) and to the moment its results reached
+ * host memory (total_ms), in milliseconds.  Errors: PRNU_ENOTFOUND. */
+int query_latency(prnu_ctx* ctx, uint64_t qid, double* queued_ms, double* total_ms);
+
 /* Serving statistics since creation: completed queries, candidates scored,
  * launches issued by the server, and the peak device bytes admitted. */
 typedef struct {

@@ -84,6 +84,7 @@ _SIGNATURES = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
     "query_submit": (C.c_int, [_P, C.POINTER(prnu_query), C.POINTER(C.c_uint64)]),
     "query_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
+    "query_latency": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "prnu_server_stats_get": (C.c_int, [_P, C.POINTER(prnu_server_stats)]),
     "prnu_get_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
     "prnu_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
@@ -261,6 +262,11 @@ class Context:
             return None
         _check(code, "query_poll")
         return res
+
+    def query_latency(self, qid: int) -> dict:
+        qm, tm = C.c_double(), C.c_double()
+        _check(lib().query_latency(self.h, qid, C.byref(qm), C.byref(tm)), "query_latency")
+        return dict(queued_ms=qm.value, total_ms=tm.value)
 
     def prnu_server_stats_get(self) -> dict:
         s = prnu_server_stats()

@@ -301,7 +301,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
 
   if (!naive) {
     const FixedShape* fs = tn.variant >= 0 ? find_fixed(H, W) : nullptr;
-    if (fs && (H / 2) % fs->ppb != 0) fs = nullptr;
+    if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
     for (int i0 = 0; i0 < n; i0 += wave) {
       a.item0 = i0;
       a.nitems = std::min(wave, n - i0);

@@ -59,12 +59,15 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
     if (rc != PRNU_OK) throw Error{rc, prnu_last_error()};
     Tuning base = tuning_for(ctx, H, W);
     const FixedShape* fs = find_fixed(H, W);
-    std::vector<int> variants = {-1};
-    if (fs && (H / 2) % fs->ppb == 0)
-      for (int v = 0; v < (int)fs->cols.size(); ++v) variants.push_back(v);
+    // (column variant, row pairs per block); -1 = generic kernels
+    std::vector<std::pair<int, int>> variants = {{-1, base.ppb}};
+    if (fs)
+      for (const FixedRow& r : fs->rows)
+        if (fixed_supports(*fs, H, r.ppb))
+          for (int v = 0; v < (int)fs->cols.size(); ++v) variants.push_back({v, r.ppb});
     const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
     std::vector<int> waves;
-    for (int w : {16, 32, 64, 128})
+    for (int w : {8, 16, 32, 64, 128})
       if ((size_t)w * per_item < ctx->budget / 4) waves.push_back(w);
     if (waves.empty()) waves.push_back(1);
     // 8 x 16 grid nodes per frame: 256 candidates per timed search
@@ -80,13 +83,14 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
     prnu_result* d_out = nullptr;
     ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * F);
     d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
-    for (int v : variants) {
+    for (auto vp : variants) {
       for (int w : waves) {
         const double spent =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         if (spent > budget_ms && best_ms < 1e300) break;
         Tuning t = base;
-        t.variant = v;
+        t.variant = vp.first;
+        t.ppb = vp.second;
         t.wave = w;
         ctx->tuning[{H, W}] = t;
         SearchCall call;

@@ -65,7 +65,30 @@ struct PassArgs {
   int pairs_per_block;
   int col_log2;               // columns per column-pass block = 1 << col_log2
   int row_threads;            // threads per row FFT
+  // Optional per-slot indirection, used when one wave mixes candidates of
+  // several queries (serving): item and result of slot s live at
+  // item_ptrs[s] / result_ptrs[s], and frame f's residual at frame_ptrs[f].
+  // nullptr = the contiguous arrays above.
+  const WorkItem* const* item_ptrs;
+  CandResult* const* result_ptrs;
+  const void* const* frame_ptrs;
 };
+
+__device__ __forceinline__ WorkItem item_of(const PassArgs& a, int slot) {
+  return a.item_ptrs ? *a.item_ptrs[slot] : a.items[a.item0 + slot];
+}
+__device__ __forceinline__ CandResult* result_of(const PassArgs& a, int slot) {
+  return a.result_ptrs ? a.result_ptrs[slot] : a.results + a.item0 + slot;
+}
+// residual of frame f: base pointer, element offset of the frame's first pixel
+__device__ __forceinline__ const void* frame_of(const PassArgs& a, int f, size_t* base) {
+  if (a.frame_ptrs) {
+    *base = 0;
+    return a.frame_ptrs[f];
+  }
+  *base = (size_t)f * a.H * a.W;
+  return a.resid;
+}
 
 // ---------------------------------------------------------------- storage loads / stores
 

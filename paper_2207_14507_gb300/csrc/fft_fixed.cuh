@@ -142,17 +142,19 @@ struct RowSt {
   float2* p;
   __device__ __forceinline__ void operator()(int i, int, float2 v) const { p[rpad(i)] = v; }
 };
-// column layout: element i of column c at p[i*NC + c]
+// column layout: element i of column c at p[rpad(i*NC + c)]; the padding (one
+// float2 per 16) spreads the stride-R*NC stores of the early stages over the banks
 template <int NC>
 struct ColLd {
   const float2* p;
-  __device__ __forceinline__ float2 operator()(int i, int c) const { return p[i * NC + c]; }
+  __device__ __forceinline__ float2 operator()(int i, int c) const { return p[rpad(i * NC + c)]; }
 };
 template <int NC>
 struct ColSt {
   float2* p;
-  __device__ __forceinline__ void operator()(int i, int c, float2 v) const { p[i * NC + c] = v; }
+  __device__ __forceinline__ void operator()(int i, int c, float2 v) const { p[rpad(i * NC + c)] = v; }
 };
+__host__ __device__ constexpr int col_smem_len(int n, int nc) { return row_smem_len(n * nc); }
 
 // Stages I0 .. I1-1 of SP, ping-pong between a and b (row layout), one
 // barrier per stage.  Returns the buffer holding the result.

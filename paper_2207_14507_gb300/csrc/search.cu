@@ -133,16 +133,17 @@ __global__ void __launch_bounds__(512) k_row_forward(PassArgs a, const float* __
   const int y0 = 2 * pair, y1 = y0 + 1;
   if (active) {
     if constexpr (WARP) {
-      const WorkItem it = a.items[a.item0 + slot];
-      const size_t base = (size_t)it.frame * H * W;
+      const WorkItem it = item_of(a, slot);
+      size_t base;
+      const void* Rf = frame_of(a, it.frame, &base);
       const float cx = 0.5f * (float)(W - 1), cy = 0.5f * (float)(H - 1);
       const float dy0 = (float)y0 - cy, dy1 = (float)y1 - cy;
       const float bx0 = fmaf(it.a12, dy0, cx), by0 = fmaf(it.a22, dy0, cy);
       const float bx1 = fmaf(it.a12, dy1, cx), by1 = fmaf(it.a22, dy1, cy);
       for (int x = t; x < W; x += T) {
         const float dx = (float)x - cx;
-        const float v0 = bilinear<DT>(a.resid, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-        const float v1 = bilinear<DT>(a.resid, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+        const float v0 = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+        const float v1 = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
         buf[rpad(x)] = make_float2(v0, v1);
       }
     } else {
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(512) k_col(PassArgs a, int mode, float2* __res
     return;
   }
   if (mode == 0 || mode == 2) {
-    const WorkItem it = a.items[a.item0 + slot];
+    const WorkItem it = item_of(a, slot);
     const FpDesc fp = a.fps[it.fp];
     for (int e = tid; e < n; e += T) {
       const int i = e >> lg, col = c0 + (e & (NC - 1));
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(512) k_finalize(PassArgs a) {
   const int T = blockDim.x, t = threadIdx.x;
   const int H = a.H, W = a.W, Wh = W >> 1;
   const int slot = blockIdx.x;
-  const WorkItem it = a.items[a.item0 + slot];
+  const WorkItem it = item_of(a, slot);
   const RowStat* st = a.stats + (size_t)slot * H;
   const float2* Z = a.spec + (size_t)slot * H * Wh;
   float2* const bufA = smem;
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(512) k_finalize(PassArgs a) {
     r.cand = it.cand;
     r.group = it.group;
     r.pad = 0;
-    a.results[a.item0 + slot] = r;
+    *result_of(a, slot) = r;
   }
 }
 

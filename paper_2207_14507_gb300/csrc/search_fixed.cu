@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
   const float2* tw = a.tw + a.prow.tw_off;
-  const WorkItem it = a.items[a.item0 + slot];
-  const size_t base = (size_t)it.frame * H * W;
+  const WorkItem it = item_of(a, slot);
+  size_t base;
+  const void* Rf = frame_of(a, it.frame, &base);
   const int y0 = 2 * pair;
   const float cx = 0.5f * (float)(W - 1), cy = 0.5f * (float)(H - 1);
   const float dy0 = (float)y0 - cy, dy1 = dy0 + 1.f;
@@ -133,8 +134,8 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
 #pragma unroll
     for (int r = 0; r < S0::R; ++r) {
       const float dx = (float)(j + r * S0::NB) - cx;
-      v[r].x = bilinear_fx<DT>(a.resid, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-      v[r].y = bilinear_fx<DT>(a.resid, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+      v[r].x = bilinear_fx<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+      v[r].y = bilinear_fx<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
     }
     Dft<S0::R, false>::run(v);
 #pragma unroll
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
   const int slot = blockIdx.y;
   float2* Z = a.spec + (size_t)slot * H * Wh;
   const float2* tw = a.tw + a.pcol.tw_off;
-  const WorkItem wi = a.items[a.item0 + slot];
+  const WorkItem wi = item_of(a, slot);
   const FpDesc fp = a.fps[wi.fp];
 
   stage_stream<StageC<SP, 0, T, NC>, false>(t, tw, StripLd{Z, Wh, c0}, ColSt<NC>{sm});
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
       if (!stage_valid<FL>(t, k) || stage_c<FL>(t, k) != 0) continue;
       const int j = stage_j<FL>(t, k);
 #pragma unroll
-      for (int r = 0; r < FL::R; ++r) sm[(j + r * FL::NS) * NC] = V[k][r];
+      for (int r = 0; r < FL::R; ++r) sm[rpad((j + r * FL::NS) * NC)] = V[k][r];
     }
     __syncthreads();
 #pragma unroll
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
       for (int r = 0; r < FL::R; ++r) {
         const int i = j + r * FL::NS;
         const int im = i == 0 ? 0 : H - i;
-        const float2 F = V[k][r], Fm = sm[im * NC];
+        const float2 F = V[k][r], Fm = sm[rpad(im * NC)];
         const float2 S = load_spec(fp.spec, fp.dtype, (size_t)i * Wh);
         const float2 Sm = load_spec(fp.spec, fp.dtype, (size_t)im * Wh);
         const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
@@ -313,29 +314,35 @@ void allow(K k) {
   allow_max_dynamic_smem(k);
 }
 
-template <class RS, int RT, int PPB, class CS>
+template <class RS, int RT, class CS>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   template <int NC, int CT>
   static FixedCol col() {
     allow(k_col_fx<CS, NC, CT>);
-    return FixedCol{NC, CT, (size_t)H * NC * sizeof(float2), (void*)k_col_fx<CS, NC, CT>};
+    return FixedCol{NC, CT, (size_t)col_smem_len(H, NC) * sizeof(float2), (void*)k_col_fx<CS, NC, CT>};
   }
-  static FixedShape make(std::vector<FixedCol> cols) {
-    FixedShape s{};
-    s.W = W;
-    s.H = H;
-    s.row_threads = RT;
-    s.ppb = PPB;
-    s.row_smem = row_fx_smem<W>(PPB);
-    s.row_fwd[kF32] = (void*)k_row_forward_fx<kF32, RS, RT, PPB>;
-    s.row_fwd[kF16] = (void*)k_row_forward_fx<kF16, RS, RT, PPB>;
-    s.row_fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
-    s.row_inv = (void*)k_row_inverse_fx<RS, RT, PPB>;
+  template <int PPB>
+  static FixedRow row() {
+    FixedRow r{};
+    r.ppb = PPB;
+    r.threads = RT;
+    r.smem = row_fx_smem<W>(PPB);
+    r.fwd[kF32] = (void*)k_row_forward_fx<kF32, RS, RT, PPB>;
+    r.fwd[kF16] = (void*)k_row_forward_fx<kF16, RS, RT, PPB>;
+    r.fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
+    r.inv = (void*)k_row_inverse_fx<RS, RT, PPB>;
     allow(k_row_forward_fx<kF32, RS, RT, PPB>);
     allow(k_row_forward_fx<kF16, RS, RT, PPB>);
     allow(k_row_forward_fx<kBF16, RS, RT, PPB>);
     allow(k_row_inverse_fx<RS, RT, PPB>);
+    return r;
+  }
+  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols) {
+    FixedShape s{};
+    s.W = W;
+    s.H = H;
+    s.rows = std::move(rows);
     s.cols = std::move(cols);
     return s;
   }
@@ -344,20 +351,21 @@ struct ShapeDef {
 std::vector<FixedShape> build_registry() {
   std::vector<FixedShape> v;
   {
-    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, 2, Spec<1080, 12, 10, 9>>;
-    v.push_back(D::make({D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()}));
+    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 12, 10, 9>>;
+    v.push_back(D::make({D::row<2>(), D::row<1>()},
+                        {D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()}));
   }
   {
-    using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, 2, Spec<720, 10, 9, 8>>;
-    v.push_back(D::make({D::col<4, 384>(), D::col<8, 384>(), D::col<16, 736>()}));
+    using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 10, 9, 8>>;
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<8, 384>(), D::col<16, 736>()}));
   }
   {
-    using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, 2, Spec<2160, 15, 12, 12>>;
-    v.push_back(D::make({D::col<4, 384>(), D::col<4, 736>(), D::col<8, 736>()}));
+    using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<4, 736>(), D::col<8, 736>()}));
   }
   {
-    using D = ShapeDef<Spec<256, 16, 16>, 32, 4, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::col<8, 128>(), D::col<16, 256>()}));
+    using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
+    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<8, 128>(), D::col<16, 256>()}));
   }
   cudaGetLastError();
   return v;
@@ -374,14 +382,20 @@ const FixedShape* find_fixed(int H, int W) {
   return nullptr;
 }
 
+bool fixed_supports(const FixedShape& fs, int H, int ppb) {
+  const FixedRow& r = fs.row_for(ppb);
+  return (H / 2) % r.ppb == 0;
+}
+
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc) {
   const FixedCol& fc = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
+  const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};
   {
     ProfScope ps(lc, kKindRowForward, s);
-    dim3 g((a.H / 2) / fs.ppb, a.nitems), b(fs.row_threads * fs.ppb);
-    PRNU_CUDA_TRY(cudaLaunchKernel(fs.row_fwd[a.rdtype], g, b, args, fs.row_smem, s));
+    dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads * fr.ppb);
+    PRNU_CUDA_TRY(cudaLaunchKernel(fr.fwd[a.rdtype], g, b, args, fr.smem, s));
   }
   {
     ProfScope ps(lc, kKindColumn, s);
@@ -390,8 +404,8 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   }
   {
     ProfScope ps(lc, kKindRowInverse, s);
-    dim3 g((a.H / 2) / fs.ppb, a.nitems), b(fs.row_threads * fs.ppb);
-    PRNU_CUDA_TRY(cudaLaunchKernel(fs.row_inv, g, b, args, fs.row_smem, s));
+    dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads * fr.ppb);
+    PRNU_CUDA_TRY(cudaLaunchKernel(fr.inv, g, b, args, fr.smem, s));
   }
   lc.n += 3;
 }

@@ -14,17 +14,32 @@ struct FixedCol {
   void* fn;
 };
 
+// one instantiated pair of row kernels: row pairs per block, threads per pair
+struct FixedRow {
+  int ppb;
+  int threads;
+  size_t smem;
+  void* fwd[3];              // by residual storage type
+  void* inv;
+};
+
 struct FixedShape {
   int W, H;
-  int row_threads, ppb;
-  size_t row_smem;
-  void* row_fwd[3];          // by residual storage type
-  void* row_inv;
+  std::vector<FixedRow> rows;
   std::vector<FixedCol> cols;
+  // the row kernels with `ppb` pairs per block, else the first variant
+  const FixedRow& row_for(int ppb) const {
+    for (auto& r : rows)
+      if (r.ppb == ppb) return r;
+    return rows.front();
+  }
 };
 
 // The instantiated kernels for frames of H x W, or nullptr.
 const FixedShape* find_fixed(int H, int W);
+
+// whether the row kernels chosen for `ppb` pairs per block tile H/2 row pairs exactly
+bool fixed_supports(const FixedShape& fs, int H, int ppb);
 
 // row forward, column pass and row inverse of one wave (a.nitems candidates)
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc);

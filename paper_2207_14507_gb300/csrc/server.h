@@ -11,6 +11,7 @@ class Server {
   int submit(const prnu_query* q, uint64_t* qid);
   int poll(uint64_t qid, prnu_result* out, int64_t timeout_us);
   void stats(prnu_server_stats* out);
+  bool latency(uint64_t qid, double* queued_ms, double* total_ms);
 
  private:
   struct Impl;

@@ -262,12 +262,13 @@ def test_fixed_plan_kernels_match_generic_and_oracle(ctx, prnu, H, W, nvar):
     try:
         ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 4, -1)
         res_g, got_g = _gpu_search(ctx, prnu, wl, windows=win)
-        for v in range(nvar):
-            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 4, v)
-            res_f, got_f = _gpu_search(ctx, prnu, wl, windows=win)
-            _assert_all_close(got_f, got_g, 1e-5)
-            assert res_f[0, 0]["cand_idx"] == res_g[0, 0]["cand_idx"]
-            assert (res_f[0, 0]["dy"], res_f[0, 0]["dx"]) == (res_g[0, 0]["dy"], res_g[0, 0]["dx"])
+        for ppb in ((1, 2, 4) if H == 256 else (1, 2)):
+            for v in range(nvar):
+                ctx.prnu_set_tuning(H, W, t0["col_width"], ppb, 4, v)
+                res_f, got_f = _gpu_search(ctx, prnu, wl, windows=win)
+                _assert_all_close(got_f, got_g, 1e-5)
+                assert res_f[0, 0]["cand_idx"] == res_g[0, 0]["cand_idx"]
+                assert (res_f[0, 0]["dy"], res_f[0, 0]["dx"]) == (res_g[0, 0]["dy"], res_g[0, 0]["dx"])
     finally:
         ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"])
     R = oracle.prnu_residual(wl.frames[0])[0]
