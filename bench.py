@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-extras", action="store_true", help="skip the naive-path and CPU-oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", choices=["plain", "batched", "precision", "serving"], default="plain",
+                    help="plain = the 1080p metric line; the others print their own JSON record")
+    ap.add_argument("--queries", type=int, default=16, help="serving: queries per run")
     ap.add_argument("--autotune-ms", type=float, default=5000.0,
                     help="time budget of the library autotuner run before the warm-up (0 = defaults)")
     return ap.parse_args()
@@ -374,10 +377,223 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- other workloads
+
+def _timed_steps(step, steps, warmup, dev):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched(args):
+    """Config 3: 256 full-HD frames in one call, +-k warm-start windows
+    (k uniform in 2..10), FP32; plain per-candidate path on a sample of the
+    same inputs for the speedup."""
+    import torch
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    wl = synth.make_workload(3, F=args.frames if args.frames != 30 else 256)
+    F, H, W = wl.frames.shape
+    win = wl.windows
+    ncand = int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in win))
+    ctx = prnu.Context(0)
+    tuning = ctx.prnu_autotune(H, W, prnu.PRNU_F32, budget_ms=args.autotune_ms) if args.autotune_ms > 0 else None
+    frames_d = torch.from_numpy(wl.frames).to(dev)
+    K_d = torch.from_numpy(wl.fingerprints[0]).to(dev)
+    R = torch.empty((F, H, W), device=dev)
+    out_d = torch.empty((F, 32), dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.prnu_residual(frames_d, R)
+        h = ctx.prnu_fingerprint_term(K_d)
+        ctx.eis_grid_search(R, [h], wl.grid, windows=win, out=out_d)
+        ctx.prnu_fingerprint_release(h)
+
+    ctx.prnu_profile_begin()
+    ms = _timed_steps(step, args.steps, args.warmup, dev)
+    prof = ctx.prnu_profile_end()
+    value = ncand / (ms / 1e3)
+    # the plain per-candidate path on the first 4 frames' windows (same inputs)
+    h = ctx.prnu_fingerprint_term(K_d)
+    sub = slice(0, 4)
+    nsub = int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in win[sub]))
+    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub], naive=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub], naive=True)
+    torch.cuda.synchronize(dev)
+    naive = nsub / (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub])
+    torch.cuda.synchronize(dev)
+    fused_sub = nsub / (time.perf_counter() - t0)
+    ctx.prnu_fingerprint_release(h)
+    peak, kind = hbm_peak()
+    pb = path_bytes(H, W, 4, 8)
+    print(json.dumps({
+        "workload": "batched-1080p (config 3)", "metric": "candidates/s", "value": round(value, 1),
+        "frames": F, "candidates_per_step": ncand, "window_sizes": [int(win[1:, 1].min()), int(win[1:, 1].max())],
+        "ms_per_step": round(ms, 2), "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "path_roofline_frac": round(pb * value / 1e9 / peak, 4), "peak": f"{peak} GB/s {kind}",
+        "naive_baseline": {"value": round(naive, 1), "speedup": round(value / naive, 2),
+                           "sample": f"first 4 frames' windows ({nsub} candidates), one call each way",
+                           "fused_same_sample": round(fused_sub, 1)},
+        "tuning": tuning, "kernels": {k: round(v["total_ms"] / args.steps, 2) for k, v in prof.items()},
+    }), flush=True)
+    ctx.close()
+
+
+def run_precision(args):
+    """Config 4: 32 frames of 3840x2160, full 41x41 grid, half of the frames
+    from an independent fingerprint; FP16 and BF16 residual storage with an
+    FP16 fingerprint spectrum (FP32 arithmetic), and FP32 for comparison."""
+    import torch
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    wl = synth.make_workload(4, F=args.frames if args.frames != 30 else 32)
+    F, H, W = wl.frames.shape
+    ncand = F * wl.grid.size
+    ctx = prnu.Context(0)
+    frames_d = torch.from_numpy(wl.frames).to(dev)
+    K_d = torch.from_numpy(wl.fingerprints[0]).to(dev)
+    peak, kind = hbm_peak()
+    legs = {}
+    for name, tdt, fpd, s_in, s_k, flags in (
+            ("f16", torch.float16, prnu.PRNU_F16, 2, 4, prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE),
+            ("bf16", torch.bfloat16, prnu.PRNU_F16, 2, 4, prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE),
+            ("f32", torch.float32, prnu.PRNU_F32, 4, 8, prnu.PRNU_WEIGHT_BY_INTENSITY)):
+        tuning = ctx.prnu_autotune(H, W, fpd, budget_ms=args.autotune_ms) if args.autotune_ms > 0 else None
+        R = torch.empty((F, H, W), dtype=tdt, device=dev)
+        scale = torch.empty(F, device=dev)
+        res = {}
+
+        def step():
+            ctx.prnu_residual(frames_d, R, scale=scale, flags=flags)
+            h = ctx.prnu_fingerprint_term(K_d, fpd)
+            res["r"] = ctx.eis_grid_search(R, [h], wl.grid, scale=scale)
+            ctx.prnu_fingerprint_release(h)
+
+        ctx.prnu_profile_begin()
+        ms = _timed_steps(step, args.steps, args.warmup, dev)
+        prof = ctx.prnu_profile_end()
+        value = ncand / (ms / 1e3)
+        pce = res["r"]["pce"][:, 0]
+        legs[name] = {"value": round(value, 1), "ms_per_step": round(ms, 1),
+                      "path_roofline_frac": round(path_bytes(H, W, s_in, s_k) * value / 1e9 / peak, 4),
+                      "matched_min_pce": float(pce[wl.frame_fp == 0].min()),
+                      "unmatched_max_pce": float(pce[wl.frame_fp == 1].max()),
+                      "decisions_at_60": [bool(p >= 60) for p in pce], "tuning": tuning,
+                      "kernels": {k: round(v["total_ms"] / args.steps, 1) for k, v in prof.items()}}
+    print(json.dumps({"workload": "precision-4k (config 4)", "metric": "candidates/s", "frames": F,
+                      "candidates_per_step": ncand, "steps": args.steps, "warmup": args.warmup,
+                      "peak": f"{peak} GB/s {kind}", "legs": legs}), flush=True)
+    ctx.close()
+
+
+def run_serving(args):
+    """Config 5: Poisson query stream (720p/1080p/4K, 8-64 frames, 1-16
+    fingerprints, one matching with probability 0.5, +-k windows, FP16
+    storage, 120 GB admission budget).  Three runs: all queries at once
+    (capacity), a Poisson stream at 70% of the measured capacity, and the
+    nominal 20 queries/s (overloaded)."""
+    import threading
+    import torch
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    n = args.queries
+    queries, banks = synth.make_query_stream(3 * n, rate_hz=20.0, pool_frames=8, match_sources=1)
+    ctx = prnu.Context(0, hbm_budget_bytes=120 << 30)
+    tunings = {}
+    for (H, W) in banks:
+        tunings[f"{H}x{W}"] = ctx.prnu_autotune(H, W, prnu.PRNU_F16, budget_ms=args.autotune_ms) \
+            if args.autotune_ms > 0 else None
+    handles = {k: [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(dev), prnu.PRNU_F16) for K in bank]
+               for k, bank in banks.items()}
+    frames = [torch.from_numpy(q.frames).to(dev) for q in queries]
+    torch.cuda.synchronize(dev)
+    ncand = [len(q.fp_ids) * int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in q.windows)) for q in queries]
+
+    def submit(q, fr):
+        hs = [handles[(q.H, q.W)][i] for i in q.fp_ids]
+        return ctx.query_submit(fr, hs, synth.GRID_FULL, windows=q.windows, dtype=prnu.PRNU_F16,
+                                flags=prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE)
+
+    def run(idx, arrivals):
+        ids = {}
+        done = []
+
+        def poller():
+            for i in idx:
+                while i not in ids:
+                    time.sleep(0.0005)
+                ctx.query_poll(ids[i], queries[i].frames.shape[0], len(queries[i].fp_ids), timeout_us=-1)
+                done.append(i)
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for i, t in zip(idx, arrivals):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            ids[i] = submit(queries[i], frames[i])
+        th.join()
+        wall = time.perf_counter() - t0
+        lat = np.array([ctx.query_latency(ids[i])["total_ms"] for i in idx])
+        return wall, lat
+
+    # capacity: everything at once
+    idx0 = list(range(0, n))
+    wall, lat = run(idx0, [0.0] * n)
+    cap_q = n / wall
+    cap_c = sum(ncand[i] for i in idx0) / wall
+    # Poisson at 70% of capacity, and at the nominal 20 queries/s
+    rng = np.random.default_rng(5)
+    out = {}
+    for name, rate, idx in (("70pct_capacity", 0.7 * cap_q, list(range(n, 2 * n))),
+                            ("20qps_overloaded", 20.0, list(range(2 * n, 3 * n)))):
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=len(idx)))
+        w2, l2 = run(idx, list(arr))
+        out[name] = {"rate_qps": round(rate, 3), "queries": len(idx), "wall_s": round(w2, 2),
+                     "throughput_qps": round(len(idx) / w2, 3),
+                     "candidates_per_s": round(sum(ncand[i] for i in idx) / w2, 1),
+                     "p50_ms": round(float(np.percentile(l2, 50)), 1), "p99_ms": round(float(np.percentile(l2, 99)), 1),
+                     "overloaded": bool(rate > cap_q)}
+    st = ctx.prnu_server_stats_get()
+    print(json.dumps({"workload": "serving (config 5)", "metric": "served p50/p99 query latency",
+                      "capacity": {"queries_per_s": round(cap_q, 3), "candidates_per_s": round(cap_c, 1),
+                                   "queries": n, "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                                   "p99_ms": round(float(np.percentile(lat, 99)), 1)},
+                      "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
+                      "budget_gb": 120, "admitted_bytes_peak": st["admitted_bytes_peak"],
+                      "server_launches": st["server_launches"], "dtype": "f16", "tuning": tunings}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "precision":
+        run_precision(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -246,6 +246,9 @@ typedef struct {
     int wave;             /* candidates in flight, >= 1 */
     int variant;          /* compile-time-planned column kernel variant for this size
                              (0.. n-1), or -1 for the generic runtime-plan kernels */
+    int persistent;       /* 1: sizes with compile-time-planned kernels run a whole call
+                             as one persistent launch that schedules every phase of every
+                             candidate as tasks (spectra stay in L2); 0: waves */
 } prnu_tuning;
 
 /* Read / override the configuration used for frames of H x W. */

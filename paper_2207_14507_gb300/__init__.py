@@ -54,7 +54,8 @@ class prnu_server_stats(C.Structure):
 
 
 class prnu_tuning(C.Structure):
-    _fields_ = [("col_width", C.c_int), ("pairs_per_block", C.c_int), ("wave", C.c_int), ("variant", C.c_int)]
+    _fields_ = [("col_width", C.c_int), ("pairs_per_block", C.c_int), ("wave", C.c_int), ("variant", C.c_int),
+                ("persistent", C.c_int)]
 
 
 class prnu_kernel_stat(C.Structure):
@@ -288,13 +289,13 @@ class Context:
     def prnu_get_tuning(self, H, W) -> dict:
         t = prnu_tuning()
         _check(lib().prnu_get_tuning(self.h, H, W, C.byref(t)), "prnu_get_tuning")
-        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant)
+        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant, persistent=t.persistent)
 
-    def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave, variant=0):
-        t = prnu_tuning(col_width, pairs_per_block, wave, variant)
+    def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave, variant=0, persistent=0):
+        t = prnu_tuning(col_width, pairs_per_block, wave, variant, persistent)
         _check(lib().prnu_set_tuning(self.h, H, W, C.byref(t)), "prnu_set_tuning")
 
     def prnu_autotune(self, H, W, dtype=PRNU_F32, budget_ms=2000.0, stream=None) -> dict:
         t = prnu_tuning()
         _check(lib().prnu_autotune(self.h, H, W, dtype, budget_ms, C.byref(t), _stream(stream)), "prnu_autotune")
-        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant)
+        return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant, persistent=t.persistent)

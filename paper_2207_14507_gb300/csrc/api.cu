@@ -265,15 +265,28 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   int rowT, rowMB;
   row_launch_shape(prow, &rowT, &rowMB);
   const int wave = naive ? 1 : std::max(1, std::min(tn.wave, n));
+  const FixedShape* fs = (!naive && tn.variant >= 0) ? find_fixed(H, W) : nullptr;
+  if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
+  bool persistent = fs && tn.persistent && (H / 2) % fs->persist.ppb == 0;
+  if (persistent) {   // tickets of one launch: (n + 3) steps of 2 row phases, the column phase and a finalisation
+    const long long nrf = (H / 2) / fs->persist.ppb, ncol = (Wh + fs->persist.nc - 1) / fs->persist.nc;
+    persistent = (long long)(n + 3) * (2 * nrf + ncol + 1) < (long long)INT_MAX;
+  }
+  const int slots = persistent ? kPersistSlots : wave;
 
+  if (*c->h_err) {   // a persistent launch of an earlier asynchronous call gave up
+    *c->h_err = 0;
+    throw Error{PRNU_EDEVICE_ABORT, "a device-side wait of an earlier call timed out; its results are invalid"};
+  }
   PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->last_done, 0));
   for (auto& f : call.fps) PRNU_CUDA_TRY(cudaStreamWaitEvent(s, f->ready, 0));
   ensure_buf(c, c->ws_items, sizeof(WorkItem) * std::max(n, 1));
   ensure_buf(c, c->ws_results, sizeof(CandResult) * std::max(n, 1));
   ensure_buf(c, c->ws_groups, sizeof(int) * (ngroups + 1));
   ensure_buf(c, c->ws_fpdesc, sizeof(FpDesc) * std::max<size_t>(1, call.fps.size()));
-  ensure_buf(c, c->ws_spec, (size_t)wave * H * Wh * sizeof(float2));
-  ensure_buf(c, c->ws_stats, (size_t)wave * H * sizeof(RowStat));
+  ensure_buf(c, c->ws_spec, (size_t)slots * H * Wh * sizeof(float2));
+  ensure_buf(c, c->ws_stats, (size_t)slots * H * sizeof(RowStat));
+  if (persistent) ensure_buf(c, c->ws_persist, sizeof(int) * (2 + 4 * (size_t)n));
   std::vector<FpDesc> fd = fp_descs(call);
   Stager st(c);
   st.add(c->ws_items.p, call.items.data(), call.items.size());
@@ -299,9 +312,16 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.col_log2 = tn.col_log2;
   a.row_threads = rowT;
 
-  if (!naive) {
-    const FixedShape* fs = tn.variant >= 0 ? find_fixed(H, W) : nullptr;
-    if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
+  if (persistent) {
+    int* st0 = reinterpret_cast<int*>(c->ws_persist.p);
+    PersistArgs p{st0, st0 + 1, st0 + 2, st0 + 2 + n, st0 + 2 + 2 * (size_t)n, st0 + 2 + 3 * (size_t)n, n,
+                  kPersistSlots};
+    PRNU_CUDA_TRY(cudaMemsetAsync(st0, 0, sizeof(int) * (2 + 4 * (size_t)n), s));
+    a.item0 = 0;
+    a.nitems = n;
+    launch_persistent(a, p, *fs, c->sm_count, s, c->launches);
+    PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, p.error, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else if (!naive) {
     for (int i0 = 0; i0 < n; i0 += wave) {
       a.item0 = i0;
       a.nitems = std::min(wave, n - i0);
@@ -404,6 +424,10 @@ static int search_common(prnu_ctx* ctx, const void* d_resid, int dtype, const fl
     if (!dev_out) {
       PRNU_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(prnu_result) * (size_t)F * P, cudaMemcpyDeviceToHost, s));
       PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*ctx->h_err) {
+        *ctx->h_err = 0;
+        throw Error{PRNU_EDEVICE_ABORT, "a device-side wait of the persistent kernel timed out"};
+      }
     }
   });
 }
@@ -451,6 +475,8 @@ int prnu_create(prnu_ctx** out, int device, size_t hbm_budget_bytes) {
     PRNU_CUDA_TRY(cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
     PRNU_CUDA_TRY(cudaEventRecord(c->last_done, 0));
     PRNU_CUDA_TRY(cudaEventRecord(c->stage_free, 0));
+    PRNU_CUDA_TRY(cudaHostAlloc((void**)&c->h_err, sizeof(int), cudaHostAllocDefault));
+    *c->h_err = 0;
     set_kernel_attributes();
     *out = c.release();
   });
@@ -472,10 +498,11 @@ int prnu_destroy(prnu_ctx* ctx) {
     }
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
-                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid})
+                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
     cudaEventDestroy(ctx->last_done);
     cudaEventDestroy(ctx->stage_free);
     delete ctx;
@@ -732,6 +759,7 @@ int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
     out->pairs_per_block = t.ppb;
     out->wave = t.wave;
     out->variant = t.variant;
+    out->persistent = t.persistent;
   });
 }
 
@@ -756,7 +784,8 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
     const FixedShape* fs = find_fixed(H, W);
     PRNU_CHECK_ARG(cfg->variant >= -1 && cfg->variant < (fs ? (int)fs->cols.size() : 0),
                    "variant out of range for this frame size (-1 = generic kernels)");
-    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant};
+    PRNU_CHECK_ARG(cfg->persistent == 0 || cfg->persistent == 1, "persistent must be 0 or 1");
+    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant, cfg->persistent};
   });
 }
 

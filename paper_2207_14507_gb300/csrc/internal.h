@@ -155,6 +155,7 @@ struct Tuning {
   int ppb = 2;        // generic kernels: row pairs per row block
   int wave = 64;      // candidates in flight
   int variant = 0;    // compile-time-planned column variant; -1 = generic kernels only
+  int persistent = 0; // compile-time-planned shapes: one persistent launch per call instead of waves
 };
 
 }  // namespace prnu
@@ -172,8 +173,10 @@ struct prnu_ctx {
   prnu::LaunchCounter launches;
   cudaEvent_t last_done = nullptr;
   // call workspace
-  prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid;
+  prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
+      ws_persist;
   size_t tw_bytes = 0;
+  int* h_err = nullptr;           // pinned: error flag of the last persistent launch
   std::vector<char> h_stage;      // staging for host->device descriptors
   char* h_pinned = nullptr;
   size_t h_pinned_bytes = 0;

@@ -1,0 +1,200 @@
+// search_common.cuh -- device helpers shared by the wave kernels (search.cu),
+// the compile-time-planned kernels and the persistent kernel (search_fixed.cu).
+#pragma once
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace prnu {
+
+// ---------------------------------------------------------------- helpers
+
+struct WarpRed {
+  float ma;
+  int ia;
+  float mb;
+  int ib;
+  double sa;
+  double sb;
+};
+
+__device__ __forceinline__ void better_f(float& v, int& i, float v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+__device__ __forceinline__ void better_d(double& v, int& i, double v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+__device__ __forceinline__ void warp_maxarg(float& v, int& i) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    better_f(v, i, v2, i2);
+  }
+}
+__device__ __forceinline__ void warp_maxarg_d(double& v, int& i) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    better_d(v, i, v2, i2);
+  }
+}
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+// cyclic distance between indices a and b modulo n
+__device__ __forceinline__ int cdist(int a, int b, int n) {
+  int d = a - b;
+  if (d < 0) d = -d;
+  return d < n - d ? d : n - d;
+}
+
+constexpr int kHalfWindow = 5;      // Eq. 3: 11 x 11 exclusion
+constexpr int kWindowCount = 121;
+
+template <int DT>
+__device__ __forceinline__ float bilinear(const void* R, size_t base, int H, int W, float qx, float qy) {
+  const float fx0 = floorf(qx), fy0 = floorf(qy);
+  const float fx = qx - fx0, fy = qy - fy0;
+  const int x0 = (int)fx0, y0 = (int)fy0;
+  const bool xi0 = (unsigned)x0 < (unsigned)W, xi1 = (unsigned)(x0 + 1) < (unsigned)W;
+  const bool yi0 = (unsigned)y0 < (unsigned)H, yi1 = (unsigned)(y0 + 1) < (unsigned)H;
+  const size_t r0 = base + (size_t)y0 * W + x0;
+  const float v00 = (yi0 && xi0) ? load_store_type<DT>(R, r0) : 0.f;
+  const float v01 = (yi0 && xi1) ? load_store_type<DT>(R, r0 + 1) : 0.f;
+  const float v10 = (yi1 && xi0) ? load_store_type<DT>(R, r0 + W) : 0.f;
+  const float v11 = (yi1 && xi1) ? load_store_type<DT>(R, r0 + W + 1) : 0.f;
+  const float gx = 1.f - fx, gy = 1.f - fy;
+  return gy * (gx * v00 + fx * v01) + fy * (gx * v10 + fx * v11);
+}
+
+// Loads of data that other blocks of the same launch may have written (the
+// persistent kernel reuses workspace slots): cached in L2 only, never in the
+// non-coherent L1.
+__device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ RowStat ld_l2(const RowStat* p) {
+  RowStat r;
+  const float2 a = __ldcg(reinterpret_cast<const float2*>(p));
+  r.max = a.x;
+  r.arg = __float_as_int(a.y);
+  r.sumsq = __ldcg(&p->sumsq);
+  return r;
+}
+
+// Full spectrum z = G_a + i G_b of two packed half-spectrum rows (the inverse
+// of the split done after the forward row FFT).
+__device__ __forceinline__ void build_full_row(float2* buf, const float2* __restrict__ pa,
+                                               const float2* __restrict__ pb, int W, int t, int T) {
+  const int Wh = W >> 1;
+  for (int k = t; k < Wh; k += T) {
+    const float2 A = pa[k], B = pb[k];
+    if (k == 0) {
+      buf[rpad(0)] = make_float2(A.x, B.x);
+      buf[rpad(Wh)] = make_float2(A.y, B.y);
+    } else {
+      buf[rpad(k)] = make_float2(A.x - B.y, A.y + B.x);
+      buf[rpad(W - k)] = make_float2(A.x + B.y, B.x - A.y);
+    }
+  }
+}
+
+__host__ __device__ inline size_t row_smem_bytes(int W, int ppb) {
+  return (size_t)ppb * 2 * row_smem_len(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
+}
+
+// Peak, energy outside the cyclic 11x11 window and PCE (Eq. 3) of candidate
+// `is` whose row statistics and spectrum sit in workspace slot `ws`; all
+// threads of the block take part (any block size that is a multiple of 32).
+static __device__ __noinline__ void finalize_body(const PassArgs& a, int is, int ws, float2* smem) {
+  __shared__ int s_py, s_px;
+  __shared__ float s_peak;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int H = a.H, W = a.W, Wh = W >> 1;
+  const WorkItem it = item_of(a, is);
+  const RowStat* st = a.stats + (size_t)ws * H;
+  const float2* Z = a.spec + (size_t)ws * H * Wh;
+  float2* const bufA = smem;
+  float2* const bufB = smem + row_smem_len(W);
+  WarpRed* red = reinterpret_cast<WarpRed*>(smem + 2 * row_smem_len(W));
+  const int nw = T >> 5, w = t >> 5;
+
+  float bv = -INFINITY;
+  int bi = INT_MAX;
+  for (int y = t; y < H; y += T) {
+    const RowStat r = st[y];
+    better_f(bv, bi, r.max, y * W + r.arg);
+  }
+  warp_maxarg(bv, bi);
+  if ((t & 31) == 0) { red[w].ma = bv; red[w].ia = bi; }
+  __syncthreads();
+  if (t == 0) {
+    for (int k = 1; k < nw; ++k) better_f(bv, bi, red[k].ma, red[k].ia);
+    if (bi == INT_MAX) bi = 0;
+    s_peak = bv;
+    s_py = bi / W;
+    s_px = bi - (bi / W) * W;
+  }
+  __syncthreads();
+  const int py = s_py, px = s_px;
+  double e = 0.0;
+  for (int y = t; y < H; y += T)
+    if (cdist(y, py, H) > kHalfWindow) e += st[y].sumsq;
+  int prev = -1;
+  for (int d = -kHalfWindow; d <= kHalfWindow; ++d) {
+    const int r = (py + d + H) % H;
+    const int p = r >> 1;
+    if (p == prev) continue;
+    prev = p;
+    build_full_row(bufA, Z + (size_t)(2 * p) * Wh, Z + (size_t)(2 * p + 1) * Wh, W, t, T);
+    __syncthreads();
+    const float2* buf = fft_row<true>(bufA, bufB, a.prow, a.tw, t, T);
+    for (int q = 0; q < 2; ++q) {
+      if (cdist(2 * p + q, py, H) > kHalfWindow) continue;
+      for (int x = t; x < W; x += T) {
+        if (cdist(x, px, W) <= kHalfWindow) continue;
+        const float2 v = buf[rpad(x)];
+        const double c = q ? v.y : v.x;
+        e += c * c;
+      }
+    }
+    __syncthreads();
+  }
+  e = warp_sum(e);
+  if ((t & 31) == 0) red[w].sa = e;
+  __syncthreads();
+  if (t == 0) {
+    double etot = red[0].sa;
+    for (int k = 1; k < nw; ++k) etot += red[k].sa;
+    const double E = etot / ((double)H * (double)W - (double)kWindowCount);
+    const double pk = (double)s_peak;
+    double pce;
+    if (E > 0.0) pce = (pk < 0 ? -1.0 : 1.0) * pk * pk / E;
+    else pce = pk == 0.0 ? 0.0 : (pk < 0 ? -INFINITY : INFINITY);
+    const FpDesc fp = a.fps[it.fp];
+    double pv = pk / ((double)H * (double)W) * (double)(*fp.inv_scale);
+    if (a.scale) pv /= (double)a.scale[it.frame];
+    CandResult r;
+    r.pce = pce;
+    r.peak = (float)pv;
+    r.py = py;
+    r.px = px;
+    r.cand = it.cand;
+    r.group = it.group;
+    r.pad = 0;
+    *result_of(a, is) = r;
+  }
+}
+
+
+}  // namespace prnu

@@ -4,90 +4,73 @@
 // Same arithmetic as the generic kernels in search.cu (the same Stockham
 // stages and radix-R DFTs, the same packed half spectrum), with the plan known
 // at compile time and fewer shared-memory passes:
-//   k_row_forward_fx : stage 0 of the row FFT takes its inputs straight from
+//   row_forward_body : stage 0 of the row FFT takes its inputs straight from
 //                      the bilinear warp (no shared-memory fill);
-//   k_col_fx         : stage 0 loads the strip from global memory; the last
+//   col_body         : stage 0 loads the strip from global memory; the last
 //                      forward stage, the spectrum product and the first
 //                      inverse stage stay in registers (the inverse plan is
 //                      the forward plan reversed, so every thread already
 //                      holds its inputs); the last inverse stage stores to
 //                      global memory; stages in between run in place;
-//   k_row_inverse_fx : stage 0 rebuilds the two rows' full spectrum straight
+//   row_inverse_body : stage 0 rebuilds the two rows' full spectrum straight
 //                      from global memory; the last stage's outputs are
 //                      reduced to the row statistics from registers.
-#include <float.h>
-#include <limits.h>
+// Each body runs either as its own wave kernel (one launch per phase over a
+// wave of candidates) or inside k_persist, one launch that schedules all
+// phases of all candidates of a call as tasks (see below).
+#include <algorithm>
 
 #include "fft_fixed.cuh"
 #include "internal.h"
+#include "search_common.cuh"
 #include "search_fixed.h"
 
 namespace prnu {
 
 namespace {
 
-struct WarpRedF {
-  float ma;
-  int ia;
-  float mb;
-  int ib;
-  double sa;
-  double sb;
-};
-
-__device__ __forceinline__ void better_fx(float& v, int& i, float v2, int i2) {
-  if (v2 > v || (v2 == v && i2 < i)) {
-    v = v2;
-    i = i2;
-  }
-}
-
-template <int DT>
-__device__ __forceinline__ float bilinear_fx(const void* R, size_t base, int H, int W, float qx, float qy) {
-  const float fx0 = floorf(qx), fy0 = floorf(qy);
-  const float fx = qx - fx0, fy = qy - fy0;
-  const int x0 = (int)fx0, y0 = (int)fy0;
-  const bool xi0 = (unsigned)x0 < (unsigned)W, xi1 = (unsigned)(x0 + 1) < (unsigned)W;
-  const bool yi0 = (unsigned)y0 < (unsigned)H, yi1 = (unsigned)(y0 + 1) < (unsigned)H;
-  const size_t r0 = base + (size_t)y0 * W + x0;
-  const float v00 = (yi0 && xi0) ? load_store_type<DT>(R, r0) : 0.f;
-  const float v01 = (yi0 && xi1) ? load_store_type<DT>(R, r0 + 1) : 0.f;
-  const float v10 = (yi1 && xi0) ? load_store_type<DT>(R, r0 + W) : 0.f;
-  const float v11 = (yi1 && xi1) ? load_store_type<DT>(R, r0 + W + 1) : 0.f;
-  const float gx = 1.f - fx, gy = 1.f - fy;
-  return gy * (gx * v00 + fx * v01) + fy * (gx * v10 + fx * v11);
+// Loads of spectra: L2-only (CG) inside the persistent kernel, whose blocks
+// read what other blocks of the same launch wrote into reused slots; plain
+// (L1-cached) in the wave kernels, where the row inverse reads every packed
+// element twice (for bins k and W - k).
+template <bool CG>
+__device__ __forceinline__ float2 ld_spec(const float2* p) {
+  if constexpr (CG) return ld_l2(p);
+  else return *p;
 }
 
 // full spectrum element i of z = G_a + i G_b from two packed rows
+template <bool CG>
 struct FullRowLd {
   const float2* pa;
   const float2* pb;
   int W, Wh;
   __device__ __forceinline__ float2 operator()(int i, int) const {
     if (i == 0) {
-      const float2 A = pa[0], B = pb[0];
+      const float2 A = ld_spec<CG>(pa), B = ld_spec<CG>(pb);
       return make_float2(A.x, B.x);
     }
     if (i == Wh) {
-      const float2 A = pa[0], B = pb[0];
+      const float2 A = ld_spec<CG>(pa), B = ld_spec<CG>(pb);
       return make_float2(A.y, B.y);
     }
     if (i < Wh) {
-      const float2 A = pa[i], B = pb[i];
+      const float2 A = ld_spec<CG>(pa + i), B = ld_spec<CG>(pb + i);
       return make_float2(A.x - B.y, A.y + B.x);
     }
     const int k = W - i;
-    const float2 A = pa[k], B = pb[k];
+    const float2 A = ld_spec<CG>(pa + k), B = ld_spec<CG>(pb + k);
     return make_float2(A.x + B.y, B.x - A.y);
   }
 };
 
+template <bool CG>
 struct StripLd {
   const float2* Z;
   int Wh, c0;
   __device__ __forceinline__ float2 operator()(int i, int c) const {
     const int col = c0 + c;
-    return col < Wh ? Z[(size_t)i * Wh + col] : make_float2(0.f, 0.f);
+    return col < Wh ? ld_spec<CG>(Z + (size_t)i * Wh + col) : make_float2(0.f, 0.f);
   }
 };
 struct StripSt {
@@ -101,23 +84,23 @@ struct StripSt {
 
 template <int W>
 __host__ __device__ constexpr size_t row_fx_smem(int ppb) {
-  return (size_t)ppb * 2 * row_smem_len(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRedF);
+  return (size_t)ppb * 2 * row_smem_len(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
 }
 
 // ---------------------------------------------------------------- row forward
 
+// Row pairs bx*PPB .. bx*PPB+PPB-1 of candidate `is` (item slot), spectrum
+// written to workspace slot `ws`.  Block = PPB groups of T threads.
 template <int DT, class SP, int T, int PPB>
-__global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
+__device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int ws, int bx, float2* smem) {
   constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
-  extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x - grp * T;
   const int H = a.H;
-  const int pair = blockIdx.x * PPB + grp;
-  const int slot = blockIdx.y;
+  const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
   const float2* tw = a.tw + a.prow.tw_off;
-  const WorkItem it = item_of(a, slot);
+  const WorkItem it = item_of(a, is);
   size_t base;
   const void* Rf = frame_of(a, it.frame, &base);
   const int y0 = 2 * pair;
@@ -134,8 +117,8 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
 #pragma unroll
     for (int r = 0; r < S0::R; ++r) {
       const float dx = (float)(j + r * S0::NB) - cx;
-      v[r].x = bilinear_fx<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-      v[r].y = bilinear_fx<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+      v[r].x = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+      v[r].y = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
     }
     Dft<S0::R, false>::run(v);
 #pragma unroll
@@ -143,7 +126,7 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
   }
   __syncthreads();
   const float2* res = RowStagesPP<SP, 1, SP::S, T, false>::run(A, B, t, tw);
-  float2* o0 = a.spec + ((size_t)slot * H + y0) * Wh;
+  float2* o0 = a.spec + ((size_t)ws * H + y0) * Wh;
   float2* o1 = o0 + Wh;
   for (int k = t; k < Wh; k += T) {
     float2 P, Q;
@@ -163,21 +146,20 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
 
 // ---------------------------------------------------------------- column pass
 
-template <class SP, int NC, int T>
-__global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
+// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
+template <class SP, int NC, int T, bool CG = false>
+__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm) {
   constexpr int H = SP::N;
   using IS = typename SP::Rev;
-  extern __shared__ float2 sm[];
   const int t = threadIdx.x;
   const int Wh = a.W >> 1;
-  const int c0 = blockIdx.x * NC;
-  const int slot = blockIdx.y;
-  float2* Z = a.spec + (size_t)slot * H * Wh;
+  const int c0 = bx * NC;
+  float2* Z = a.spec + (size_t)ws * H * Wh;
   const float2* tw = a.tw + a.pcol.tw_off;
-  const WorkItem wi = item_of(a, slot);
+  const WorkItem wi = item_of(a, is);
   const FpDesc fp = a.fps[wi.fp];
 
-  stage_stream<StageC<SP, 0, T, NC>, false>(t, tw, StripLd{Z, Wh, c0}, ColSt<NC>{sm});
+  stage_stream<StageC<SP, 0, T, NC>, false>(t, tw, StripLd<CG>{Z, Wh, c0}, ColSt<NC>{sm});
   __syncthreads();
   ColStagesIP<SP, 1, SP::S - 1, T, NC, false>::run(sm, t, tw);
 
@@ -240,24 +222,23 @@ __global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
 
 // ---------------------------------------------------------------- row inverse + statistics
 
-template <class SP, int T, int PPB>
-__global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
+template <class SP, int T, int PPB, bool CG = false>
+__device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int bx, float2* smem) {
   constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
-  extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x - grp * T;
   const int H = a.H;
-  const int pair = blockIdx.x * PPB + grp;
-  const int slot = blockIdx.y;
+  const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
-  WarpRedF* red = reinterpret_cast<WarpRedF*>(smem + (size_t)PPB * 2 * L) + grp * 32;
+  WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
   const float2* tw = a.tw + a.prow.tw_off;
-  const float2* pa = a.spec + ((size_t)slot * H + 2 * pair) * Wh;
-  stage_stream<StageC<SP, 0, T>, true>(t, tw, FullRowLd{pa, pa + Wh, W, Wh}, RowSt{A});
+  const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
+  stage_stream<StageC<SP, 0, T>, true>(t, tw, FullRowLd<CG>{pa, pa + Wh, W, Wh}, RowSt{A});
   __syncthreads();
   const float2* res = RowStagesPP<SP, 1, SP::S - 1, T, true>::run(A, B, t, tw);
   using SL = StageC<SP, SP::S - 1, T>;
   static_assert(SL::NB == SL::NS, "last stage writes j + r*NS");
+  static_assert(PPB == 1 || T % 32 == 0, "row-pair groups must not share a warp (warp-level reductions)");
   float2 V[SL::IT][SL::R];
   stage_load<SL>(t, RowLd{res}, V);
   stage_compute<SL, true>(t, tw, V);
@@ -272,38 +253,263 @@ __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
     for (int r = 0; r < SL::R; ++r) {
       const int x = j + r * SL::NS;
       const float2 v = V[k][r];
-      better_fx(ma, ia, v.x, x);
-      better_fx(mb, ib, v.y, x);
+      better_f(ma, ia, v.x, x);
+      better_f(mb, ib, v.y, x);
       sa = fmaf(v.x, v.x, sa);
       sb = fmaf(v.y, v.y, sb);
     }
   }
   double da = sa, db = sb;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    float m2 = __shfl_xor_sync(0xffffffffu, ma, o);
-    int i2 = __shfl_xor_sync(0xffffffffu, ia, o);
-    better_fx(ma, ia, m2, i2);
-    m2 = __shfl_xor_sync(0xffffffffu, mb, o);
-    i2 = __shfl_xor_sync(0xffffffffu, ib, o);
-    better_fx(mb, ib, m2, i2);
-    da += __shfl_xor_sync(0xffffffffu, da, o);
-    db += __shfl_xor_sync(0xffffffffu, db, o);
-  }
+  warp_maxarg(ma, ia);
+  warp_maxarg(mb, ib);
+  da = warp_sum(da);
+  db = warp_sum(db);
   const int w = t >> 5;
-  if ((t & 31) == 0) red[w] = WarpRedF{ma, ia, mb, ib, da, db};
+  if ((t & 31) == 0) red[w] = WarpRed{ma, ia, mb, ib, da, db};
   __syncthreads();
   if (t == 0) {
     constexpr int NW = (T + 31) / 32;
     for (int k = 1; k < NW; ++k) {
-      better_fx(ma, ia, red[k].ma, red[k].ia);
-      better_fx(mb, ib, red[k].mb, red[k].ib);
+      better_f(ma, ia, red[k].ma, red[k].ia);
+      better_f(mb, ib, red[k].mb, red[k].ib);
       da += red[k].sa;
       db += red[k].sb;
     }
-    RowStat* st = a.stats + (size_t)slot * H + 2 * pair;
+    RowStat* st = a.stats + (size_t)ws * H + 2 * pair;
     st[0] = RowStat{ma, ia, da};
     st[1] = RowStat{mb, ib, db};
+  }
+}
+
+// ---------------------------------------------------------------- wave kernels
+
+template <int DT, class SP, int T, int PPB>
+__global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
+  extern __shared__ float2 smem[];
+  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem);
+}
+
+template <class SP, int NC, int T>
+__global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
+  extern __shared__ float2 smem[];
+  col_body<SP, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem);
+}
+
+template <class SP, int T, int PPB>
+__global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
+  extern __shared__ float2 smem[];
+  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, smem);
+}
+
+// ---------------------------------------------------------------- persistent kernel
+
+// Separate (not inlined) task functions: each keeps its own register
+// allocation instead of the kernel holding the union of all three.
+template <int DT, class SP, int T, int PPB>
+__device__ __noinline__ void row_forward_task(const PassArgs& a, int is, int ws, int bx, float2* smem) {
+  row_forward_body<DT, SP, T, PPB>(a, is, ws, bx, smem);
+}
+template <class SP, int NC, int T>
+__device__ __noinline__ void col_task(const PassArgs& a, int is, int ws, int bx, float2* smem) {
+  col_body<SP, NC, T, true>(a, is, ws, bx, smem);
+}
+template <class SP, int T, int PPB>
+__device__ __noinline__ void row_inverse_task(const PassArgs& a, int ws, int bx, float2* smem) {
+  row_inverse_body<SP, T, PPB, true>(a, ws, bx, smem);
+}
+
+// finalize_body with the window's rows recomputed by the compile-time-planned
+// inverse row FFT (one row pair per thread group, PPB pairs per round).
+template <class SP, int T, int PPB>
+__device__ __noinline__ void finalize_task(const PassArgs& a, int is, int ws, float2* smem) {
+  constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W), TB = T * PPB;
+  __shared__ int s_py, s_px, s_np;
+  __shared__ float s_peak;
+  __shared__ int s_pairs[2 * kHalfWindow + 1];
+  const int t = threadIdx.x, grp = t / T, tg = t - grp * T;
+  const int H = a.H;
+  const WorkItem it = item_of(a, is);
+  const RowStat* st = a.stats + (size_t)ws * H;
+  const float2* Z = a.spec + (size_t)ws * H * Wh;
+  const float2* tw = a.tw + a.prow.tw_off;
+  WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * 2 * L);
+  constexpr int NW = TB / 32;
+  const int w = t >> 5;
+
+  float bv = -INFINITY;
+  int bi = INT_MAX;
+  for (int y = t; y < H; y += TB) {
+    const RowStat r = ld_l2(st + y);
+    better_f(bv, bi, r.max, y * W + r.arg);
+  }
+  warp_maxarg(bv, bi);
+  if ((t & 31) == 0) {
+    red[w].ma = bv;
+    red[w].ia = bi;
+  }
+  __syncthreads();
+  if (t == 0) {
+    for (int k = 1; k < NW; ++k) better_f(bv, bi, red[k].ma, red[k].ia);
+    if (bi == INT_MAX) bi = 0;
+    s_peak = bv;
+    s_py = bi / W;
+    s_px = bi - (bi / W) * W;
+    int np = 0, prev = -1;
+    for (int d = -kHalfWindow; d <= kHalfWindow; ++d) {
+      const int p = ((s_py + d + H) % H) >> 1;
+      if (p != prev) s_pairs[np++] = p;
+      prev = p;
+    }
+    s_np = np;
+  }
+  __syncthreads();
+  const int py = s_py, px = s_px, np = s_np;
+  double e = 0.0;
+  for (int y = t; y < H; y += TB)
+    if (cdist(y, py, H) > kHalfWindow) e += ld_l2(st + y).sumsq;
+  using SL = StageC<SP, SP::S - 1, T>;
+  for (int r0 = 0; r0 < np; r0 += PPB) {
+    const int k = r0 + grp;
+    const bool act = k < np;
+    const int p = act ? s_pairs[k] : 0;
+    float2* A = smem + (size_t)grp * 2 * L;
+    float2* B = A + L;
+    const float2* pa = Z + (size_t)(2 * p) * Wh;
+    stage_stream<StageC<SP, 0, T>, true>(tg, tw, FullRowLd<true>{pa, pa + Wh, W, Wh}, RowSt{A});
+    __syncthreads();
+    const float2* res = RowStagesPP<SP, 1, SP::S - 1, T, true>::run(A, B, tg, tw);
+    float2 V[SL::IT][SL::R];
+    stage_load<SL>(tg, RowLd{res}, V);
+    stage_compute<SL, true>(tg, tw, V);
+    if (act) {
+#pragma unroll
+      for (int kk = 0; kk < SL::IT; ++kk) {
+        if (!stage_valid<SL>(tg, kk)) continue;
+        const int j = stage_j<SL>(tg, kk);
+#pragma unroll
+        for (int r = 0; r < SL::R; ++r) {
+          const int x = j + r * SL::NS;
+          if (cdist(x, px, W) <= kHalfWindow) continue;
+          if (cdist(2 * p, py, H) <= kHalfWindow) e += (double)V[kk][r].x * V[kk][r].x;
+          if (cdist(2 * p + 1, py, H) <= kHalfWindow) e += (double)V[kk][r].y * V[kk][r].y;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  e = warp_sum(e);
+  if ((t & 31) == 0) red[w].sa = e;
+  __syncthreads();
+  if (t == 0) {
+    double etot = red[0].sa;
+    for (int k = 1; k < NW; ++k) etot += red[k].sa;
+    const double E = etot / ((double)H * (double)W - (double)kWindowCount);
+    const double pk = (double)s_peak;
+    double pce;
+    if (E > 0.0) pce = (pk < 0 ? -1.0 : 1.0) * pk * pk / E;
+    else pce = pk == 0.0 ? 0.0 : (pk < 0 ? -INFINITY : INFINITY);
+    const FpDesc fp = a.fps[it.fp];
+    double pv = pk / ((double)H * (double)W) * (double)(*fp.inv_scale);
+    if (a.scale) pv /= (double)a.scale[it.frame];
+    CandResult res;
+    res.pce = pce;
+    res.peak = (float)pv;
+    res.py = py;
+    res.px = px;
+    res.cand = it.cand;
+    res.group = it.group;
+    res.pad = 0;
+    *result_of(a, is) = res;
+  }
+}
+//
+// One launch runs every phase of every candidate of a call.  Blocks take
+// tasks by an atomic ticket.  Ticket order is a skewed pipeline: step s holds
+// the row-forward tasks of candidate s, the column tasks of s-1, the
+// row-inverse tasks of s-2 and the finalisation of s-3, so each task depends
+// only on tasks with smaller tickets, which running blocks hold: the kernel
+// cannot deadlock, whatever number of blocks is resident.  A task waits
+// (bounded, with back-off) for the per-candidate count of its inputs; on
+// timeout it raises the error flag and gives up instead of hanging.  Spectra
+// and row statistics live in S workspace slots used round-robin (candidate g
+// in slot g % S), so only about four candidates' spectra are in flight and
+// they stay in L2; a row-forward task also waits for the finalisation of
+// candidate g - S, the previous user of its slot.
+
+constexpr long long kSpinLimit = 1ll << 23;   // ~2 s with the back-off below
+
+__device__ __forceinline__ bool wait_count(const int* c, int need, int* err) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (*(volatile const int*)c >= need) {
+      __threadfence();
+      return true;
+    }
+    if (*(volatile int*)err) return false;
+    __nanosleep(it < 32 ? 64 : 256);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+template <int DT, class RS, int RT, int PPB, class CS, int NC>
+__global__ void __launch_bounds__(RT * PPB, 2) k_persist(PassArgs a, PersistArgs p) {
+  constexpr int TB = RT * PPB;
+  extern __shared__ float2 smem[];
+  __shared__ int s_task, s_ok;
+  const int H = a.H, Wh = a.W / 2;
+  const int NRF = (H / 2) / PPB;
+  const int NCOL = (Wh + NC - 1) / NC;
+  const int NRI = NRF;
+  const int TPS = NRF + NCOL + NRI + 1;
+  const int total = (p.G + 3) * TPS;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(p.ticket, 1);
+    __syncthreads();
+    const int tk = s_task;
+    __syncthreads();
+    if (tk >= total) break;
+    const int step = tk / TPS, r = tk - (tk / TPS) * TPS;
+    int type, g, idx;
+    if (r < NRF) {
+      type = 0; g = step; idx = r;
+    } else if (r < NRF + NCOL) {
+      type = 1; g = step - 1; idx = r - NRF;
+    } else if (r < NRF + NCOL + NRI) {
+      type = 2; g = step - 2; idx = r - NRF - NCOL;
+    } else {
+      type = 3; g = step - 3; idx = 0;
+    }
+    if (g < 0 || g >= p.G) continue;
+    const int ws = g % p.S;
+    if (threadIdx.x == 0) {
+      const int* dep = nullptr;
+      int need = 1;
+      if (type == 0) {
+        if (g >= p.S) dep = p.fin_done + (g - p.S);
+      } else if (type == 1) {
+        dep = p.rf_done + g;
+        need = NRF;
+      } else if (type == 2) {
+        dep = p.col_done + g;
+        need = NCOL;
+      } else {
+        dep = p.ri_done + g;
+        need = NRI;
+      }
+      s_ok = dep ? wait_count(dep, need, p.error) : 1;
+    }
+    __syncthreads();
+    if (!s_ok) continue;
+    if (type == 0) row_forward_task<DT, RS, RT, PPB>(a, g, ws, idx, smem);
+    else if (type == 1) col_task<CS, NC, TB>(a, g, ws, idx, smem);
+    else if (type == 2) row_inverse_task<RS, RT, PPB>(a, ws, idx, smem);
+    else finalize_task<RS, RT, PPB>(a, g, ws, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      int* c = type == 0 ? p.rf_done : type == 1 ? p.col_done : type == 2 ? p.ri_done : p.fin_done;
+      atomicAdd(c + g, 1);
+    }
   }
 }
 
@@ -338,12 +544,36 @@ struct ShapeDef {
     allow(k_row_inverse_fx<RS, RT, PPB>);
     return r;
   }
-  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols) {
+  // PRT threads per row pair (PRT * PPB per block, also the column task's
+  // threads): chosen so that every stage holds one butterfly per thread
+  template <int PRT, int PPB, int NC>
+  static FixedPersist persist() {
+    FixedPersist f{};
+    f.ppb = PPB;
+    f.nc = NC;
+    f.threads = PRT * PPB;
+    const size_t rs = row_fx_smem<W>(PPB);
+    const size_t cs = (size_t)col_smem_len(H, NC) * sizeof(float2);
+    const size_t fs = (size_t)2 * row_smem_len(W) * sizeof(float2) + 32 * sizeof(WarpRed);
+    f.smem = std::max(rs, std::max(cs, fs));
+    f.fn[kF32] = (void*)k_persist<kF32, RS, PRT, PPB, CS, NC>;
+    f.fn[kF16] = (void*)k_persist<kF16, RS, PRT, PPB, CS, NC>;
+    f.fn[kBF16] = (void*)k_persist<kBF16, RS, PRT, PPB, CS, NC>;
+    for (int d = 0; d < 3; ++d) {
+      allow_max_dynamic_smem(f.fn[d]);
+      int nb = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f.fn[d], f.threads, f.smem);
+      f.blocks_per_sm[d] = std::max(1, nb);
+    }
+    return f;
+  }
+  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, FixedPersist ps) {
     FixedShape s{};
     s.W = W;
     s.H = H;
     s.rows = std::move(rows);
     s.cols = std::move(cols);
+    s.persist = ps;
     return s;
   }
 };
@@ -353,19 +583,22 @@ std::vector<FixedShape> build_registry() {
   {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 12, 10, 9>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()}));
+                        {D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()},
+                        D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 10, 9, 8>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<8, 384>(), D::col<16, 736>()}));
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<8, 384>(), D::col<16, 736>()},
+                        D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<4, 736>(), D::col<8, 736>()}));
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<4, 736>(), D::col<8, 736>()},
+                        D::persist<384, 1, 2>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<8, 128>(), D::col<16, 256>()}));
+    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<8, 128>(), D::col<16, 256>()}, D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
   return v;
@@ -408,6 +641,16 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
     PRNU_CUDA_TRY(cudaLaunchKernel(fr.inv, g, b, args, fr.smem, s));
   }
   lc.n += 3;
+}
+
+void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape& fs, int sm_count, cudaStream_t s,
+                       LaunchCounter& lc) {
+  const FixedPersist& f = fs.persist;
+  void* args[] = {const_cast<PassArgs*>(&a), const_cast<PersistArgs*>(&p)};
+  ProfScope ps(lc, kKindFused, s);
+  const int grid = sm_count * f.blocks_per_sm[a.rdtype];
+  PRNU_CUDA_TRY(cudaLaunchKernel(f.fn[a.rdtype], dim3(grid), dim3(f.threads), args, f.smem, s));
+  lc.n += 1;
 }
 
 }  // namespace prnu

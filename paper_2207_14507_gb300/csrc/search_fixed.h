@@ -23,10 +23,34 @@ struct FixedRow {
   void* inv;
 };
 
+// the persistent kernel of a shape: row pairs per task, columns per task,
+// block size, shared memory, resident blocks per SM, by residual type
+struct FixedPersist {
+  int ppb, nc, threads;
+  size_t smem;
+  void* fn[3];
+  int blocks_per_sm[3];
+};
+
+// Device state of one persistent launch: the ticket, the error flag, and the
+// per-candidate completion counts of the four phases ([G] each), all zeroed
+// before the launch.  S = workspace slots (spectra, row statistics).
+struct PersistArgs {
+  int* ticket;
+  int* error;
+  int* rf_done;
+  int* col_done;
+  int* ri_done;
+  int* fin_done;
+  int G;
+  int S;
+};
+
 struct FixedShape {
   int W, H;
   std::vector<FixedRow> rows;
   std::vector<FixedCol> cols;
+  FixedPersist persist;
   // the row kernels with `ppb` pairs per block, else the first variant
   const FixedRow& row_for(int ppb) const {
     for (auto& r : rows)
@@ -43,5 +67,12 @@ bool fixed_supports(const FixedShape& fs, int H, int ppb);
 
 // row forward, column pass and row inverse of one wave (a.nitems candidates)
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc);
+
+// every phase of p.G candidates (items 0..G-1 of a) in one persistent launch;
+// a.spec / a.stats hold p.S workspace slots
+void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape& fs, int sm_count, cudaStream_t s,
+                       LaunchCounter& lc);
+
+constexpr int kPersistSlots = 8;
 
 }  // namespace prnu

@@ -264,13 +264,15 @@ class ServingQuery:
 def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
                       resolutions=((720, 1280), (1080, 1920), (2160, 3840)),
                       frames_range=(8, 64), fps_range=(1, 16), bank_size: int = 16,
-                      pool_frames: int = 64, grid: Grid = GRID_FULL, config: int = 5):
+                      pool_frames: int = 64, grid: Grid = GRID_FULL, config: int = 5,
+                      match_sources: int | None = None):
     """Poisson query stream over per-resolution fingerprint banks and frame pools.
 
     To keep generation cheap, each resolution gets a pool of `pool_frames`
-    stabilised frames per bank fingerprint that is actually drawn as a match;
-    a query takes a contiguous run of a pool (wrapping around).  Returns
-    (queries, banks) where banks[(H, W)] is a list of float32 fingerprints.
+    stabilised frames per bank fingerprint that is actually drawn as a match
+    (with `match_sources` set, only bank fingerprints 0..match_sources-1 can be
+    the match); a query takes a contiguous run of a pool (wrapping around).
+    Returns (queries, banks) where banks[(H, W)] is a list of float32 fingerprints.
     """
     ra = rng_for(config, STREAM_ARRIVALS)
     t = 0.0
@@ -287,6 +289,12 @@ def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
         P = int(ra.integers(fps_range[0], fps_range[1] + 1))
         fp_ids = sorted(ra.choice(bank_size, size=P, replace=False).tolist())
         match = int(fp_ids[int(ra.integers(0, P))]) if ra.random() < 0.5 else -1
+        if match >= 0 and match_sources is not None and match >= match_sources:
+            m = int(ra.integers(0, match_sources))
+            if m not in fp_ids:
+                fp_ids[fp_ids.index(match)] = m
+                fp_ids.sort()
+            match = m
         src = match if match >= 0 else bank_size  # bank_size = "no bank fingerprint"
         key = (H, W, src)
         if key not in pools:

@@ -280,6 +280,44 @@ def test_fixed_plan_kernels_match_generic_and_oracle(ctx, prnu, H, W, nvar):
         assert got_g[0, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL)
 
 
+@pytest.mark.parametrize("H,W,nvar", FIXED_SHAPES)
+def test_persistent_launch_matches_wave_kernels(ctx, prnu, H, W, nvar):
+    """One persistent launch per call (tasks over ring slots) gives the wave
+    kernels' PCEs and arg-max, with fewer candidates than slots and with many
+    times more (slot reuse)."""
+    g = synth.Grid(0.98, 0.01, 5, -1.0, 0.5, 5)
+    wl = synth.make_workload(2, H=H, W=W, F=2, grid=g, on_grid=True, s_max=16)
+    t0 = ctx.prnu_get_tuning(H, W)
+    try:
+        for win in (np.array([[2, 2, 2, 2], [1, 1, 3, 3]], np.int32),        # 2 candidates
+                    np.array([[0, 4, 0, 4], [0, 3, 1, 4]], np.int32)):       # 41 candidates
+            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 8, 0, 0)
+            res_w, got_w = _gpu_search(ctx, prnu, wl, windows=win)
+            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], 8, 0, 1)
+            res_p, got_p = _gpu_search(ctx, prnu, wl, windows=win)
+            _assert_all_close(got_p, got_w, 1e-5)
+            for f in range(2):
+                assert res_p[f, 0]["cand_idx"] == res_w[f, 0]["cand_idx"]
+                assert (res_p[f, 0]["dy"], res_p[f, 0]["dx"]) == (res_w[f, 0]["dy"], res_w[f, 0]["dx"])
+    finally:
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"])
+
+
+def test_persistent_config1_against_oracle(ctx, prnu):
+    wl = synth.make_workload(1)
+    t0 = ctx.prnu_get_tuning(256, 256)
+    try:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], t0["wave"], 0, 1)
+        res, got = _gpu_search(ctx, prnu, wl)
+    finally:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"])
+    best, ref = _oracle_search(wl)
+    _assert_all_close(got, ref, FP32_TOL)
+    _assert_best_equal(res, best)
+
+
 def test_tuning_rejects_bad_variants(ctx, prnu):
     t = ctx.prnu_get_tuning(1080, 1920)
     with pytest.raises(prnu.PrnuError):
