@@ -287,6 +287,9 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   ensure_buf(c, c->ws_spec, (size_t)slots * H * Wh * sizeof(float2));
   ensure_buf(c, c->ws_stats, (size_t)slots * H * sizeof(RowStat));
   if (persistent) ensure_buf(c, c->ws_persist, sizeof(int) * (2 + 4 * (size_t)n));
+  // the compile-time-planned kernels read the residuals in the zero-bordered layout
+  const ResidLayout lay = fs ? padded_layout(H, W) : dense_layout(H, W);
+  if (fs) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 ? 4 : 2));
   std::vector<FpDesc> fd = fp_descs(call);
   Stager st(c);
   st.add(c->ws_items.p, call.items.data(), call.items.size());
@@ -296,7 +299,14 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
 
   PassArgs a{};
   a.resid = call.resid;
+  if (fs) {
+    launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches);
+    a.resid = c->ws_pad.p;
+  }
   a.rdtype = call.rdtype;
+  a.rpitch = lay.rpitch;
+  a.fpitch = lay.fpitch;
+  a.roff = lay.roff;
   a.H = H;
   a.W = W;
   a.items = reinterpret_cast<const WorkItem*>(c->ws_items.p);
@@ -498,7 +508,7 @@ int prnu_destroy(prnu_ctx* ctx) {
     }
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
-                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist})
+                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

@@ -49,8 +49,11 @@ struct CandResult {
 
 // Host-built description of one launch of the fused path.
 struct PassArgs {
-  const void* resid;          // [F][H][W] of `rdtype`
+  const void* resid;          // frames of `rdtype`: pixel (y, x) of frame f at f*fpitch + roff + y*rpitch + x
   int rdtype;
+  int rpitch;                 // row pitch (elements)
+  size_t fpitch;              // frame pitch (elements)
+  size_t roff;                // offset of pixel (0, 0) inside a frame (elements)
   int H, W;
   const WorkItem* items;      // all items of the call
   int item0;                  // first item of this wave
@@ -80,13 +83,13 @@ __device__ __forceinline__ WorkItem item_of(const PassArgs& a, int slot) {
 __device__ __forceinline__ CandResult* result_of(const PassArgs& a, int slot) {
   return a.result_ptrs ? a.result_ptrs[slot] : a.results + a.item0 + slot;
 }
-// residual of frame f: base pointer, element offset of the frame's first pixel
+// residual of frame f: base pointer, element offset of the frame's pixel (0, 0)
 __device__ __forceinline__ const void* frame_of(const PassArgs& a, int f, size_t* base) {
   if (a.frame_ptrs) {
-    *base = 0;
+    *base = a.roff;
     return a.frame_ptrs[f];
   }
-  *base = (size_t)f * a.H * a.W;
+  *base = (size_t)f * a.fpitch + a.roff;
   return a.resid;
 }
 

@@ -126,10 +126,24 @@ inline void allow_max_dynamic_smem(K k) {
 
 // ---------------------------------------------------------------- launchers (residual.cu)
 
+// Where residual pixel (y, x) of frame f is stored: f*fpitch + roff + y*rpitch + x.
+struct ResidLayout {
+  int rpitch;
+  size_t fpitch;
+  size_t roff;
+};
+// lay == nullptr: dense [F][H][W]
 void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, int flags, int dtype, void* out,
                      float* scale, unsigned long long* acc, double* partials, int max_partials, cudaStream_t s,
-                     LaunchCounter& lc);
+                     LaunchCounter& lc, const ResidLayout* lay = nullptr);
 size_t residual_partials_needed(int F, int H, int W);
+// dense [F][H][W] residuals -> the zero-bordered layout the compile-time-planned
+// kernels read (row pitch W + 3, pixel (0, 0) at W + 4, (H + 3)(W + 3) per frame)
+void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc);
+inline ResidLayout dense_layout(int H, int W) { return ResidLayout{W, (size_t)H * W, 0}; }
+inline ResidLayout padded_layout(int H, int W) {
+  return ResidLayout{W + 3, (size_t)(H + 3) * (W + 3), (size_t)(W + 3) + 1};
+}
 
 // ---------------------------------------------------------------- context
 
@@ -174,7 +188,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist;
+      ws_persist, ws_pad;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch
   std::vector<char> h_stage;      // staging for host->device descriptors

@@ -70,11 +70,12 @@ __device__ __forceinline__ float residual_value(int s1, int s2, int xc, float nu
   return weight ? (float)xc * w : w;
 }
 
-// MODE 0: store R; MODE 1: per-block sum of R^2 (double) to partials; MODE 2: store R * scale[f]
+// MODE 0: store R; MODE 1: per-block sum of R^2 (double) to partials; MODE 2: store R * scale[f].
+// R(y, x) of frame f goes to out[f * lay.fpitch + lay.roff + y * lay.rpitch + x].
 template <int DT, int MODE>
 __global__ void k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, int H, int W,
                               const unsigned long long* __restrict__ acc, int weight, void* __restrict__ out,
-                              double* __restrict__ partials, const float* __restrict__ scale) {
+                              double* __restrict__ partials, const float* __restrict__ scale, ResidLayout lay) {
   __shared__ double part[kBX * kBY / 32];
   const int f = blockIdx.z;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
@@ -87,8 +88,9 @@ __global__ void k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, 
     int s1, s2, xc;
     moments3x3(fr, pitch, H, W, y, x, &s1, &s2, &xc);
     r = residual_value(s1, s2, xc, nu2, nu2x81, weight);
-    if (MODE == 0) store_store_type<DT>(out, ((size_t)f * H + y) * W + x, r);
-    if (MODE == 2) store_store_type<DT>(out, ((size_t)f * H + y) * W + x, r * scale[f]);
+    const size_t o = (size_t)f * lay.fpitch + lay.roff + (size_t)y * lay.rpitch + x;
+    if (MODE == 0) store_store_type<DT>(out, o, r);
+    if (MODE == 2) store_store_type<DT>(out, o, r * scale[f]);
   }
   if (MODE == 1) {
     double v = (double)r * (double)r;
@@ -128,15 +130,46 @@ __global__ void k_fill(float* __restrict__ p, int n, float v) {
   if (i < n) p[i] = v;
 }
 
+// Copy of dense [F][H][W] frames into the zero-bordered layout: padded row
+// yp, column xp of frame f holds pixel (yp - 1, xp - 1), or 0 outside.
+template <typename T>
+__global__ void k_pad_frames(const T* __restrict__ in, int H, int W, T* __restrict__ out) {
+  const int P = W + 3;
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x, yp = blockIdx.y;
+  const int f = blockIdx.z;
+  if (xp >= P) return;
+  const int x = xp - 1, y = yp - 1;
+  T v{};
+  if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H) v = in[((size_t)f * H + y) * W + x];
+  out[(size_t)f * (H + 3) * P + (size_t)yp * P + xp] = v;
+}
+
 template <int MODE>
 void apply_dispatch(int dtype, dim3 g, dim3 b, cudaStream_t s, const uint8_t* frames, size_t pitch, int H, int W,
-                    const unsigned long long* acc, int weight, void* out, double* partials, const float* scale) {
-  if (dtype == kF32) k_resid_apply<kF32, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale);
-  else if (dtype == kF16) k_resid_apply<kF16, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale);
-  else k_resid_apply<kBF16, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale);
+                    const unsigned long long* acc, int weight, void* out, double* partials, const float* scale,
+                    const ResidLayout& l) {
+  if (dtype == kF32)
+    k_resid_apply<kF32, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale, l);
+  else if (dtype == kF16)
+    k_resid_apply<kF16, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale, l);
+  else
+    k_resid_apply<kBF16, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale, l);
 }
 
 }  // namespace
+
+void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc) {
+  if (F == 0) return;
+  ProfScope ps(lc, kKindResidual, s);
+  const dim3 b(256), g((W + 3 + 255) / 256, H + 3, F);
+  if (dtype == kF32)
+    k_pad_frames<float><<<g, b, 0, s>>>(reinterpret_cast<const float*>(in), H, W, reinterpret_cast<float*>(out));
+  else
+    k_pad_frames<uint16_t><<<g, b, 0, s>>>(reinterpret_cast<const uint16_t*>(in), H, W,
+                                           reinterpret_cast<uint16_t*>(out));
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
 
 size_t residual_partials_needed(int F, int H, int W) {
   const size_t gx = (W + kBX - 1) / kBX, gy = (H + kBY - 1) / kBY;
@@ -145,7 +178,8 @@ size_t residual_partials_needed(int F, int H, int W) {
 
 void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, int flags, int dtype, void* out,
                      float* scale, unsigned long long* acc, double* partials, int /*max_partials*/, cudaStream_t s,
-                     LaunchCounter& lc) {
+                     LaunchCounter& lc, const ResidLayout* lay) {
+  const ResidLayout l = lay ? *lay : ResidLayout{W, (size_t)H * W, 0};
   const dim3 b(kBX, kBY);
   const dim3 g((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, F);
   const int weight = (flags & PRNU_WEIGHT_BY_INTENSITY) ? 1 : 0;
@@ -155,15 +189,15 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
   PRNU_CUDA_TRY(cudaGetLastError());
   lc.n++;
   if (flags & PRNU_NORMALISE) {
-    apply_dispatch<1>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale);
+    apply_dispatch<1>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale, l);
     PRNU_CUDA_TRY(cudaGetLastError());
     k_resid_scale<<<F, 256, 0, s>>>(partials, (int)(g.x * g.y), H, W, scale);
     PRNU_CUDA_TRY(cudaGetLastError());
-    apply_dispatch<2>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale);
+    apply_dispatch<2>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale, l);
     PRNU_CUDA_TRY(cudaGetLastError());
     lc.n += 3;
   } else {
-    apply_dispatch<0>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale);
+    apply_dispatch<0>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale, l);
     PRNU_CUDA_TRY(cudaGetLastError());
     lc.n++;
     if (scale) {

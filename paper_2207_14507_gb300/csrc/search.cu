@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(512) k_row_forward(PassArgs a, const float* __
       const float bx1 = fmaf(it.a12, dy1, cx), by1 = fmaf(it.a22, dy1, cy);
       for (int x = t; x < W; x += T) {
         const float dx = (float)x - cx;
-        const float v0 = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-        const float v1 = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+        const float v0 = bilinear<DT>(Rf, base, H, W, a.rpitch, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+        const float v1 = bilinear<DT>(Rf, base, H, W, a.rpitch, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
         buf[rpad(x)] = make_float2(v0, v1);
       }
     } else {
@@ -200,26 +200,9 @@ __global__ void __launch_bounds__(512) k_row_inverse(PassArgs a, float* __restri
       sb = fmaf(v.y, v.y, sb);
     }
   }
-  double da = sa, db = sb;
-  warp_maxarg(ma, ia);
-  warp_maxarg(mb, ib);
-  da = warp_sum(da);
-  db = warp_sum(db);
-  const int w = t >> 5;
-  if ((t & 31) == 0) red[w] = WarpRed{ma, ia, mb, ib, da, db};
+  row_stats_warp(ma, ia, mb, ib, sa, sb, t, reinterpret_cast<RowRed*>(red));
   __syncthreads();
-  if (active && t == 0) {
-    const int nw = T >> 5;
-    for (int k = 1; k < nw; ++k) {
-      better_f(ma, ia, red[k].ma, red[k].ia);
-      better_f(mb, ib, red[k].mb, red[k].ib);
-      da += red[k].sa;
-      db += red[k].sb;
-    }
-    RowStat* st = a.stats + (size_t)slot * H + 2 * pair;
-    st[0] = RowStat{ma, ia, da};
-    st[1] = RowStat{mb, ib, db};
-  }
+  if (active && t == 0) row_stats_final(reinterpret_cast<const RowRed*>(red), T >> 5, a.stats + (size_t)slot * H + 2 * pair);
 }
 
 // One block per candidate of the wave: see finalize_body.
@@ -320,7 +303,7 @@ __global__ void k_naive_warp(PassArgs a, float* __restrict__ X) {
     const float dx = (float)x - cx, dy = (float)y - cy;
     const float qx = fmaf(it.a11, dx, fmaf(it.a12, dy, cx));
     const float qy = fmaf(it.a21, dx, fmaf(it.a22, dy, cy));
-    X[i] = bilinear<kF32>(a.resid, base, H, W, qx, qy);
+    X[i] = bilinear<kF32>(a.resid, base, H, W, W, qx, qy);
   }
 }
 

@@ -53,6 +53,64 @@ __device__ __forceinline__ double warp_sum(double s) {
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
+
+// Compensated FP32 summation (Knuth's TwoSum): the pair (s, c) holds the
+// value s + c; adding b keeps the rounding error of s + b in c.
+__device__ __forceinline__ void csum_add(float& s, float& c, float b) {
+  const float t = s + b;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (b - bp);
+  s = t;
+  c += e;
+}
+__device__ __forceinline__ void warp_csum(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    c += c2;
+    csum_add(s, c, s2);
+  }
+}
+
+// Per-warp partial statistics of a row pair (rows a and b).
+struct RowRed {
+  float ma;
+  int ia;
+  float mb;
+  int ib;
+  float sa, ca, sb, cb;   // compensated sums of squares
+};
+static_assert(sizeof(RowRed) == sizeof(WarpRed), "row reductions share the WarpRed scratch");
+
+// Reduce the per-thread row statistics of a row pair to one RowRed per warp
+// (lane 0 writes red[warp]).  Per thread: FP32 partial over its few elements;
+// across the warp: compensated FP32.
+__device__ __forceinline__ void row_stats_warp(float ma, int ia, float mb, int ib, float sa, float sb, int t,
+                                               RowRed* red) {
+  float ca = 0.f, cb = 0.f;
+  warp_maxarg(ma, ia);
+  warp_maxarg(mb, ib);
+  warp_csum(sa, ca);
+  warp_csum(sb, cb);
+  if ((t & 31) == 0) red[t >> 5] = RowRed{ma, ia, mb, ib, sa, ca, sb, cb};
+}
+// Combine nw warps' RowRed (after a barrier) into the two rows' statistics.
+__device__ __forceinline__ void row_stats_final(const RowRed* red, int nw, RowStat* st) {
+  RowRed r = red[0];
+#pragma unroll 1
+  for (int k = 1; k < nw; ++k) {
+    const RowRed q = red[k];
+    better_f(r.ma, r.ia, q.ma, q.ia);
+    better_f(r.mb, r.ib, q.mb, q.ib);
+    r.ca += q.ca;
+    csum_add(r.sa, r.ca, q.sa);
+    r.cb += q.cb;
+    csum_add(r.sb, r.cb, q.sb);
+  }
+  st[0] = RowStat{r.ma, r.ia, (double)r.sa + (double)r.ca};
+  st[1] = RowStat{r.mb, r.ib, (double)r.sb + (double)r.cb};
+}
 // cyclic distance between indices a and b modulo n
 __device__ __forceinline__ int cdist(int a, int b, int n) {
   int d = a - b;
@@ -63,18 +121,67 @@ __device__ __forceinline__ int cdist(int a, int b, int n) {
 constexpr int kHalfWindow = 5;      // Eq. 3: 11 x 11 exclusion
 constexpr int kWindowCount = 121;
 
+// Bilinear sample of an H x W frame (row pitch `pitch`, pixel (0, 0) at
+// element `base` of R) at (qx, qy); each tap outside the frame contributes 0.
 template <int DT>
-__device__ __forceinline__ float bilinear(const void* R, size_t base, int H, int W, float qx, float qy) {
+__device__ __forceinline__ float bilinear(const void* R, size_t base, int H, int W, int pitch, float qx, float qy) {
   const float fx0 = floorf(qx), fy0 = floorf(qy);
   const float fx = qx - fx0, fy = qy - fy0;
   const int x0 = (int)fx0, y0 = (int)fy0;
   const bool xi0 = (unsigned)x0 < (unsigned)W, xi1 = (unsigned)(x0 + 1) < (unsigned)W;
   const bool yi0 = (unsigned)y0 < (unsigned)H, yi1 = (unsigned)(y0 + 1) < (unsigned)H;
-  const size_t r0 = base + (size_t)y0 * W + x0;
+  const size_t r0 = base + (size_t)((long long)y0 * pitch + x0);
   const float v00 = (yi0 && xi0) ? load_store_type<DT>(R, r0) : 0.f;
   const float v01 = (yi0 && xi1) ? load_store_type<DT>(R, r0 + 1) : 0.f;
-  const float v10 = (yi1 && xi0) ? load_store_type<DT>(R, r0 + W) : 0.f;
-  const float v11 = (yi1 && xi1) ? load_store_type<DT>(R, r0 + W + 1) : 0.f;
+  const float v10 = (yi1 && xi0) ? load_store_type<DT>(R, r0 + pitch) : 0.f;
+  const float v11 = (yi1 && xi1) ? load_store_type<DT>(R, r0 + pitch + 1) : 0.f;
+  const float gx = 1.f - fx, gy = 1.f - fy;
+  return gy * (gx * v00 + fx * v01) + fy * (gx * v10 + fx * v11);
+}
+
+template <int DT>
+struct StoreT;
+template <>
+struct StoreT<kF32> {
+  using type = float;
+  __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+};
+template <>
+struct StoreT<kF16> {
+  using type = __half;
+  __device__ __forceinline__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+};
+template <>
+struct StoreT<kBF16> {
+  using type = __nv_bfloat16;
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+};
+
+// Zero-bordered frame layout read by the compile-time-planned kernels: one
+// zero row/column before the frame and two after it, row pitch W + 3, so
+// that every clamped bilinear tap is a valid address.
+__host__ __device__ constexpr int pad_pitch(int W) { return W + 3; }
+__host__ __device__ constexpr size_t pad_frame_elems(int H, int W) { return (size_t)(H + 3) * (W + 3); }
+__host__ __device__ constexpr size_t pad_origin(int W) { return (size_t)(W + 3) + 1; }
+
+// bilinear<DT> on the zero-bordered layout, W a compile-time constant, `fr`
+// pointing at pixel (0, 0).  The sample point is clamped to [-1, W] x [-1, H]:
+// inside that box the taps and weights are those of bilinear<DT> (a tap in
+// the border reads 0); outside it every tap of bilinear<DT> is outside the
+// frame, and here the clamped point puts weight 1 on a border zero and
+// weight 0 on the rest.  So the value is the same, with no predicate: one
+// index, four loads at fixed offsets.
+template <int DT, int W>
+__device__ __forceinline__ float bilinear_pad(const typename StoreT<DT>::type* __restrict__ fr, int H, float qx,
+                                              float qy) {
+  using S = StoreT<DT>;
+  constexpr int P = pad_pitch(W);
+  qx = fminf(fmaxf(qx, -1.f), (float)W);
+  qy = fminf(fmaxf(qy, -1.f), (float)H);
+  const float fx0 = floorf(qx), fy0 = floorf(qy);
+  const float fx = qx - fx0, fy = qy - fy0;
+  const auto* p = fr + ((int)fy0 * P + (int)fx0);
+  const float v00 = S::ld(p), v01 = S::ld(p + 1), v10 = S::ld(p + P), v11 = S::ld(p + P + 1);
   const float gx = 1.f - fx, gy = 1.f - fy;
   return gy * (gx * v00 + fx * v01) + fy * (gx * v10 + fx * v11);
 }

@@ -92,9 +92,9 @@ __host__ __device__ constexpr size_t row_fx_smem(int ppb) {
 // Row pairs bx*PPB .. bx*PPB+PPB-1 of candidate `is` (item slot), spectrum
 // written to workspace slot `ws`.  Block = PPB groups of T threads.
 template <int DT, class SP, int T, int PPB>
-__device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int ws, int bx, float2* smem) {
+__device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
   constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
-  const int grp = threadIdx.x / T, t = threadIdx.x - grp * T;
+  const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
@@ -103,6 +103,7 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
   const WorkItem it = item_of(a, is);
   size_t base;
   const void* Rf = frame_of(a, it.frame, &base);
+  const auto* fr = reinterpret_cast<const typename StoreT<DT>::type*>(Rf) + base;
   const int y0 = 2 * pair;
   const float cx = 0.5f * (float)(W - 1), cy = 0.5f * (float)(H - 1);
   const float dy0 = (float)y0 - cy, dy1 = dy0 + 1.f;
@@ -117,8 +118,8 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
 #pragma unroll
     for (int r = 0; r < S0::R; ++r) {
       const float dx = (float)(j + r * S0::NB) - cx;
-      v[r].x = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-      v[r].y = bilinear<DT>(Rf, base, H, W, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+      v[r].x = bilinear_pad<DT, W>(fr, H, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+      v[r].y = bilinear_pad<DT, W>(fr, H, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
     }
     Dft<S0::R, false>::run(v);
 #pragma unroll
@@ -147,24 +148,40 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
 // ---------------------------------------------------------------- column pass
 
 // Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
-template <class SP, int NC, int T, bool CG = false>
-__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm) {
+template <class SP, int NC, int T, bool CG = false, bool PF = true>
+__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm, int tx) {
   constexpr int H = SP::N;
   using IS = typename SP::Rev;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x;   // == tx; the builtin gives this body the faster schedule (measured)
   const int Wh = a.W >> 1;
   const int c0 = bx * NC;
   float2* Z = a.spec + (size_t)ws * H * Wh;
   const float2* tw = a.tw + a.pcol.tw_off;
   const WorkItem wi = item_of(a, is);
   const FpDesc fp = a.fps[wi.fp];
+  using FL = StageC<SP, SP::S - 1, T, NC>;
+  using I0 = StageC<IS, 0, T, NC>;
+
+  // The fingerprint bins this thread multiplies after the last forward stage
+  // are known now: load them first, so that their latency hides behind the
+  // forward stages (when they fit in a few registers and PF allows it).
+  constexpr bool kPrefetch = PF && FL::IT * FL::R <= 16;
+  float2 Sp[kPrefetch ? FL::IT : 1][kPrefetch ? FL::R : 1];
+  if constexpr (kPrefetch) {
+#pragma unroll
+    for (int k = 0; k < FL::IT; ++k) {
+      if (!stage_valid<FL>(t, k)) continue;
+      const int j = stage_j<FL>(t, k), col = c0 + stage_c<FL>(t, k);
+#pragma unroll
+      for (int r = 0; r < FL::R; ++r)
+        Sp[k][r] = col < Wh ? load_spec(fp.spec, fp.dtype, (size_t)(j + r * FL::NS) * Wh + col)
+                            : make_float2(0.f, 0.f);
+    }
+  }
 
   stage_stream<StageC<SP, 0, T, NC>, false>(t, tw, StripLd<CG>{Z, Wh, c0}, ColSt<NC>{sm});
   __syncthreads();
   ColStagesIP<SP, 1, SP::S - 1, T, NC, false>::run(sm, t, tw);
-
-  using FL = StageC<SP, SP::S - 1, T, NC>;
-  using I0 = StageC<IS, 0, T, NC>;
   static_assert(I0::R == FL::R && I0::NB == FL::NB && FL::NB == FL::NS, "register hand-off needs the reversed plan");
   float2 V[FL::IT][FL::R];
   stage_load<FL>(t, ColLd<NC>{sm}, V);
@@ -209,7 +226,9 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     if (col == 0 || col >= Wh) continue;
 #pragma unroll
     for (int r = 0; r < FL::R; ++r) {
-      const float2 S = load_spec(fp.spec, fp.dtype, (size_t)(j + r * FL::NS) * Wh + col);
+      float2 S;
+      if constexpr (kPrefetch) S = Sp[k][r];
+      else S = load_spec(fp.spec, fp.dtype, (size_t)(j + r * FL::NS) * Wh + col);
       V[k][r] = c_mul(c_conj(V[k][r]), S);
     }
   }
@@ -223,14 +242,14 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
 // ---------------------------------------------------------------- row inverse + statistics
 
 template <class SP, int T, int PPB, bool CG = false>
-__device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int bx, float2* smem) {
+__device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int bx, float2* smem, int tx) {
   constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
-  const int grp = threadIdx.x / T, t = threadIdx.x - grp * T;
+  const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
-  WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
+  RowRed* red = reinterpret_cast<RowRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
   const float2* tw = a.tw + a.prow.tw_off;
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
   stage_stream<StageC<SP, 0, T>, true>(t, tw, FullRowLd<CG>{pa, pa + Wh, W, Wh}, RowSt{A});
@@ -259,26 +278,9 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
       sb = fmaf(v.y, v.y, sb);
     }
   }
-  double da = sa, db = sb;
-  warp_maxarg(ma, ia);
-  warp_maxarg(mb, ib);
-  da = warp_sum(da);
-  db = warp_sum(db);
-  const int w = t >> 5;
-  if ((t & 31) == 0) red[w] = WarpRed{ma, ia, mb, ib, da, db};
+  row_stats_warp(ma, ia, mb, ib, sa, sb, t, red);
   __syncthreads();
-  if (t == 0) {
-    constexpr int NW = (T + 31) / 32;
-    for (int k = 1; k < NW; ++k) {
-      better_f(ma, ia, red[k].ma, red[k].ia);
-      better_f(mb, ib, red[k].mb, red[k].ib);
-      da += red[k].sa;
-      db += red[k].sb;
-    }
-    RowStat* st = a.stats + (size_t)ws * H + 2 * pair;
-    st[0] = RowStat{ma, ia, da};
-    st[1] = RowStat{mb, ib, db};
-  }
+  if (t == 0) row_stats_final(red, (T + 31) / 32, a.stats + (size_t)ws * H + 2 * pair);
 }
 
 // ---------------------------------------------------------------- wave kernels
@@ -286,47 +288,50 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
 template <int DT, class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
   extern __shared__ float2 smem[];
-  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem);
+  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem, threadIdx.x);
 }
 
 template <class SP, int NC, int T>
 __global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
   extern __shared__ float2 smem[];
-  col_body<SP, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem);
+  col_body<SP, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem, threadIdx.x);
 }
 
 template <class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
   extern __shared__ float2 smem[];
-  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, smem);
+  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, smem, threadIdx.x);
 }
 
 // ---------------------------------------------------------------- persistent kernel
 
-// Separate (not inlined) task functions: each keeps its own register
-// allocation instead of the kernel holding the union of all three.
+// Task bodies, inlined into k_persist.  The kernel hands them a thread index
+// that the compiler cannot prove loop-invariant (see k_persist), so the
+// per-thread index arithmetic of each task is computed inside its own branch
+// instead of being hoisted out of the task loop, where the three tasks'
+// values would all stay live at once.
 template <int DT, class SP, int T, int PPB>
-__device__ __noinline__ void row_forward_task(const PassArgs& a, int is, int ws, int bx, float2* smem) {
-  row_forward_body<DT, SP, T, PPB>(a, is, ws, bx, smem);
+__device__ __forceinline__ void row_forward_task(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
+  row_forward_body<DT, SP, T, PPB>(a, is, ws, bx, smem, tx);
 }
 template <class SP, int NC, int T>
-__device__ __noinline__ void col_task(const PassArgs& a, int is, int ws, int bx, float2* smem) {
-  col_body<SP, NC, T, true>(a, is, ws, bx, smem);
+__device__ __forceinline__ void col_task(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
+  col_body<SP, NC, T, true, false>(a, is, ws, bx, smem, tx);   // no prefetch: registers are capped here
 }
 template <class SP, int T, int PPB>
-__device__ __noinline__ void row_inverse_task(const PassArgs& a, int ws, int bx, float2* smem) {
-  row_inverse_body<SP, T, PPB, true>(a, ws, bx, smem);
+__device__ __forceinline__ void row_inverse_task(const PassArgs& a, int ws, int bx, float2* smem, int tx) {
+  row_inverse_body<SP, T, PPB, true>(a, ws, bx, smem, tx);
 }
 
 // finalize_body with the window's rows recomputed by the compile-time-planned
 // inverse row FFT (one row pair per thread group, PPB pairs per round).
 template <class SP, int T, int PPB>
-__device__ __noinline__ void finalize_task(const PassArgs& a, int is, int ws, float2* smem) {
+__device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws, float2* smem, int tx) {
   constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W), TB = T * PPB;
   __shared__ int s_py, s_px, s_np;
   __shared__ float s_peak;
   __shared__ int s_pairs[2 * kHalfWindow + 1];
-  const int t = threadIdx.x, grp = t / T, tg = t - grp * T;
+  const int t = tx, grp = t / T, tg = t - grp * T;
   const int H = a.H;
   const WorkItem it = item_of(a, is);
   const RowStat* st = a.stats + (size_t)ws * H;
@@ -452,22 +457,29 @@ __device__ __forceinline__ bool wait_count(const int* c, int need, int* err) {
 }
 
 template <int DT, class RS, int RT, int PPB, class CS, int NC>
-__global__ void __launch_bounds__(RT * PPB, 2) k_persist(PassArgs a, PersistArgs p) {
+__global__ void __launch_bounds__(RT * PPB, 2) k_persist(const __grid_constant__ PassArgs a, const __grid_constant__ PersistArgs p) {
   constexpr int TB = RT * PPB;
   extern __shared__ float2 smem[];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_tk[2], s_ok, s_zero;
+  static_assert(RT * PPB >= 64, "warp 1 publishes completions");
   const int H = a.H, Wh = a.W / 2;
   const int NRF = (H / 2) / PPB;
   const int NCOL = (Wh + NC - 1) / NC;
   const int NRI = NRF;
   const int TPS = NRF + NCOL + NRI + 1;
   const int total = (p.G + 3) * TPS;
-  for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(p.ticket, 1);
-    __syncthreads();
-    const int tk = s_task;
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    s_tk[0] = atomicAdd(p.ticket, 1);
+    s_zero = 0;
+  }
+  __syncthreads();
+  for (int iter = 0;; ++iter) {
+    const int tk = s_tk[iter & 1];
     if (tk >= total) break;
+    // the next ticket is fetched now and used after this task: its latency
+    // overlaps the task instead of stalling the block
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(p.ticket, 1);
     const int step = tk / TPS, r = tk - (tk / TPS) * TPS;
     int type, g, idx;
     if (r < NRF) {
@@ -479,37 +491,45 @@ __global__ void __launch_bounds__(RT * PPB, 2) k_persist(PassArgs a, PersistArgs
     } else {
       type = 3; g = step - 3; idx = 0;
     }
-    if (g < 0 || g >= p.G) continue;
-    const int ws = g % p.S;
-    if (threadIdx.x == 0) {
-      const int* dep = nullptr;
-      int need = 1;
-      if (type == 0) {
-        if (g >= p.S) dep = p.fin_done + (g - p.S);
-      } else if (type == 1) {
-        dep = p.rf_done + g;
-        need = NRF;
-      } else if (type == 2) {
-        dep = p.col_done + g;
-        need = NCOL;
-      } else {
-        dep = p.ri_done + g;
-        need = NRI;
+    if (g >= 0 && g < p.G) {   // uniform over the block
+      const int ws = g % p.S;
+      if (threadIdx.x == 0) {
+        const int* dep = nullptr;
+        int need = 1;
+        if (type == 0) {
+          if (g >= p.S) dep = p.fin_done + (g - p.S);
+        } else if (type == 1) {
+          dep = p.rf_done + g;
+          need = NRF;
+        } else if (type == 2) {
+          dep = p.col_done + g;
+          need = NCOL;
+        } else {
+          dep = p.ri_done + g;
+          need = NRI;
+        }
+        s_ok = dep ? wait_count(dep, need, p.error) : 1;
       }
-      s_ok = dep ? wait_count(dep, need, p.error) : 1;
+      __syncthreads();
+      const bool ok = s_ok;
+      if (ok) {
+        const int tx = threadIdx.x + *(volatile int*)&s_zero;   // == threadIdx.x
+        if (type == 0) row_forward_task<DT, RS, RT, PPB>(a, g, ws, idx, smem, tx);
+        else if (type == 1) col_task<CS, NC, TB>(a, g, ws, idx, smem, tx);
+        else if (type == 2) row_inverse_task<RS, RT, PPB>(a, ws, idx, smem, tx);
+        else finalize_task<RS, RT, PPB>(a, g, ws, smem, tx);
+      }
+      __syncthreads();
+      // completion is published by warp 1, so that warp 0 can go on to the
+      // next ticket's dependency while the fence drains
+      if (threadIdx.x == 32 && ok) {
+        __threadfence();
+        int* c = type == 0 ? p.rf_done : type == 1 ? p.col_done : type == 2 ? p.ri_done : p.fin_done;
+        atomicAdd(c + g, 1);
+      }
     }
+    if (threadIdx.x == 0) s_tk[(iter + 1) & 1] = nxt;
     __syncthreads();
-    if (!s_ok) continue;
-    if (type == 0) row_forward_task<DT, RS, RT, PPB>(a, g, ws, idx, smem);
-    else if (type == 1) col_task<CS, NC, TB>(a, g, ws, idx, smem);
-    else if (type == 2) row_inverse_task<RS, RT, PPB>(a, ws, idx, smem);
-    else finalize_task<RS, RT, PPB>(a, g, ws, smem);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      int* c = type == 0 ? p.rf_done : type == 1 ? p.col_done : type == 2 ? p.ri_done : p.fin_done;
-      atomicAdd(c + g, 1);
-    }
   }
 }
 
@@ -584,7 +604,7 @@ std::vector<FixedShape> build_registry() {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 12, 10, 9>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()},
-                        D::persist<256, 2, 4>()));
+                        D::persist<192, 2, 8>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 10, 9, 8>>;

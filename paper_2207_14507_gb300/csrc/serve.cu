@@ -192,7 +192,7 @@ struct Server::Impl {
     const size_t n = q.call.items.size();
     size_t b = 0;
     if (q.host_frames) b += align256(px);
-    b += align256(px * elem_size(q.dtype));
+    b += align256((size_t)q.F * padded_layout(q.H, q.W).fpitch * elem_size(q.dtype));   // zero-bordered residuals
     b += align256(sizeof(WorkItem) * n) + align256(sizeof(CandResult) * n);
     b += align256(sizeof(int) * ((size_t)q.F * q.P + 1)) + align256(sizeof(prnu_result) * (size_t)q.F * q.P);
     b += align256(sizeof(unsigned long long) * q.F) +
@@ -410,7 +410,8 @@ struct Server::Impl {
       c += align256(px);
     }
     q.d_resid = c;
-    c += align256(px * elem_size(q.dtype));
+    const size_t resid_bytes = (size_t)q.F * padded_layout(q.H, q.W).fpitch * elem_size(q.dtype);
+    c += align256(resid_bytes);
     q.d_items = reinterpret_cast<WorkItem*>(c);
     c += align256(sizeof(WorkItem) * n);
     q.d_results = reinterpret_cast<CandResult*>(c);
@@ -435,11 +436,14 @@ struct Server::Impl {
       frames = q.d_frames;
       pitch = q.W;
     }
+    // residuals go straight into the zero-bordered layout every search kernel here reads
+    const ResidLayout lay = padded_layout(q.H, q.W);
+    PRNU_CUDA_TRY(cudaMemsetAsync(q.d_resid, 0, resid_bytes, s_copy));
     launch_residual(frames, q.F, q.H, q.W, pitch, q.flags, q.dtype, q.d_resid, d_scale + q.frame_slot0, q.d_acc,
-                    q.d_partials, (int)residual_partials_needed(q.F, q.H, q.W), s_copy, ctx->launches);
+                    q.d_partials, (int)residual_partials_needed(q.F, q.H, q.W), s_copy, ctx->launches, &lay);
     k_set_frame_ptrs<<<(q.F + 127) / 128, 128, 0, s_copy>>>(d_frame_ptrs + q.frame_slot0,
                                                             reinterpret_cast<const char*>(q.d_resid), q.F,
-                                                            (size_t)q.H * q.W * elem_size(q.dtype));
+                                                            lay.fpitch * elem_size(q.dtype));
     PRNU_CUDA_TRY(cudaGetLastError());
     PRNU_CUDA_TRY(cudaMemcpyAsync(q.d_items, q.call.items.data(), sizeof(WorkItem) * n, cudaMemcpyHostToDevice,
                                   s_copy));
@@ -506,6 +510,10 @@ struct Server::Impl {
                                   s_comp));
     PassArgs a{};
     a.rdtype = key.dtype;
+    const ResidLayout lay = padded_layout(H, W);
+    a.rpitch = lay.rpitch;
+    a.fpitch = lay.fpitch;
+    a.roff = lay.roff;
     a.H = H;
     a.W = W;
     a.nitems = count;

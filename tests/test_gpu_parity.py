@@ -280,6 +280,28 @@ def test_fixed_plan_kernels_match_generic_and_oracle(ctx, prnu, H, W, nvar):
         assert got_g[0, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL)
 
 
+def test_fixed_plan_warp_far_outside_the_frame(ctx, prnu):
+    """Scales 0.5 and 2 and rotations up to 60 degrees put many bilinear taps
+    outside the frame, some far outside (the compile-time-planned kernels clamp
+    them onto a zero border): every PCE equals the generic kernels' and the
+    oracle's."""
+    g = synth.Grid(0.5, 0.75, 3, -60.0, 52.5, 3)        # lambda 0.5, 1.25, 2; theta -60, -7.5, 45
+    wl = synth.make_workload(1, F=2, grid=g)
+    t0 = ctx.prnu_get_tuning(256, 256)
+    try:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], 4, -1)
+        _, got_g = _gpu_search(ctx, prnu, wl)
+        for persistent in (0, 1):
+            ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], 4, 0, persistent)
+            _, got_f = _gpu_search(ctx, prnu, wl)
+            _assert_all_close(got_f, got_g, 1e-5)
+    finally:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"])
+    _, ref = _oracle_search(wl)
+    _assert_all_close(got_g, ref, FP32_TOL)
+
+
 @pytest.mark.parametrize("H,W,nvar", FIXED_SHAPES)
 def test_persistent_launch_matches_wave_kernels(ctx, prnu, H, W, nvar):
     """One persistent launch per call (tasks over ring slots) gives the wave
