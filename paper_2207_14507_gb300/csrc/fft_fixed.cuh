@@ -1,13 +1,29 @@
 // fft_fixed.cuh -- Stockham FFT stages with a compile-time plan.
 //
-// The same autosort stage as fft.cuh (stage with radix R, Ns = product of the
+// The autosort stage of fft.cuh (stage with radix R, Ns = product of the
 // earlier radices: butterfly j reads x[j + r*n/R], twiddles input r by
 // w_{Ns*R}^{r*(j mod Ns)}, writes output r to y[(j/Ns)*Ns*R + (j mod Ns) + r*Ns]),
-// but with n, R, Ns and the thread count known at compile time, so every index,
-// division and loop bound folds to constants.  Loads and stores go through
-// accessor objects, so a kernel can feed the first stage straight from global
-// memory (or from its own computation) and take the last stage's outputs
-// straight from registers.
+// with n, R, Ns and the thread count known at compile time and the shared
+// memory layouts chosen so that every element a thread touches lies at a
+// compile-time offset from one per-thread base address:
+//
+//  * row layout (one transform per thread group): element i at
+//    i + 2*floor(i/16).  With a first radix of 16 and n/R and Ns multiples of
+//    16 in the later stages, the loads j + r*n/R and stores base + r*Ns move
+//    by whole 16-element blocks, so each is base + constant.  The two float2
+//    of padding per 16 keep the stride-18 stores of the first stage and the
+//    unit-stride loads of the next one free of bank conflicts, and keep every
+//    even element 16-byte aligned, so the first stage stores pairs of outputs
+//    with one 16-byte store.
+//  * column layout (NC interleaved transforms): element i of column c at
+//    i*NC + c, unpadded; a thread owns a pair of adjacent columns, so every
+//    shared and global access is a 16-byte vector and the two columns share
+//    one set of twiddles.
+//
+// Stage twiddles come from per-stage tables evaluated at compile time in
+// double precision with an exact argument reduction and rounded to float; a
+// butterfly reads its R-1 twiddles as 16-byte pairs at constant offsets from
+// one base address, the pairs of neighbouring butterflies adjacent.
 #pragma once
 #include <type_traits>
 
@@ -21,11 +37,6 @@ struct Spec {
   static constexpr int S = (R1 == 1) ? 1 : (R2 == 1) ? 2 : (R3 == 1) ? 3 : 4;
   __host__ __device__ static constexpr int r(int i) { return i == 0 ? R0 : i == 1 ? R1 : i == 2 ? R2 : R3; }
   __host__ __device__ static constexpr int ns(int i) { return i == 0 ? 1 : ns(i - 1) * r(i - 1); }
-  __host__ __device__ static constexpr int min_radix() {
-    int m = R0;
-    for (int i = 1; i < S; ++i) m = r(i) < m ? r(i) : m;
-    return m;
-  }
   static_assert(R0 * R1 * R2 * R3 == N_, "radices must multiply to N");
   // the reversed plan: the inverse transform that follows a forward one
   using Rev = typename std::conditional<
@@ -35,157 +46,227 @@ struct Spec {
           typename std::conditional<S == 3, Spec<N_, R2, R1, R0>, Spec<N_, R3, R2, R1, R0>>::type>::type>::type;
 };
 
-// Stage I of plan SP run by T threads over NC interleaved transforms
-// (butterfly g = t + it*T of the stage maps to j = g / NC, c = g % NC).
-template <class SP, int I, int T, int NC = 1>
-struct StageC {
+// stage I of plan SP
+template <class SP, int I>
+struct Stg {
   static constexpr int N = SP::N;
   static constexpr int R = SP::r(I);
   static constexpr int NS = SP::ns(I);
-  static constexpr int NB = N / R;
-  static constexpr int UNIT = N / (NS * R);
-  static constexpr int NCOL = NC;
-  static constexpr int TOTAL = NB * NC;
-  static constexpr int THREADS = T;
-  static constexpr int IT = (TOTAL + T - 1) / T;
-  static constexpr bool EXACT = (TOTAL % T) == 0;
+  static constexpr int NB = N / R;   // butterflies
 };
 
-template <class STG>
-__device__ __forceinline__ bool stage_valid(int t, int it) {
-  if constexpr (STG::EXACT) return true;
-  else return t + it * STG::THREADS < STG::TOTAL;
-}
-template <class STG>
-__device__ __forceinline__ int stage_j(int t, int it) {
-  return (t + it * STG::THREADS) / STG::NCOL;
-}
-template <class STG>
-__device__ __forceinline__ int stage_c(int t, int it) {
-  return (t + it * STG::THREADS) % STG::NCOL;
-}
+// ---------------------------------------------------------------- compile-time twiddles
 
-// V[it][r] = ld(j + r*NB, c)
-template <class STG, class LD>
-__device__ __forceinline__ void stage_load(int t, const LD& ld, float2 (&V)[STG::IT][STG::R]) {
-#pragma unroll
-  for (int it = 0; it < STG::IT; ++it) {
-    if (!stage_valid<STG>(t, it)) continue;
-    const int j = stage_j<STG>(t, it), c = stage_c<STG>(t, it);
-#pragma unroll
-    for (int r = 0; r < STG::R; ++r) V[it][r] = ld(j + r * STG::NB, c);
+// Series for |x| <= pi/4; a term is dropped once it is below 1e-100, so no
+// step underflows (constant evaluation rejects subnormal results).
+__host__ __device__ constexpr double ce_sin_small(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 16; ++k) {
+    term *= -x * x / double((2 * k) * (2 * k + 1));
+    if (term < 1e-100 && term > -1e-100) break;
+    sum += term;
   }
+  return sum;
 }
-
-// twiddle the inputs and take the length-R DFT of every butterfly held
-template <class STG, bool INV>
-__device__ __forceinline__ void stage_compute(int t, const float2* __restrict__ tw, float2 (&V)[STG::IT][STG::R]) {
-#pragma unroll
-  for (int it = 0; it < STG::IT; ++it) {
-    if (!stage_valid<STG>(t, it)) continue;
-    if constexpr (STG::NS > 1) {
-      const int k = stage_j<STG>(t, it) % STG::NS;
-      twiddle_inputs<STG::R, INV>(V[it], k, STG::UNIT, tw);
-    }
-    Dft<STG::R, INV>::run(V[it]);
+__host__ __device__ constexpr double ce_cos_small(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 16; ++k) {
+    term *= -x * x / double((2 * k - 1) * (2 * k));
+    if (term < 1e-100 && term > -1e-100) break;
+    sum += term;
   }
+  return sum;
 }
 
-// output index of element r of butterfly j
-template <class STG>
-__device__ __forceinline__ int stage_out(int j, int r) {
-  if constexpr (STG::NS == 1) {
-    return j * STG::R + r;
-  } else {
-    const int k = j % STG::NS;
-    return (j - k) * STG::R + k + r * STG::NS;
-  }
-}
-
-// st(out_index, c, value) for every output held
-template <class STG, class ST>
-__device__ __forceinline__ void stage_store(int t, const ST& st, float2 (&V)[STG::IT][STG::R]) {
-#pragma unroll
-  for (int it = 0; it < STG::IT; ++it) {
-    if (!stage_valid<STG>(t, it)) continue;
-    const int j = stage_j<STG>(t, it), c = stage_c<STG>(t, it);
-#pragma unroll
-    for (int r = 0; r < STG::R; ++r) st(stage_out<STG>(j, r), c, V[it][r]);
-  }
-}
-
-// Out-of-place stage, one butterfly at a time (few registers): ld -> st.
-template <class STG, bool INV, class LD, class ST>
-__device__ __forceinline__ void stage_stream(int t, const float2* __restrict__ tw, const LD& ld, const ST& st) {
-#pragma unroll
-  for (int it = 0; it < STG::IT; ++it) {
-    if (!stage_valid<STG>(t, it)) continue;
-    const int j = stage_j<STG>(t, it), c = stage_c<STG>(t, it);
-    float2 v[STG::R];
-#pragma unroll
-    for (int r = 0; r < STG::R; ++r) v[r] = ld(j + r * STG::NB, c);
-    if constexpr (STG::NS > 1) twiddle_inputs<STG::R, INV>(v, j % STG::NS, STG::UNIT, tw);
-    Dft<STG::R, INV>::run(v);
-#pragma unroll
-    for (int r = 0; r < STG::R; ++r) st(stage_out<STG>(j, r), c, v[r]);
-  }
-}
-
-// ---------------------------------------------------------------- shared-memory accessors
-
-// row layout: element i of the transform at p[i + (i >> 4)]
-struct RowLd {
-  const float2* p;
-  __device__ __forceinline__ float2 operator()(int i, int) const { return p[rpad(i)]; }
+struct CeCosSin {
+  double c, s;
 };
-struct RowSt {
-  float2* p;
-  __device__ __forceinline__ void operator()(int i, int, float2 v) const { p[rpad(i)] = v; }
-};
-// column layout: element i of column c at p[rpad(i*NC + c)]; the padding (one
-// float2 per 16) spreads the stride-R*NC stores of the early stages over the banks
-template <int NC>
-struct ColLd {
-  const float2* p;
-  __device__ __forceinline__ float2 operator()(int i, int c) const { return p[rpad(i * NC + c)]; }
-};
-template <int NC>
-struct ColSt {
-  float2* p;
-  __device__ __forceinline__ void operator()(int i, int c, float2 v) const { p[rpad(i * NC + c)] = v; }
-};
-__host__ __device__ constexpr int col_smem_len(int n, int nc) { return row_smem_len(n * nc); }
+// cos and sin of 2*pi*m/n, reduced exactly in integers to an angle pi*p/q in
+// [0, pi/4] (quadrant and octant symmetries), so multiples of pi/4 are exact.
+__host__ __device__ constexpr CeCosSin ce_cossin2pi(long m, long n) {
+  long p = ((m % n) + n) % n * 2, q = n;        // angle pi*p/q, p in [0, 2q)
+  double sgs = 1.0, sgc = 1.0;
+  if (p > q) {                                  // (pi, 2pi): sin(2pi - a) = -sin a
+    p = 2 * q - p;
+    sgs = -1.0;
+  }
+  if (2 * p > q) {                              // (pi/2, pi]: cos(pi - a) = -cos a
+    p = q - p;
+    sgc = -1.0;
+  }
+  bool swap = false;
+  if (4 * p > q) {                              // (pi/4, pi/2]: cos a = sin(pi/2 - a)
+    p = q - 2 * p;
+    q = 2 * q;
+    swap = true;
+  }
+  const double x = 3.14159265358979323846264338327950288 * double(p) / double(q);
+  const double c = ce_cos_small(x), s = ce_sin_small(x);
+  return CeCosSin{sgc * (swap ? s : c), sgs * (swap ? c : s)};
+}
 
-// Stages I0 .. I1-1 of SP, ping-pong between a and b (row layout), one
-// barrier per stage.  Returns the buffer holding the result.
-template <class SP, int I, int I1, int T, bool INV>
-struct RowStagesPP {
-  __device__ __forceinline__ static float2* run(float2* a, float2* b, int t, const float2* __restrict__ tw) {
-    if constexpr (I < I1) {
-      using STG = StageC<SP, I, T>;
-      stage_stream<STG, INV>(t, tw, RowLd{a}, RowSt{b});
-      __syncthreads();
-      return RowStagesPP<SP, I + 1, I1, T, INV>::run(b, a, t, tw);
-    } else {
-      return a;
+// Twiddles of one stage, w_{Ns*R}^{r*k} (forward, w = exp(-2 pi i / n)) for
+// k < Ns, 1 <= r < R, in pairs: entry (m, k) = (w^{(2m+1)k}, w^{(2m+2)k}) as
+// one float4 at v[4*(m*Ns + k)], m < RP/2 (RP = R - 1 rounded up to even;
+// a pair past r = R - 1 is zero).  Consecutive k are adjacent, so the
+// threads of a warp, which hold consecutive k, read whole cache lines.
+template <int R, int NS>
+struct TwTab {
+  static constexpr int RP = (R & 1) ? R - 1 : R;
+  alignas(16) float v[2 * NS * RP];
+};
+template <int R, int NS>
+constexpr TwTab<R, NS> make_twtab() {
+  TwTab<R, NS> t{};
+  for (int m = 0; m < TwTab<R, NS>::RP / 2; ++m)
+    for (int k = 0; k < NS; ++k)
+      for (int h = 0; h < 2; ++h) {
+        const int r = 2 * m + 1 + h;
+        if (r >= R) continue;
+        const CeCosSin w = ce_cossin2pi((long)r * k, (long)NS * R);
+        t.v[4 * (m * NS + k) + 2 * h] = float(w.c);
+        t.v[4 * (m * NS + k) + 2 * h + 1] = float(-w.s);
+      }
+  return t;
+}
+template <int R, int NS>
+__device__ constexpr TwTab<R, NS> kStageTw = make_twtab<R, NS>();
+
+template <bool INV>
+__device__ __forceinline__ float2 tw_mul(float2 v, float wx, float wy) {
+  return INV ? make_float2(v.x * wx + v.y * wy, v.y * wx - v.x * wy)
+             : make_float2(v.x * wx - v.y * wy, v.x * wy + v.y * wx);
+}
+
+// v[n][r] *= w_{Ns*R}^{r*k} (conjugate for INV) for the NV transforms of one
+// butterfly position (they share k); nothing for Ns = 1.
+template <int R, int NS, bool INV, int NV>
+__device__ __forceinline__ void twiddle_tab(float2 (&v)[NV][R], int k) {
+  if constexpr (NS > 1) {
+    constexpr int RP = TwTab<R, NS>::RP;
+    const float4* p = reinterpret_cast<const float4*>(kStageTw<R, NS>.v) + k;
+#pragma unroll
+    for (int m = 0; m < RP / 2; ++m) {
+      const float4 w = __ldg(p + m * NS);
+      const int r = 2 * m + 1;
+#pragma unroll
+      for (int n = 0; n < NV; ++n) v[n][r] = tw_mul<INV>(v[n][r], w.x, w.y);
+      if (r + 1 < R) {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) v[n][r + 1] = tw_mul<INV>(v[n][r + 1], w.z, w.w);
+      }
     }
   }
+}
+
+// ---------------------------------------------------------------- row layout
+
+__host__ __device__ constexpr int rp2(int i) { return i + 2 * (i >> 4); }
+__host__ __device__ constexpr int row_len2(int n) { return n + n / 8; }
+
+// Stage 0 output store of a radix-16 first stage (Ns = 1): outputs j*16 + r at
+// 18*j + r, as eight 16-byte pairs.
+__device__ __forceinline__ void row_store16(float2* out, int j, const float2 (&v)[16]) {
+  float4* d = reinterpret_cast<float4*>(out + 18 * j);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) d[m] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+}
+
+// Stage I (>= 1) of row plan SP on one transform, T threads (thread t),
+// in -> out, both in the row layout.
+template <class SP, int I, int T, bool INV>
+__device__ __forceinline__ void row_stage(const float2* __restrict__ in, float2* __restrict__ out, int t) {
+  using G = Stg<SP, I>;
+  static_assert(G::NB % 16 == 0 && G::NS % 16 == 0 && T % 16 == 0, "row stages need 16-element blocks");
+  constexpr int IT = (G::NB + T - 1) / T;
+  constexpr int LB = G::NB / 16 * 18, LS = G::NS / 16 * 18;
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = t + it * T;
+    if (G::NB % T != 0 && j >= G::NB) break;
+    float2 v[1][G::R];
+    const float2* src = in + rp2(j);
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) v[0][r] = src[r * LB];
+    const int k = (G::NB == G::NS) ? j : j % G::NS;
+    twiddle_tab<G::R, G::NS, INV, 1>(v, k);
+    Dft<G::R, INV>::run(v[0]);
+    float2* dst = out + rp2((j - k) * G::R + k);
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) dst[r * LS] = v[0][r];
+  }
+}
+
+// Last stage of row plan SP (Ns = n/R, one butterfly per thread, t < n/R):
+// outputs x = t + r*Ns stay in registers.
+template <class SP, int T, bool INV>
+__device__ __forceinline__ void row_stage_last(const float2* __restrict__ in, int t,
+                                               float2 (&v)[1][Stg<SP, SP::S - 1>::R]) {
+  using G = Stg<SP, SP::S - 1>;
+  static_assert(G::NB == G::NS && G::NB <= T && G::NB % 16 == 0, "last stage: one butterfly per thread");
+  constexpr int LB = G::NB / 16 * 18;
+  const float2* src = in + rp2(t);
+#pragma unroll
+  for (int r = 0; r < G::R; ++r) v[0][r] = src[r * LB];
+  twiddle_tab<G::R, G::NS, INV, 1>(v, t);
+  Dft<G::R, INV>::run(v[0]);
+}
+
+// ---------------------------------------------------------------- column layout
+
+// Threads -> (butterfly row j, column pair cp): cp = t % NP, j = t / NP + it * (T / NP).
+template <int NC, int T>
+struct ColMap {
+  static constexpr int NP = NC / 2;
+  static constexpr int TJ = T / NP;
+  static_assert(NC % 2 == 0 && T % NP == 0, "a thread owns a pair of columns");
 };
 
-// Stages I .. I1-1 of SP in place (column layout): load all, barrier,
-// transform and store, barrier.
+__device__ __forceinline__ void split2(float4 q, float2& a, float2& b) {
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ float4 join2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// In-place middle stage I of column plan SP (NC columns, T threads): load
+// everything, barrier, transform, store, barrier.
+template <class SP, int I, int T, int NC, bool INV>
+__device__ __forceinline__ void col_stage_ip(float4* sm4, int t) {
+  using G = Stg<SP, I>;
+  using M = ColMap<NC, T>;
+  constexpr int IT = (G::NB + M::TJ - 1) / M::TJ;
+  const int cp = t % M::NP, j0 = t / M::NP;
+  float2 v[IT][2][G::R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * M::TJ;
+    if (G::NB % M::TJ != 0 && j >= G::NB) continue;
+    const float4* src = sm4 + j * M::NP + cp;
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) split2(src[r * G::NB * M::NP], v[it][0][r], v[it][1][r]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * M::TJ;
+    if (G::NB % M::TJ != 0 && j >= G::NB) continue;
+    const int k = j % G::NS;
+    twiddle_tab<G::R, G::NS, INV, 2>(v[it], k);
+    Dft<G::R, INV>::run(v[it][0]);
+    Dft<G::R, INV>::run(v[it][1]);
+    float4* dst = sm4 + ((j - k) * G::R + k) * M::NP + cp;
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) dst[r * G::NS * M::NP] = join2(v[it][0][r], v[it][1][r]);
+  }
+  __syncthreads();
+}
+
 template <class SP, int I, int I1, int T, int NC, bool INV>
-struct ColStagesIP {
-  __device__ __forceinline__ static void run(float2* p, int t, const float2* __restrict__ tw) {
+struct ColStages {
+  __device__ __forceinline__ static void run(float4* sm4, int t) {
     if constexpr (I < I1) {
-      using STG = StageC<SP, I, T, NC>;
-      float2 V[STG::IT][STG::R];
-      stage_load<STG>(t, ColLd<NC>{p}, V);
-      __syncthreads();
-      stage_compute<STG, INV>(t, tw, V);
-      stage_store<STG>(t, ColSt<NC>{p}, V);
-      __syncthreads();
-      ColStagesIP<SP, I + 1, I1, T, NC, INV>::run(p, t, tw);
+      col_stage_ip<SP, I, T, NC, INV>(sm4, t);
+      ColStages<SP, I + 1, I1, T, NC, INV>::run(sm4, t);
     }
   }
 };

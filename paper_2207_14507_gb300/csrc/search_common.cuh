@@ -165,25 +165,29 @@ __host__ __device__ constexpr size_t pad_frame_elems(int H, int W) { return (siz
 __host__ __device__ constexpr size_t pad_origin(int W) { return (size_t)(W + 3) + 1; }
 
 // bilinear<DT> on the zero-bordered layout, W a compile-time constant, `fr`
-// pointing at pixel (0, 0).  The sample point is clamped to [-1, W] x [-1, H]:
-// inside that box the taps and weights are those of bilinear<DT> (a tap in
-// the border reads 0); outside it every tap of bilinear<DT> is outside the
-// frame, and here the clamped point puts weight 1 on a border zero and
-// weight 0 on the rest.  So the value is the same, with no predicate: one
-// index, four loads at fixed offsets.
-template <int DT, int W>
+// pointing at pixel (0, 0).  With CLAMP the sample point is clamped to
+// [-1, W] x [-1, H]: inside that box the taps and weights are those of
+// bilinear<DT> (a tap in the border reads 0); outside it every tap of
+// bilinear<DT> is outside the frame, and the clamped point puts weight 1 on a
+// border zero and weight 0 on the rest.  So the value is the same, with no
+// predicate: one index, four loads at fixed offsets.  Without CLAMP the
+// caller guarantees the point is in the box.  The tap index fy0*P + fx0 is
+// formed in float, where it is exact (|value| < 2^24 for the frame sizes here).
+template <int DT, int W, bool CLAMP = true>
 __device__ __forceinline__ float bilinear_pad(const typename StoreT<DT>::type* __restrict__ fr, int H, float qx,
                                               float qy) {
   using S = StoreT<DT>;
   constexpr int P = pad_pitch(W);
-  qx = fminf(fmaxf(qx, -1.f), (float)W);
-  qy = fminf(fmaxf(qy, -1.f), (float)H);
+  if constexpr (CLAMP) {
+    qx = fminf(fmaxf(qx, -1.f), (float)W);
+    qy = fminf(fmaxf(qy, -1.f), (float)H);
+  }
   const float fx0 = floorf(qx), fy0 = floorf(qy);
   const float fx = qx - fx0, fy = qy - fy0;
-  const auto* p = fr + ((int)fy0 * P + (int)fx0);
+  const auto* p = fr + __float2int_rn(fmaf(fy0, (float)P, fx0));
   const float v00 = S::ld(p), v01 = S::ld(p + 1), v10 = S::ld(p + P), v11 = S::ld(p + P + 1);
-  const float gx = 1.f - fx, gy = 1.f - fy;
-  return gy * (gx * v00 + fx * v01) + fy * (gx * v10 + fx * v11);
+  const float top = fmaf(fx, v01 - v00, v00), bot = fmaf(fx, v11 - v10, v10);
+  return fmaf(fy, bot - top, top);
 }
 
 // Loads of data that other blocks of the same launch may have written (the

@@ -1,9 +1,11 @@
 // search_fixed.cu -- compile-time-planned kernels of the grid search for the
 // frame sizes of the workloads (256x256, 1280x720, 1920x1080, 3840x2160).
 //
-// Same arithmetic as the generic kernels in search.cu (the same Stockham
-// stages and radix-R DFTs, the same packed half spectrum), with the plan known
-// at compile time and fewer shared-memory passes:
+// Same arithmetic as the generic kernels in search.cu (Stockham stages,
+// radix-R DFTs in registers, the same packed half spectrum), with the plan,
+// the frame size and the thread count known at compile time, so that every
+// address is a per-thread base plus a constant (fft_fixed.cuh), and with
+// fewer shared-memory passes:
 //   row_forward_body : stage 0 of the row FFT takes its inputs straight from
 //                      the bilinear warp (no shared-memory fill);
 //   col_body         : stage 0 loads the strip from global memory; the last
@@ -11,7 +13,8 @@
 //                      inverse stage stay in registers (the inverse plan is
 //                      the forward plan reversed, so every thread already
 //                      holds its inputs); the last inverse stage stores to
-//                      global memory; stages in between run in place;
+//                      global memory; stages in between run in place; each
+//                      thread works on a pair of adjacent columns;
 //   row_inverse_body : stage 0 rebuilds the two rows' full spectrum straight
 //                      from global memory; the last stage's outputs are
 //                      reduced to the row statistics from registers.
@@ -30,76 +33,60 @@ namespace prnu {
 namespace {
 
 // Loads of spectra: L2-only (CG) inside the persistent kernel, whose blocks
-// read what other blocks of the same launch wrote into reused slots; plain
-// (L1-cached) in the wave kernels, where the row inverse reads every packed
-// element twice (for bins k and W - k).
+// read what other blocks of the same launch wrote into reused slots; through
+// the read-only path in the wave kernels, where the spectrum was written by an
+// earlier launch.
 template <bool CG>
 __device__ __forceinline__ float2 ld_spec(const float2* p) {
-  if constexpr (CG) return ld_l2(p);
-  else return *p;
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
 }
-
-// full spectrum element i of z = G_a + i G_b from two packed rows
 template <bool CG>
-struct FullRowLd {
-  const float2* pa;
-  const float2* pb;
-  int W, Wh;
-  __device__ __forceinline__ float2 operator()(int i, int) const {
-    if (i == 0) {
-      const float2 A = ld_spec<CG>(pa), B = ld_spec<CG>(pb);
-      return make_float2(A.x, B.x);
-    }
-    if (i == Wh) {
-      const float2 A = ld_spec<CG>(pa), B = ld_spec<CG>(pb);
-      return make_float2(A.y, B.y);
-    }
-    if (i < Wh) {
-      const float2 A = ld_spec<CG>(pa + i), B = ld_spec<CG>(pb + i);
-      return make_float2(A.x - B.y, A.y + B.x);
-    }
-    const int k = W - i;
-    const float2 A = ld_spec<CG>(pa + k), B = ld_spec<CG>(pb + k);
-    return make_float2(A.x + B.y, B.x - A.y);
-  }
-};
-
-template <bool CG>
-struct StripLd {
-  const float2* Z;
-  int Wh, c0;
-  __device__ __forceinline__ float2 operator()(int i, int c) const {
-    const int col = c0 + c;
-    return col < Wh ? ld_spec<CG>(Z + (size_t)i * Wh + col) : make_float2(0.f, 0.f);
-  }
-};
-struct StripSt {
-  float2* Z;
-  int Wh, c0;
-  __device__ __forceinline__ void operator()(int i, int c, float2 v) const {
-    const int col = c0 + c;
-    if (col < Wh) Z[(size_t)i * Wh + col] = v;
-  }
-};
+__device__ __forceinline__ float4 ld_spec4(const float4* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
 
 template <int W>
 __host__ __device__ constexpr size_t row_fx_smem(int ppb) {
-  return (size_t)ppb * 2 * row_smem_len(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
+  return (size_t)ppb * 2 * row_len2(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
 }
+__host__ __device__ constexpr size_t col_fx_smem(int H, int nc) { return (size_t)H * nc * sizeof(float2); }
 
 // ---------------------------------------------------------------- row forward
+
+// The 16 warped samples x = t + r*NB0 (r < 16) of output rows y0 and y0 + 1,
+// packed as one complex row (row y0 real, row y0 + 1 imaginary).  CLAMP
+// false is only taken when every sample point of the row pair lies in
+// [-1, W] x [-1, H], where the clamp of bilinear_pad is the identity.
+template <int DT, int W, int NB0, bool CLAMP>
+__device__ __forceinline__ void warp_row16(const typename StoreT<DT>::type* __restrict__ fr, int H, const WorkItem& it,
+                                           float dxj, float bx0, float by0, float bx1, float by1, float2 (&v)[16]) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const float dx = dxj + (float)(r * NB0);
+    v[r].x = bilinear_pad<DT, W, CLAMP>(fr, H, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
+    v[r].y = bilinear_pad<DT, W, CLAMP>(fr, H, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
+  }
+}
+
+__device__ __forceinline__ bool in_box(float qx, float qy, int W, int H) {
+  return qx >= -1.f && qx <= (float)W && qy >= -1.f && qy <= (float)H;
+}
 
 // Row pairs bx*PPB .. bx*PPB+PPB-1 of candidate `is` (item slot), spectrum
 // written to workspace slot `ws`.  Block = PPB groups of T threads.
 template <int DT, class SP, int T, int PPB>
 __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
-  constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
+  constexpr int W = SP::N, Wh = W / 2, L = row_len2(W);
+  using S0 = Stg<SP, 0>;
+  static_assert(S0::R == 16 && SP::S >= 2 && SP::S <= 3, "row plans: radix 16 first, two or three stages");
+  constexpr int NB0 = S0::NB;
   const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
-  const float2* tw = a.tw + a.prow.tw_off;
   const WorkItem it = item_of(a, is);
   size_t base;
   const void* Rf = frame_of(a, it.frame, &base);
@@ -109,34 +96,49 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
   const float dy0 = (float)y0 - cy, dy1 = dy0 + 1.f;
   const float bx0 = fmaf(it.a12, dy0, cx), by0 = fmaf(it.a22, dy0, cy);
   const float bx1 = fmaf(it.a12, dy1, cx), by1 = fmaf(it.a22, dy1, cy);
-  using S0 = StageC<SP, 0, T>;
-#pragma unroll
-  for (int k = 0; k < S0::IT; ++k) {
-    if (!stage_valid<S0>(t, k)) continue;
-    const int j = t + k * T;
-    float2 v[S0::R];
-#pragma unroll
-    for (int r = 0; r < S0::R; ++r) {
-      const float dx = (float)(j + r * S0::NB) - cx;
-      v[r].x = bilinear_pad<DT, W>(fr, H, fmaf(it.a11, dx, bx0), fmaf(it.a21, dx, by0));
-      v[r].y = bilinear_pad<DT, W>(fr, H, fmaf(it.a11, dx, bx1), fmaf(it.a21, dx, by1));
-    }
-    Dft<S0::R, false>::run(v);
-#pragma unroll
-    for (int r = 0; r < S0::R; ++r) A[rpad(j * S0::R + r)] = v[r];
+  // The sample coordinates are monotone in x, so the ends of the two rows
+  // bound them all (uniform over the thread group).
+  const float dxl = -cx, dxr = (float)(W - 1) - cx;
+  const bool inside = in_box(fmaf(it.a11, dxl, bx0), fmaf(it.a21, dxl, by0), W, H) &&
+                      in_box(fmaf(it.a11, dxr, bx0), fmaf(it.a21, dxr, by0), W, H) &&
+                      in_box(fmaf(it.a11, dxl, bx1), fmaf(it.a21, dxl, by1), W, H) &&
+                      in_box(fmaf(it.a11, dxr, bx1), fmaf(it.a21, dxr, by1), W, H);
+  if (t < NB0) {
+    float2 v[16];
+    const float dxj = (float)t - cx;
+    if (inside) warp_row16<DT, W, NB0, false>(fr, H, it, dxj, bx0, by0, bx1, by1, v);
+    else warp_row16<DT, W, NB0, true>(fr, H, it, dxj, bx0, by0, bx1, by1, v);
+    Dft<16, false>::run(v);
+    row_store16(A, t, v);
   }
   __syncthreads();
-  const float2* res = RowStagesPP<SP, 1, SP::S, T, false>::run(A, B, t, tw);
+  const float2* res = B;
+  row_stage<SP, 1, T, false>(A, B, t);
+  __syncthreads();
+  if constexpr (SP::S == 3) {
+    row_stage<SP, 2, T, false>(B, A, t);
+    __syncthreads();
+    res = A;
+  }
+  // split z = G_a + i G_b into the two rows' half spectra (packed: bin 0
+  // holds (DC, Nyquist))
   float2* o0 = a.spec + ((size_t)ws * H + y0) * Wh;
   float2* o1 = o0 + Wh;
-  for (int k = t; k < Wh; k += T) {
+  constexpr int MI = (Wh + T - 1) / T;
+  const float2* rk = res + rp2(t);
+  const float2* rm = res - t + 2 * ((-t) >> 4);   // + rp2(X) gives rp2(X - t) for X = 0 mod 16
+#pragma unroll
+  for (int m = 0; m < MI; ++m) {
+    const int k = t + m * T;
+    if (Wh % T != 0 && k >= Wh) break;
+    const float2 zk = rk[m * (T / 16 * 18)];
     float2 P, Q;
-    if (k == 0) {
-      const float2 z0 = res[rpad(0)], zn = res[rpad(Wh)];
-      P = make_float2(z0.x, zn.x);
-      Q = make_float2(z0.y, zn.y);
+    if (m == 0 && t == 0) {
+      const float2 zn = res[rp2(Wh)];
+      P = make_float2(zk.x, zn.x);
+      Q = make_float2(zk.y, zn.y);
     } else {
-      const float2 zk = res[rpad(k)], zm = res[rpad(W - k)];
+      const float2 zm = rm[rp2(W - m * T)];
       P = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
       Q = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
     }
@@ -147,135 +149,251 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
 
 // ---------------------------------------------------------------- column pass
 
-// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
-template <class SP, int NC, int T, bool CG = false, bool PF = true>
-__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm, int tx) {
-  constexpr int H = SP::N;
-  using IS = typename SP::Rev;
-  const int t = threadIdx.x;   // == tx; the builtin gives this body the faster schedule (measured)
-  const int Wh = a.W >> 1;
-  const int c0 = bx * NC;
-  float2* Z = a.spec + (size_t)ws * H * Wh;
-  const float2* tw = a.tw + a.pcol.tw_off;
-  const WorkItem wi = item_of(a, is);
-  const FpDesc fp = a.fps[wi.fp];
-  using FL = StageC<SP, SP::S - 1, T, NC>;
-  using I0 = StageC<IS, 0, T, NC>;
-
-  // The fingerprint bins this thread multiplies after the last forward stage
-  // are known now: load them first, so that their latency hides behind the
-  // forward stages (when they fit in a few registers and PF allows it).
-  constexpr bool kPrefetch = PF && FL::IT * FL::R <= 16;
-  float2 Sp[kPrefetch ? FL::IT : 1][kPrefetch ? FL::R : 1];
-  if constexpr (kPrefetch) {
+// The fingerprint bins (i, col0) and (i, col0 + 1) for i = j + r*NS.
+template <int R, int NS, int Wh>
+__device__ __forceinline__ void load_fp_pair(const FpDesc& fp, int j, int col0, float2 (&s)[2][R]) {
+  const size_t b = ((size_t)j * Wh + col0) / 2;
+  if (fp.dtype == kF32) {
+    const float4* p = reinterpret_cast<const float4*>(fp.spec) + b;
 #pragma unroll
-    for (int k = 0; k < FL::IT; ++k) {
-      if (!stage_valid<FL>(t, k)) continue;
-      const int j = stage_j<FL>(t, k), col = c0 + stage_c<FL>(t, k);
+    for (int r = 0; r < R; ++r) split2(__ldg(p + (size_t)r * NS * (Wh / 2)), s[0][r], s[1][r]);
+  } else {
+    const float2* p = reinterpret_cast<const float2*>(fp.spec) + b;   // two __half2
 #pragma unroll
-      for (int r = 0; r < FL::R; ++r)
-        Sp[k][r] = col < Wh ? load_spec(fp.spec, fp.dtype, (size_t)(j + r * FL::NS) * Wh + col)
-                            : make_float2(0.f, 0.f);
+    for (int r = 0; r < R; ++r) {
+      const float2 u = __ldg(p + (size_t)r * NS * (Wh / 2));
+      s[0][r] = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+      s[1][r] = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
     }
   }
+}
 
-  stage_stream<StageC<SP, 0, T, NC>, false>(t, tw, StripLd<CG>{Z, Wh, c0}, ColSt<NC>{sm});
+// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
+template <class SP, int W, int NC, int T, bool CG = false>
+__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm) {
+  constexpr int H = SP::N, Wh = W / 2;
+  using IS = typename SP::Rev;
+  using M = ColMap<NC, T>;
+  constexpr int NP = M::NP, TJ = M::TJ;
+  static_assert(Wh % NC == 0, "strips tile the half spectrum");
+  const int t = threadIdx.x;
+  const int c0 = bx * NC;
+  const int cp = t % NP, j0 = t / NP;
+  const int col0 = c0 + 2 * cp;
+  float2* Z = a.spec + (size_t)ws * H * Wh;
+  float4* sm4 = reinterpret_cast<float4*>(sm);
+  const WorkItem wi = item_of(a, is);
+  const FpDesc fp = a.fps[wi.fp];
+
+  {  // forward stage 0 from global memory
+    using G = Stg<SP, 0>;
+    constexpr int IT = (G::NB + TJ - 1) / TJ;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int j = j0 + it * TJ;
+      if (G::NB % TJ != 0 && j >= G::NB) continue;
+      float2 v[2][G::R];
+      const float4* src = reinterpret_cast<const float4*>(Z + (size_t)j * Wh + col0);
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) split2(ld_spec4<CG>(src + (size_t)r * G::NB * (Wh / 2)), v[0][r], v[1][r]);
+      Dft<G::R, false>::run(v[0]);
+      Dft<G::R, false>::run(v[1]);
+      float4* dst = sm4 + j * G::R * NP + cp;
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) dst[r * NP] = join2(v[0][r], v[1][r]);
+    }
+  }
   __syncthreads();
-  ColStagesIP<SP, 1, SP::S - 1, T, NC, false>::run(sm, t, tw);
+  ColStages<SP, 1, SP::S - 1, T, NC, false>::run(sm4, t);
+
+  // last forward stage -> spectrum product -> first inverse stage, in registers
+  using FL = Stg<SP, SP::S - 1>;
+  using I0 = Stg<IS, 0>;
   static_assert(I0::R == FL::R && I0::NB == FL::NB && FL::NB == FL::NS, "register hand-off needs the reversed plan");
-  float2 V[FL::IT][FL::R];
-  stage_load<FL>(t, ColLd<NC>{sm}, V);
+  constexpr int IT = (FL::NB + TJ - 1) / TJ;
+  float2 v[IT][2][FL::R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * TJ;
+    if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+    const float4* src = sm4 + j * NP + cp;
+#pragma unroll
+    for (int r = 0; r < FL::R; ++r) split2(src[r * FL::NB * NP], v[it][0][r], v[it][1][r]);
+  }
   __syncthreads();
-  stage_compute<FL, false>(t, tw, V);
-  // outputs of the last forward stage: row i = j + r*NS of column c
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * TJ;
+    if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+    twiddle_tab<FL::R, FL::NS, false, 2>(v[it], j);
+    Dft<FL::R, false>::run(v[it][0]);
+    Dft<FL::R, false>::run(v[it][1]);
+  }
+  // thread holds bins i = j + r*NS of columns col0 and col0 + 1
   if (c0 == 0) {
-    // packed column 0 (DC + i*Nyquist): the product needs row H - i as well
+    // packed column 0 (DC + i*Nyquist): the product needs bin H - i as well
+    float2* X0 = sm;   // free: every thread has loaded its inputs
+    if (cp == 0) {
 #pragma unroll
-    for (int k = 0; k < FL::IT; ++k) {
-      if (!stage_valid<FL>(t, k) || stage_c<FL>(t, k) != 0) continue;
-      const int j = stage_j<FL>(t, k);
+      for (int it = 0; it < IT; ++it) {
+        const int j = j0 + it * TJ;
+        if (FL::NB % TJ != 0 && j >= FL::NB) continue;
 #pragma unroll
-      for (int r = 0; r < FL::R; ++r) sm[rpad((j + r * FL::NS) * NC)] = V[k][r];
+        for (int r = 0; r < FL::R; ++r) X0[j + r * FL::NS] = v[it][0][r];
+      }
     }
     __syncthreads();
+    if (cp == 0) {
 #pragma unroll
-    for (int k = 0; k < FL::IT; ++k) {
-      if (!stage_valid<FL>(t, k) || stage_c<FL>(t, k) != 0) continue;
-      const int j = stage_j<FL>(t, k);
+      for (int it = 0; it < IT; ++it) {
+        const int j = j0 + it * TJ;
+        if (FL::NB % TJ != 0 && j >= FL::NB) continue;
 #pragma unroll
-      for (int r = 0; r < FL::R; ++r) {
-        const int i = j + r * FL::NS;
-        const int im = i == 0 ? 0 : H - i;
-        const float2 F = V[k][r], Fm = sm[rpad(im * NC)];
-        const float2 S = load_spec(fp.spec, fp.dtype, (size_t)i * Wh);
-        const float2 Sm = load_spec(fp.spec, fp.dtype, (size_t)im * Wh);
-        const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
-        const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
-        const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
-        const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
-        const float2 p1 = c_mul(c_conj(Aa), Ka), p2 = c_mul(c_conj(Bb), Kb);
-        V[k][r] = make_float2(p1.x - p2.y, p1.y + p2.x);
+        for (int r = 0; r < FL::R; ++r) {
+          const int i = j + r * FL::NS;
+          const int im = i == 0 ? 0 : H - i;
+          const float2 F = v[it][0][r], Fm = X0[im];
+          const float2 S = load_spec(fp.spec, fp.dtype, (size_t)i * Wh);
+          const float2 Sm = load_spec(fp.spec, fp.dtype, (size_t)im * Wh);
+          const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
+          const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
+          const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
+          const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
+          const float2 p1 = c_mul(c_conj(Aa), Ka), p2 = c_mul(c_conj(Bb), Kb);
+          v[it][0][r] = make_float2(p1.x - p2.y, p1.y + p2.x);
+        }
       }
     }
     __syncthreads();
   }
+  const bool col0_done = col0 == 0;
 #pragma unroll
-  for (int k = 0; k < FL::IT; ++k) {
-    if (!stage_valid<FL>(t, k)) continue;
-    const int j = stage_j<FL>(t, k), col = c0 + stage_c<FL>(t, k);
-    if (col == 0 || col >= Wh) continue;
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * TJ;
+    if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+    float2 s[2][FL::R];
+    load_fp_pair<FL::R, FL::NS, Wh>(fp, j, col0, s);
 #pragma unroll
     for (int r = 0; r < FL::R; ++r) {
-      float2 S;
-      if constexpr (kPrefetch) S = Sp[k][r];
-      else S = load_spec(fp.spec, fp.dtype, (size_t)(j + r * FL::NS) * Wh + col);
-      V[k][r] = c_mul(c_conj(V[k][r]), S);
+      if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), s[0][r]);
+      v[it][1][r] = c_mul(c_conj(v[it][1][r]), s[1][r]);
+    }
+    Dft<FL::R, true>::run(v[it][0]);
+    Dft<FL::R, true>::run(v[it][1]);
+    float4* dst = sm4 + j * FL::R * NP + cp;
+#pragma unroll
+    for (int r = 0; r < FL::R; ++r) dst[r * NP] = join2(v[it][0][r], v[it][1][r]);
+  }
+  __syncthreads();
+  ColStages<IS, 1, IS::S - 1, T, NC, true>::run(sm4, t);
+
+  {  // last inverse stage: shared memory -> global memory
+    using G = Stg<IS, IS::S - 1>;
+    static_assert(G::NB == G::NS, "last stage");
+    constexpr int ITL = (G::NB + TJ - 1) / TJ;
+#pragma unroll
+    for (int it = 0; it < ITL; ++it) {
+      const int j = j0 + it * TJ;
+      if (G::NB % TJ != 0 && j >= G::NB) continue;
+      float2 w[2][G::R];
+      const float4* src = sm4 + j * NP + cp;
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) split2(src[r * G::NB * NP], w[0][r], w[1][r]);
+      twiddle_tab<G::R, G::NS, true, 2>(w, j);
+      Dft<G::R, true>::run(w[0]);
+      Dft<G::R, true>::run(w[1]);
+      float4* dst = reinterpret_cast<float4*>(Z + (size_t)j * Wh + col0);
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) dst[(size_t)r * G::NS * (Wh / 2)] = join2(w[0][r], w[1][r]);
     }
   }
-  stage_compute<I0, true>(t, tw, V);
-  stage_store<I0>(t, ColSt<NC>{sm}, V);
-  __syncthreads();
-  ColStagesIP<IS, 1, IS::S - 1, T, NC, true>::run(sm, t, tw);
-  stage_stream<StageC<IS, IS::S - 1, T, NC>, true>(t, tw, ColLd<NC>{sm}, StripSt{Z, Wh, c0});
 }
 
 // ---------------------------------------------------------------- row inverse + statistics
 
+// Inverse row FFT of z = G_a + i G_b, the full spectrum of the packed rows
+// pa and pb (W/2 bins each), by the T threads of one group (thread t) with
+// buffers A and B (row layout).  Afterwards thread t < n/R_last holds the
+// outputs x = t + r*Ns_last of the last stage in v (v.x row a, v.y row b).
+// Holds barriers: every thread of the block calls it.
+template <class SP, int T, bool CG>
+__device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* pb, float2* A, float2* B, int t,
+                                                float2 (&v)[1][Stg<SP, SP::S - 1>::R]) {
+  constexpr int W = SP::N, Wh = W / 2;
+  using S0 = Stg<SP, 0>;
+  static_assert(S0::R == 16 && SP::S >= 2 && SP::S <= 3, "row plans: radix 16 first, two or three stages");
+  constexpr int NB0 = S0::NB;   // bins j + r*NB0: r < 8 below W/2, r >= 8 mirrored
+  if (t < NB0) {
+    float2 u[16];
+    float2 a0 = make_float2(0.f, 0.f), b0 = a0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float2 A_ = ld_spec<CG>(pa + t + r * NB0), B_ = ld_spec<CG>(pb + t + r * NB0);
+      if (r == 0) {
+        a0 = A_;
+        b0 = B_;
+      }
+      u[r] = make_float2(A_.x - B_.y, A_.y + B_.x);
+    }
+    const float2* ma = pa + (W - t);
+    const float2* mb = pb + (W - t);
+#pragma unroll
+    for (int r = 8; r < 16; ++r) {
+      float2 A_, B_;
+      if (r == 8) {   // bin W/2 - t; for t = 0 the Nyquist bin, packed in bin 0
+        const int k8 = t ? Wh - t : 0;
+        A_ = ld_spec<CG>(pa + k8);
+        B_ = ld_spec<CG>(pb + k8);
+      } else {
+        A_ = ld_spec<CG>(ma - r * NB0);
+        B_ = ld_spec<CG>(mb - r * NB0);
+      }
+      u[r] = make_float2(A_.x + B_.y, B_.x - A_.y);
+    }
+    if (t == 0) {   // DC and Nyquist of both rows: (re, im) = (DC, Nyquist) in bin 0
+      u[0] = make_float2(a0.x, b0.x);
+      u[8] = make_float2(a0.y, b0.y);
+    }
+    Dft<16, true>::run(u);
+    row_store16(A, t, u);
+  }
+  __syncthreads();
+  constexpr int NBL = Stg<SP, SP::S - 1>::NB;
+  if constexpr (SP::S == 2) {
+    if (NBL == T || t < NBL) row_stage_last<SP, T, true>(A, t, v);
+  } else {
+    row_stage<SP, 1, T, true>(A, B, t);
+    __syncthreads();
+    if (NBL == T || t < NBL) row_stage_last<SP, T, true>(B, t, v);
+  }
+}
+
 template <class SP, int T, int PPB, bool CG = false>
 __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int bx, float2* smem, int tx) {
-  constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W);
+  constexpr int W = SP::N, Wh = W / 2, L = row_len2(W);
+  using GL = Stg<SP, SP::S - 1>;
+  static_assert(PPB == 1 || T % 32 == 0, "row-pair groups must not share a warp (warp-level reductions)");
   const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
   float2* A = smem + (size_t)grp * 2 * L;
   float2* B = A + L;
   RowRed* red = reinterpret_cast<RowRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
-  const float2* tw = a.tw + a.prow.tw_off;
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
-  stage_stream<StageC<SP, 0, T>, true>(t, tw, FullRowLd<CG>{pa, pa + Wh, W, Wh}, RowSt{A});
-  __syncthreads();
-  const float2* res = RowStagesPP<SP, 1, SP::S - 1, T, true>::run(A, B, t, tw);
-  using SL = StageC<SP, SP::S - 1, T>;
-  static_assert(SL::NB == SL::NS, "last stage writes j + r*NS");
-  static_assert(PPB == 1 || T % 32 == 0, "row-pair groups must not share a warp (warp-level reductions)");
-  float2 V[SL::IT][SL::R];
-  stage_load<SL>(t, RowLd{res}, V);
-  stage_compute<SL, true>(t, tw, V);
+  float2 v[1][GL::R];
+  row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, B, t, v);
   float ma = -INFINITY, mb = -INFINITY;
   int ia = INT_MAX, ib = INT_MAX;
   float sa = 0.f, sb = 0.f;
+  if (GL::NB == T || t < GL::NB) {
 #pragma unroll
-  for (int k = 0; k < SL::IT; ++k) {
-    if (!stage_valid<SL>(t, k)) continue;
-    const int j = stage_j<SL>(t, k);
-#pragma unroll
-    for (int r = 0; r < SL::R; ++r) {
-      const int x = j + r * SL::NS;
-      const float2 v = V[k][r];
-      better_f(ma, ia, v.x, x);
-      better_f(mb, ib, v.y, x);
-      sa = fmaf(v.x, v.x, sa);
-      sb = fmaf(v.y, v.y, sb);
+    for (int r = 0; r < GL::R; ++r) {
+      const int x = t + r * GL::NS;
+      const float2 u = v[0][r];
+      better_f(ma, ia, u.x, x);
+      better_f(mb, ib, u.y, x);
+      sa = fmaf(u.x, u.x, sa);
+      sb = fmaf(u.y, u.y, sb);
     }
   }
   row_stats_warp(ma, ia, mb, ib, sa, sb, t, red);
@@ -287,20 +405,21 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
 
 template <int DT, class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
-  extern __shared__ float2 smem[];
-  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem, threadIdx.x);
+  extern __shared__ float4 smem4[];
+  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4),
+                                   threadIdx.x);
 }
 
-template <class SP, int NC, int T>
-__global__ void __launch_bounds__(T) k_col_fx(PassArgs a) {
-  extern __shared__ float2 smem[];
-  col_body<SP, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, smem, threadIdx.x);
+template <class SP, int W, int NC, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_col_fx(PassArgs a) {
+  extern __shared__ float4 smem4[];
+  col_body<SP, W, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4));
 }
 
 template <class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
-  extern __shared__ float2 smem[];
-  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, smem, threadIdx.x);
+  extern __shared__ float4 smem4[];
+  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
 
 // ---------------------------------------------------------------- persistent kernel
@@ -314,9 +433,9 @@ template <int DT, class SP, int T, int PPB>
 __device__ __forceinline__ void row_forward_task(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
   row_forward_body<DT, SP, T, PPB>(a, is, ws, bx, smem, tx);
 }
-template <class SP, int NC, int T>
-__device__ __forceinline__ void col_task(const PassArgs& a, int is, int ws, int bx, float2* smem, int tx) {
-  col_body<SP, NC, T, true, false>(a, is, ws, bx, smem, tx);   // no prefetch: registers are capped here
+template <class SP, int W, int NC, int T>
+__device__ __forceinline__ void col_task(const PassArgs& a, int is, int ws, int bx, float2* smem) {
+  col_body<SP, W, NC, T, true>(a, is, ws, bx, smem);
 }
 template <class SP, int T, int PPB>
 __device__ __forceinline__ void row_inverse_task(const PassArgs& a, int ws, int bx, float2* smem, int tx) {
@@ -327,7 +446,8 @@ __device__ __forceinline__ void row_inverse_task(const PassArgs& a, int ws, int 
 // inverse row FFT (one row pair per thread group, PPB pairs per round).
 template <class SP, int T, int PPB>
 __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws, float2* smem, int tx) {
-  constexpr int W = SP::N, Wh = W / 2, L = row_smem_len(W), TB = T * PPB;
+  constexpr int W = SP::N, Wh = W / 2, L = row_len2(W), TB = T * PPB;
+  using SL = Stg<SP, SP::S - 1>;
   __shared__ int s_py, s_px, s_np;
   __shared__ float s_peak;
   __shared__ int s_pairs[2 * kHalfWindow + 1];
@@ -336,7 +456,6 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
   const WorkItem it = item_of(a, is);
   const RowStat* st = a.stats + (size_t)ws * H;
   const float2* Z = a.spec + (size_t)ws * H * Wh;
-  const float2* tw = a.tw + a.prow.tw_off;
   WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * 2 * L);
   constexpr int NW = TB / 32;
   const int w = t >> 5;
@@ -372,7 +491,6 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
   double e = 0.0;
   for (int y = t; y < H; y += TB)
     if (cdist(y, py, H) > kHalfWindow) e += ld_l2(st + y).sumsq;
-  using SL = StageC<SP, SP::S - 1, T>;
   for (int r0 = 0; r0 < np; r0 += PPB) {
     const int k = r0 + grp;
     const bool act = k < np;
@@ -380,24 +498,15 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
     float2* A = smem + (size_t)grp * 2 * L;
     float2* B = A + L;
     const float2* pa = Z + (size_t)(2 * p) * Wh;
-    stage_stream<StageC<SP, 0, T>, true>(tg, tw, FullRowLd<true>{pa, pa + Wh, W, Wh}, RowSt{A});
-    __syncthreads();
-    const float2* res = RowStagesPP<SP, 1, SP::S - 1, T, true>::run(A, B, tg, tw);
-    float2 V[SL::IT][SL::R];
-    stage_load<SL>(tg, RowLd{res}, V);
-    stage_compute<SL, true>(tg, tw, V);
-    if (act) {
+    float2 V[1][SL::R];
+    row_inverse_fft<SP, T, true>(pa, pa + Wh, A, B, tg, V);
+    if (act && (SL::NB == T || tg < SL::NB)) {
 #pragma unroll
-      for (int kk = 0; kk < SL::IT; ++kk) {
-        if (!stage_valid<SL>(tg, kk)) continue;
-        const int j = stage_j<SL>(tg, kk);
-#pragma unroll
-        for (int r = 0; r < SL::R; ++r) {
-          const int x = j + r * SL::NS;
-          if (cdist(x, px, W) <= kHalfWindow) continue;
-          if (cdist(2 * p, py, H) <= kHalfWindow) e += (double)V[kk][r].x * V[kk][r].x;
-          if (cdist(2 * p + 1, py, H) <= kHalfWindow) e += (double)V[kk][r].y * V[kk][r].y;
-        }
+      for (int r = 0; r < SL::R; ++r) {
+        const int x = tg + r * SL::NS;
+        if (cdist(x, px, W) <= kHalfWindow) continue;
+        if (cdist(2 * p, py, H) <= kHalfWindow) e += (double)V[0][r].x * V[0][r].x;
+        if (cdist(2 * p + 1, py, H) <= kHalfWindow) e += (double)V[0][r].y * V[0][r].y;
       }
     }
     __syncthreads();
@@ -457,7 +566,8 @@ __device__ __forceinline__ bool wait_count(const int* c, int need, int* err) {
 }
 
 template <int DT, class RS, int RT, int PPB, class CS, int NC>
-__global__ void __launch_bounds__(RT * PPB, 2) k_persist(const __grid_constant__ PassArgs a, const __grid_constant__ PersistArgs p) {
+__global__ void __launch_bounds__(RT * PPB, RT * PPB <= 384 ? 2 : 1)
+    k_persist(const __grid_constant__ PassArgs a, const __grid_constant__ PersistArgs p) {
   constexpr int TB = RT * PPB;
   extern __shared__ float2 smem[];
   __shared__ int s_tk[2], s_ok, s_zero;
@@ -515,7 +625,7 @@ __global__ void __launch_bounds__(RT * PPB, 2) k_persist(const __grid_constant__
       if (ok) {
         const int tx = threadIdx.x + *(volatile int*)&s_zero;   // == threadIdx.x
         if (type == 0) row_forward_task<DT, RS, RT, PPB>(a, g, ws, idx, smem, tx);
-        else if (type == 1) col_task<CS, NC, TB>(a, g, ws, idx, smem, tx);
+        else if (type == 1) col_task<CS, RS::N, NC, TB>(a, g, ws, idx, smem);
         else if (type == 2) row_inverse_task<RS, RT, PPB>(a, ws, idx, smem, tx);
         else finalize_task<RS, RT, PPB>(a, g, ws, smem, tx);
       }
@@ -543,10 +653,11 @@ void allow(K k) {
 template <class RS, int RT, class CS>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
-  template <int NC, int CT>
+  // NC columns per block, CT threads, at least MINB resident blocks per SM
+  template <int NC, int CT, int MINB>
   static FixedCol col() {
-    allow(k_col_fx<CS, NC, CT>);
-    return FixedCol{NC, CT, (size_t)col_smem_len(H, NC) * sizeof(float2), (void*)k_col_fx<CS, NC, CT>};
+    allow(k_col_fx<CS, W, NC, CT, MINB>);
+    return FixedCol{NC, CT, col_fx_smem(H, NC), (void*)k_col_fx<CS, W, NC, CT, MINB>};
   }
   template <int PPB>
   static FixedRow row() {
@@ -573,8 +684,8 @@ struct ShapeDef {
     f.nc = NC;
     f.threads = PRT * PPB;
     const size_t rs = row_fx_smem<W>(PPB);
-    const size_t cs = (size_t)col_smem_len(H, NC) * sizeof(float2);
-    const size_t fs = (size_t)2 * row_smem_len(W) * sizeof(float2) + 32 * sizeof(WarpRed);
+    const size_t cs = col_fx_smem(H, NC);
+    const size_t fs = row_fx_smem<W>(PPB);
     f.smem = std::max(rs, std::max(cs, fs));
     f.fn[kF32] = (void*)k_persist<kF32, RS, PRT, PPB, CS, NC>;
     f.fn[kF16] = (void*)k_persist<kF16, RS, PRT, PPB, CS, NC>;
@@ -601,24 +712,22 @@ struct ShapeDef {
 std::vector<FixedShape> build_registry() {
   std::vector<FixedShape> v;
   {
-    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 12, 10, 9>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 480>(), D::col<8, 480>(), D::col<8, 960>(), D::col<16, 960>()},
-                        D::persist<192, 2, 8>()));
-  }
-  {
-    using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 10, 9, 8>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<8, 384>(), D::col<16, 736>()},
+    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>>;
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 240, 3>(), D::col<8, 480, 1>(), D::col<4, 240, 2>()},
                         D::persist<192, 2, 4>()));
   }
   {
+    using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 180, 4>(), D::col<8, 360, 2>(), D::col<4, 180, 3>()},
+                        D::persist<160, 2, 4>()));
+  }
+  {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 384>(), D::col<4, 736>(), D::col<8, 736>()},
-                        D::persist<384, 1, 2>()));
+    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 360, 2>(), D::col<4, 360, 1>()}, D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<8, 128>(), D::col<16, 256>()}, D::persist<32, 8, 16>()));
+    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4>(), D::col<8, 64, 8>()}, D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
   return v;
@@ -674,3 +783,4 @@ void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape
 }
 
 }  // namespace prnu
+
