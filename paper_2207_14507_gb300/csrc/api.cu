@@ -274,8 +274,9 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   }
   const int slots = persistent ? kPersistSlots : wave;
 
-  if (*c->h_err) {   // a persistent launch of an earlier asynchronous call gave up
+  if (*c->h_err) {   // a persistent launch or a TMA wait of an earlier asynchronous call gave up
     *c->h_err = 0;
+    PRNU_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     throw Error{PRNU_EDEVICE_ABORT, "a device-side wait of an earlier call timed out; its results are invalid"};
   }
   PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->last_done, 0));
@@ -318,6 +319,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.tw = c->d_tw;
   a.prow = prow;
   a.pcol = pcol;
+  a.err = c->d_err;
   a.pairs_per_block = naive ? 2 : tn.ppb;
   a.col_log2 = tn.col_log2;
   a.row_threads = rowT;
@@ -344,6 +346,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
       }
       launch_finalize(a, s, c->launches);
     }
+    if (fs) PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   } else {
     // plain per-candidate path through full-size intermediates
     PRNU_CHECK_ARG(call.rdtype == kF32, "the per-candidate path takes FP32 residuals");
@@ -487,6 +490,8 @@ int prnu_create(prnu_ctx** out, int device, size_t hbm_budget_bytes) {
     PRNU_CUDA_TRY(cudaEventRecord(c->stage_free, 0));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&c->h_err, sizeof(int), cudaHostAllocDefault));
     *c->h_err = 0;
+    c->d_err = reinterpret_cast<int*>(ctx_alloc(c.get(), sizeof(int)));
+    PRNU_CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
     set_kernel_attributes();
     *out = c.release();
   });
@@ -511,6 +516,7 @@ int prnu_destroy(prnu_ctx* ctx) {
                          &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
+    ctx_free(ctx, ctx->d_err, sizeof(int));
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     cudaEventDestroy(ctx->last_done);

@@ -75,6 +75,7 @@ struct PassArgs {
   const WorkItem* const* item_ptrs;
   CandResult* const* result_ptrs;
   const void* const* frame_ptrs;
+  int* err;                   // device flag set when a bounded device-side wait gives up (may be nullptr)
 };
 
 __device__ __forceinline__ WorkItem item_of(const PassArgs& a, int slot) {

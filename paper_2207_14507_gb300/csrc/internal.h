@@ -190,7 +190,8 @@ struct prnu_ctx {
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
       ws_persist, ws_pad;
   size_t tw_bytes = 0;
-  int* h_err = nullptr;           // pinned: error flag of the last persistent launch
+  int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
+  int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up
   std::vector<char> h_stage;      // staging for host->device descriptors
   char* h_pinned = nullptr;
   size_t h_pinned_bytes = 0;

@@ -21,12 +21,16 @@
 // Each body runs either as its own wave kernel (one launch per phase over a
 // wave of candidates) or inside k_persist, one launch that schedules all
 // phases of all candidates of a call as tasks (see below).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "fft_fixed.cuh"
 #include "internal.h"
 #include "search_common.cuh"
 #include "search_fixed.h"
+#include "tma.cuh"
 
 namespace prnu {
 
@@ -168,9 +172,24 @@ __device__ __forceinline__ void load_fp_pair(const FpDesc& fp, int j, int col0, 
   }
 }
 
-// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
-template <class SP, int W, int NC, int T, bool CG = false>
-__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm) {
+// Rows per TMA box of an H-row strip of NC columns (float2): a divisor of H of
+// at most 256 rows whose box size is a multiple of 128 bytes, so that every
+// box lands 128-byte aligned in shared memory.
+__host__ __device__ constexpr int tma_box_rows(int H, int NC) {
+  for (int br = 256; br >= 1; --br)
+    if (H % br == 0 && (br * NC * 8) % 128 == 0) return br;
+  return 0;
+}
+constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait before giving up
+
+// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.  With
+// TMA the strip comes into shared memory by tile copies through `map` (the
+// workspace spectra as a [slots*H][W] float tensor) and leaves the same way;
+// otherwise every thread loads and stores its own elements.  A TMA wait that
+// runs out raises a.err and abandons the candidate.
+template <class SP, int W, int NC, int T, bool CG = false, bool TMA = false>
+__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
+                                         const CUtensorMap* map = nullptr) {
   constexpr int H = SP::N, Wh = W / 2;
   using IS = typename SP::Rev;
   using M = ColMap<NC, T>;
@@ -185,7 +204,31 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   const WorkItem wi = item_of(a, is);
   const FpDesc fp = a.fps[wi.fp];
 
-  {  // forward stage 0 from global memory
+  constexpr int BR = tma_box_rows(H, NC);
+  __shared__ uint64_t s_bar;
+  if constexpr (TMA) {
+    static_assert(BR > 0, "no TMA box for this strip");
+    if (t == 0) {
+      mbar_init(&s_bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+      mbar_expect_tx(&s_bar, H * NC * 8);
+#pragma unroll 1
+      for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, ws * H + b * BR, &s_bar);
+    }
+    const bool ok = mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        if (a.err) atomicExch(a.err, 1);
+        mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);   // let the copy land before the block leaves
+      }
+      __syncthreads();
+      return;
+    }
+    ColStages<SP, 0, SP::S - 1, T, NC, false>::run(sm4, t);
+  } else {  // forward stage 0 from global memory
     using G = Stg<SP, 0>;
     constexpr int IT = (G::NB + TJ - 1) / TJ;
 #pragma unroll
@@ -202,9 +245,9 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
 #pragma unroll
       for (int r = 0; r < G::R; ++r) dst[r * NP] = join2(v[0][r], v[1][r]);
     }
+    __syncthreads();
+    ColStages<SP, 1, SP::S - 1, T, NC, false>::run(sm4, t);
   }
-  __syncthreads();
-  ColStages<SP, 1, SP::S - 1, T, NC, false>::run(sm4, t);
 
   // last forward stage -> spectrum product -> first inverse stage, in registers
   using FL = Stg<SP, SP::S - 1>;
@@ -302,9 +345,27 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
       twiddle_tab<G::R, G::NS, true, 2>(w, j);
       Dft<G::R, true>::run(w[0]);
       Dft<G::R, true>::run(w[1]);
-      float4* dst = reinterpret_cast<float4*>(Z + (size_t)j * Wh + col0);
+      if constexpr (TMA) {
+        // outputs j + r*Ns sit where this thread's inputs were: no barrier needed
+        float4* dst = sm4 + j * NP + cp;
 #pragma unroll
-      for (int r = 0; r < G::R; ++r) dst[(size_t)r * G::NS * (Wh / 2)] = join2(w[0][r], w[1][r]);
+        for (int r = 0; r < G::R; ++r) dst[r * G::NS * NP] = join2(w[0][r], w[1][r]);
+      } else {
+        float4* dst = reinterpret_cast<float4*>(Z + (size_t)j * Wh + col0);
+#pragma unroll
+        for (int r = 0; r < G::R; ++r) dst[(size_t)r * G::NS * (Wh / 2)] = join2(w[0][r], w[1][r]);
+      }
+    }
+  }
+  if constexpr (TMA) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll 1
+      for (int b = 0; b < H / BR; ++b) tma_store_2d(map, 2 * c0, ws * H + b * BR, sm + b * BR * NC);
+      bulk_commit();
+      if constexpr (CG) bulk_wait_all();
+      else bulk_wait_read();
     }
   }
 }
@@ -414,6 +475,13 @@ template <class SP, int W, int NC, int T, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_col_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
   col_body<SP, W, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4));
+}
+
+template <class SP, int W, int NC, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_col_tma_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
+  extern __shared__ __align__(1024) float4 smem4t[];
+  col_body<SP, W, NC, T, false, true>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4t),
+                                      &map);
 }
 
 template <class SP, int T, int PPB>
@@ -654,10 +722,11 @@ template <class RS, int RT, class CS>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   // NC columns per block, CT threads, at least MINB resident blocks per SM
-  template <int NC, int CT, int MINB>
+  template <int NC, int CT, int MINB, bool TMA>
   static FixedCol col() {
-    allow(k_col_fx<CS, W, NC, CT, MINB>);
-    return FixedCol{NC, CT, col_fx_smem(H, NC), (void*)k_col_fx<CS, W, NC, CT, MINB>};
+    void* fn = TMA ? (void*)k_col_tma_fx<CS, W, NC, CT, MINB> : (void*)k_col_fx<CS, W, NC, CT, MINB>;
+    allow_max_dynamic_smem(fn);
+    return FixedCol{NC, CT, col_fx_smem(H, NC), fn, TMA, tma_box_rows(H, NC)};
   }
   template <int PPB>
   static FixedRow row() {
@@ -713,21 +782,28 @@ std::vector<FixedShape> build_registry() {
   std::vector<FixedShape> v;
   {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 240, 3>(), D::col<8, 480, 1>(), D::col<4, 240, 2>()},
+    v.push_back(D::make({D::row<2>(), D::row<1>()},
+                        {D::col<4, 240, 3, true>(), D::col<4, 240, 3, false>(), D::col<8, 480, 1, true>(),
+                         D::col<8, 480, 1, false>()},
                         D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 180, 4>(), D::col<8, 360, 2>(), D::col<4, 180, 3>()},
+    v.push_back(D::make({D::row<2>(), D::row<1>()},
+                        {D::col<8, 360, 2, true>(), D::col<8, 360, 2, false>(), D::col<4, 180, 4, true>(),
+                         D::col<4, 180, 4, false>()},
                         D::persist<160, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()}, {D::col<4, 360, 2>(), D::col<4, 360, 1>()}, D::persist<256, 2, 4>()));
+    v.push_back(D::make({D::row<2>(), D::row<1>()},
+                        {D::col<4, 360, 2, true>(), D::col<4, 360, 2, false>(), D::col<4, 360, 1, true>()},
+                        D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4>(), D::col<8, 64, 8>()}, D::persist<32, 8, 16>()));
+    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4, true>(), D::col<16, 128, 4, false>()},
+                        D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
   return v;
@@ -749,11 +825,48 @@ bool fixed_supports(const FixedShape& fs, int H, int ppb) {
   return (H / 2) % r.ppb == 0;
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once (nullptr if absent)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// The workspace spectra [rows][W/2] float2 as a [rows][W] float tensor with
+// boxes of br rows x 2*nc floats (nc complex columns).
+bool encode_spec_map(CUtensorMap* m, const float2* base, int W, long long rows, int nc, int br) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || br <= 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)W * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * nc), (cuuint32_t)br};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc) {
   const FixedCol& fc = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
   const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};
+  alignas(64) CUtensorMap map;
+  if (fc.tma && !encode_spec_map(&map, a.spec, a.W, (long long)a.nitems * a.H, fc.nc, fc.br))
+    throw Error{PRNU_ECUDA, "cannot describe the workspace spectra for TMA (cuTensorMapEncodeTiled)"};
+  void* targs[] = {const_cast<PassArgs*>(&a), &map};
   {
     ProfScope ps(lc, kKindRowForward, s);
     dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads * fr.ppb);
@@ -762,7 +875,7 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   {
     ProfScope ps(lc, kKindColumn, s);
     dim3 g((Wh + fc.nc - 1) / fc.nc, a.nitems), b(fc.threads);
-    PRNU_CUDA_TRY(cudaLaunchKernel(fc.fn, g, b, args, fc.smem, s));
+    PRNU_CUDA_TRY(cudaLaunchKernel(fc.fn, g, b, fc.tma ? targs : args, fc.smem, s));
   }
   {
     ProfScope ps(lc, kKindRowInverse, s);

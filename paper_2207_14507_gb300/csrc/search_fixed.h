@@ -6,12 +6,17 @@
 
 namespace prnu {
 
-// one instantiated column-pass variant: columns per block, threads, shared memory
+// one instantiated column-pass variant: columns per block, threads, shared
+// memory; with tma the kernel moves its strip by TMA tile copies of br rows
+// and takes a CUtensorMap of the workspace spectra as a second argument,
+// otherwise each thread loads and stores its own elements
 struct FixedCol {
   int nc;
   int threads;
   size_t smem;
   void* fn;
+  bool tma;
+  int br;
 };
 
 // one instantiated pair of row kernels: row pairs per block, threads per pair

@@ -509,6 +509,7 @@ struct Server::Impl {
     PRNU_CUDA_TRY(cudaMemcpyAsync(slot.d_tab, slot.h_tab, sizeof(void*) * 2 * kMaxWave, cudaMemcpyHostToDevice,
                                   s_comp));
     PassArgs a{};
+    a.err = ctx->d_err;
     a.rdtype = key.dtype;
     const ResidLayout lay = padded_layout(H, W);
     a.rpitch = lay.rpitch;

@@ -248,7 +248,7 @@ def test_fullhd_planted_frames_sampled(ctx, prnu):
             assert got[f, 0, c] == pytest.approx(o["pce"], rel=FP32_TOL), (f, c)
 
 
-FIXED_SHAPES = [(256, 256, 2), (720, 1280, 3), (1080, 1920, 3), (2160, 3840, 2)]
+FIXED_SHAPES = [(256, 256, 2), (720, 1280, 4), (1080, 1920, 4), (2160, 3840, 3)]
 
 
 @pytest.mark.parametrize("H,W,nvar", FIXED_SHAPES)
