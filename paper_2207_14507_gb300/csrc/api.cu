@@ -251,7 +251,7 @@ void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, S
 
 static std::vector<FpDesc> fp_descs(const SearchCall& call) {
   std::vector<FpDesc> d;
-  for (auto& f : call.fps) d.push_back(FpDesc{f->d_spec, f->dtype, f->d_scal + 2});
+  for (auto& f : call.fps) d.push_back(fp_desc(*f));
   return d;
 }
 
@@ -572,8 +572,18 @@ int prnu_fingerprint_term(prnu_ctx* ctx, const float* d_K, int H, int W, int sto
     f->W = W;
     f->dtype = half ? kF16 : kF32;
     f->bytes = (size_t)H * Wh * (half ? sizeof(__half2) : sizeof(float2));
+    // the column pass of the compile-time-planned kernels reads strips of the
+    // spectrum by TMA: its descriptors live right after the spectrum
+    alignas(64) unsigned char tmaps[kFpTmapBytes];
+    const size_t tmap_off = (f->bytes + 127) / 128 * 128;
+    f->bytes = tmap_off + kFpTmapBytes;
     f->d_spec = ctx_alloc(ctx, f->bytes);
     try {
+      if (encode_fp_tmaps(f->d_spec, f->dtype, H, W, tmaps)) {
+        PRNU_CUDA_TRY(
+            cudaMemcpy(static_cast<char*>(f->d_spec) + tmap_off, tmaps, kFpTmapBytes, cudaMemcpyHostToDevice));
+        f->tmap_off = tmap_off;
+      }
       f->d_scal = reinterpret_cast<float*>(ctx_alloc(ctx, 3 * sizeof(float)));
     } catch (...) {
       ctx_free(ctx, f->d_spec, f->bytes);

@@ -150,12 +150,19 @@ inline ResidLayout padded_layout(int H, int W) {
 struct Fingerprint {
   int H = 0, W = 0;
   int dtype = kF32;
-  void* d_spec = nullptr;
+  void* d_spec = nullptr;    // spectrum, then (at tmap_off) the TMA descriptors of the column pass, if any
+  size_t tmap_off = 0;       // 0: no descriptors
   float* d_scal = nullptr;   // [mean, scale, inv_scale]
   size_t bytes = 0;
   int refs = 0;
   cudaEvent_t ready = nullptr;
 };
+
+// the kernels' view of a cached fingerprint
+inline FpDesc fp_desc(const Fingerprint& f) {
+  return FpDesc{f.d_spec, f.dtype, f.d_scal + 2,
+                f.tmap_off ? static_cast<const char*>(f.d_spec) + f.tmap_off : nullptr};
+}
 
 struct DeviceBuf {
   void* p = nullptr;

@@ -175,21 +175,27 @@ __device__ __forceinline__ void load_fp_pair(const FpDesc& fp, int j, int col0, 
 // Rows per TMA box of an H-row strip of NC columns (float2): a divisor of H of
 // at most 256 rows whose box size is a multiple of 128 bytes, so that every
 // box lands 128-byte aligned in shared memory.
-__host__ __device__ constexpr int tma_box_rows(int H, int NC) {
+__host__ __device__ constexpr int tma_box_rows(int H, int NC, int esize = 8) {
   for (int br = 256; br >= 1; --br)
-    if (H % br == 0 && (br * NC * 8) % 128 == 0) return br;
+    if (H % br == 0 && (br * NC * esize) % 128 == 0) return br;
   return 0;
 }
+__host__ __device__ constexpr int fp_tmap_index(int NC) { return NC == 4 ? 0 : NC == 8 ? 1 : 2; }
+__host__ __device__ constexpr size_t col_fx_smem_fpt(int H, int nc) { return (size_t)H * (nc + 1) * sizeof(float2); }
 constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait before giving up
 
-// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.  With
-// TMA the strip comes into shared memory by tile copies through `map` (the
-// workspace spectra as a [slots*H][W] float tensor) and leaves the same way;
-// otherwise every thread loads and stores its own elements.  A TMA wait that
-// runs out raises a.err and abandons the candidate.
-template <class SP, int W, int NC, int T, bool CG = false, bool TMA = false>
+// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
+// MODE 0: every thread loads and stores its own elements.  MODE >= 1: the
+// strip comes into shared memory by TMA tile copies through `map` (the
+// workspace spectra as a [slots*H][W] float tensor) and leaves the same way.
+// MODE 2: the fingerprint strip too comes by TMA, into the strip buffer once
+// the last forward stage has taken its inputs (the packed column-0 scratch then
+// sits after the strip).  A TMA wait that runs out raises a.err and abandons
+// the candidate.
+template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0>
 __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
                                          const CUtensorMap* map = nullptr) {
+  constexpr bool TMA = MODE >= 1, FPT = MODE == 2;
   constexpr int H = SP::N, Wh = W / 2;
   using IS = typename SP::Rev;
   using M = ColMap<NC, T>;
@@ -264,6 +270,21 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     for (int r = 0; r < FL::R; ++r) split2(src[r * FL::NB * NP], v[it][0][r], v[it][1][r]);
   }
   __syncthreads();
+  // The fingerprint strip: by TMA into the strip buffer, which is free now
+  // (every thread holds its inputs), else by per-thread loads.
+  const bool fp_tma = FPT && fp.tmaps != nullptr;
+  if constexpr (FPT) {
+    if (fp_tma && t == 0) {
+      const CUtensorMap* fm = reinterpret_cast<const CUtensorMap*>(fp.tmaps) + fp_tmap_index(NC);
+      const int es = fp.dtype == kF32 ? 8 : 4, fbr = tma_box_rows(H, NC, es);
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(fm))
+                   : "memory");
+      mbar_expect_tx(&s_bar, H * NC * es);
+#pragma unroll 1
+      for (int b = 0; b < H / fbr; ++b)
+        tma_load_2d(reinterpret_cast<char*>(sm) + (size_t)b * fbr * NC * es, fm, 2 * c0, b * fbr, &s_bar);
+    }
+  }
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
     const int j = j0 + it * TJ;
@@ -272,10 +293,31 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     Dft<FL::R, false>::run(v[it][0]);
     Dft<FL::R, false>::run(v[it][1]);
   }
+  if constexpr (FPT) {
+    if (fp_tma) {
+      const bool ok = mbar_wait_bounded(&s_bar, 1, kTmaWaitPolls);
+      if (__syncthreads_or(!ok)) {
+        if (t == 0) {
+          if (a.err) atomicExch(a.err, 1);
+          mbar_wait_bounded(&s_bar, 1, kTmaWaitPolls);
+        }
+        __syncthreads();
+        return;
+      }
+    }
+  }
+  // fingerprint bin (i, col) of this strip
+  auto fp_bin = [&](int i, int col) -> float2 {
+    if (fp_tma) {
+      if (fp.dtype == kF32) return sm[i * NC + (col - c0)];
+      return __half22float2(reinterpret_cast<const __half2*>(sm)[i * NC + (col - c0)]);
+    }
+    return load_spec(fp.spec, fp.dtype, (size_t)i * Wh + col);
+  };
   // thread holds bins i = j + r*NS of columns col0 and col0 + 1
   if (c0 == 0) {
     // packed column 0 (DC + i*Nyquist): the product needs bin H - i as well
-    float2* X0 = sm;   // free: every thread has loaded its inputs
+    float2* X0 = FPT ? sm + H * NC : sm;   // with MODE 2 the strip buffer holds the fingerprint
     if (cp == 0) {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
@@ -296,8 +338,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
           const int i = j + r * FL::NS;
           const int im = i == 0 ? 0 : H - i;
           const float2 F = v[it][0][r], Fm = X0[im];
-          const float2 S = load_spec(fp.spec, fp.dtype, (size_t)i * Wh);
-          const float2 Sm = load_spec(fp.spec, fp.dtype, (size_t)im * Wh);
+          const float2 S = fp_bin(i, 0), Sm = fp_bin(im, 0);
           const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
           const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
           const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
@@ -314,13 +355,37 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   for (int it = 0; it < IT; ++it) {
     const int j = j0 + it * TJ;
     if (FL::NB % TJ != 0 && j >= FL::NB) continue;
-    float2 s[2][FL::R];
-    load_fp_pair<FL::R, FL::NS, Wh>(fp, j, col0, s);
+    if (fp_tma) {
+      const float4* s4 = reinterpret_cast<const float4*>(sm) + j * NP + cp;
+      const float2* s2 = reinterpret_cast<const float2*>(sm) + j * NP + cp;   // two __half2
 #pragma unroll
-    for (int r = 0; r < FL::R; ++r) {
-      if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), s[0][r]);
-      v[it][1][r] = c_mul(c_conj(v[it][1][r]), s[1][r]);
+      for (int r = 0; r < FL::R; ++r) {
+        float2 s0, s1;
+        if (fp.dtype == kF32) {
+          split2(s4[r * FL::NS * NP], s0, s1);
+        } else {
+          const float2 u = s2[r * FL::NS * NP];
+          s0 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+          s1 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        }
+        if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), s0);
+        v[it][1][r] = c_mul(c_conj(v[it][1][r]), s1);
+      }
+    } else {
+      float2 sf[2][FL::R];
+      load_fp_pair<FL::R, FL::NS, Wh>(fp, j, col0, sf);
+#pragma unroll
+      for (int r = 0; r < FL::R; ++r) {
+        if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), sf[0][r]);
+        v[it][1][r] = c_mul(c_conj(v[it][1][r]), sf[1][r]);
+      }
     }
+  }
+  if (fp_tma) __syncthreads();   // every fingerprint bin read before the strip buffer is rewritten
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = j0 + it * TJ;
+    if (FL::NB % TJ != 0 && j >= FL::NB) continue;
     Dft<FL::R, true>::run(v[it][0]);
     Dft<FL::R, true>::run(v[it][1]);
     float4* dst = sm4 + j * FL::R * NP + cp;
@@ -477,10 +542,10 @@ __global__ void __launch_bounds__(T, MINB) k_col_fx(PassArgs a) {
   col_body<SP, W, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4));
 }
 
-template <class SP, int W, int NC, int T, int MINB>
+template <class SP, int W, int NC, int T, int MINB, int MODE>
 __global__ void __launch_bounds__(T, MINB) k_col_tma_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(1024) float4 smem4t[];
-  col_body<SP, W, NC, T, false, true>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4t),
+  col_body<SP, W, NC, T, false, MODE>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4t),
                                       &map);
 }
 
@@ -722,11 +787,13 @@ template <class RS, int RT, class CS>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   // NC columns per block, CT threads, at least MINB resident blocks per SM
-  template <int NC, int CT, int MINB, bool TMA>
+  // MODE: 0 plain loads and stores, 1 strip by TMA, 2 strip and fingerprint by TMA
+  template <int NC, int CT, int MINB, int MODE>
   static FixedCol col() {
-    void* fn = TMA ? (void*)k_col_tma_fx<CS, W, NC, CT, MINB> : (void*)k_col_fx<CS, W, NC, CT, MINB>;
+    void* fn = MODE ? (void*)k_col_tma_fx<CS, W, NC, CT, MINB, MODE> : (void*)k_col_fx<CS, W, NC, CT, MINB>;
     allow_max_dynamic_smem(fn);
-    return FixedCol{NC, CT, col_fx_smem(H, NC), fn, TMA, tma_box_rows(H, NC)};
+    return FixedCol{NC, CT, MODE == 2 ? col_fx_smem_fpt(H, NC) : col_fx_smem(H, NC), fn, MODE != 0,
+                    tma_box_rows(H, NC)};
   }
   template <int PPB>
   static FixedRow row() {
@@ -783,26 +850,26 @@ std::vector<FixedShape> build_registry() {
   {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 240, 3, true>(), D::col<4, 240, 3, false>(), D::col<8, 480, 1, true>(),
-                         D::col<8, 480, 1, false>()},
+                        {D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(), D::col<4, 240, 3, 0>(),
+                         D::col<8, 480, 1, 1>()},
                         D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<8, 360, 2, true>(), D::col<8, 360, 2, false>(), D::col<4, 180, 4, true>(),
-                         D::col<4, 180, 4, false>()},
+                        {D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(), D::col<8, 360, 2, 0>(),
+                         D::col<4, 180, 4, 2>()},
                         D::persist<160, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 360, 2, true>(), D::col<4, 360, 2, false>(), D::col<4, 360, 1, true>()},
+                        {D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(), D::col<4, 360, 2, 0>()},
                         D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4, true>(), D::col<16, 128, 4, false>()},
+    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>()},
                         D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
@@ -857,6 +924,30 @@ bool encode_spec_map(CUtensorMap* m, const float2* base, int W, long long rows, 
 }
 
 }  // namespace
+
+static_assert(3 * sizeof(CUtensorMap) == kFpTmapBytes, "three 128-byte descriptors per fingerprint");
+
+bool encode_fp_tmaps(const void* spec, int dtype, int H, int W, void* out) {
+  if (!find_fixed(H, W)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int es = dtype == kF32 ? 8 : 4;   // bytes per complex bin
+  const int ncs[3] = {4, 8, 16};
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out);
+  for (int k = 0; k < 3; ++k) {
+    const int br = tma_box_rows(H, ncs[k], es);
+    if (br <= 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * (es / 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * ncs[k]), (cuuint32_t)br};
+    const cuuint32_t el[2] = {1, 1};
+    if (enc(&m[k], es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+            const_cast<void*>(spec), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
 
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc) {
   const FixedCol& fc = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];

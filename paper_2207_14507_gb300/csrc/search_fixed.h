@@ -80,4 +80,11 @@ void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape
 
 constexpr int kPersistSlots = 8;
 
+// TMA descriptors (CUtensorMap, 128 bytes each) of a fingerprint spectrum
+// [H][W/2] (float2 for kF32, __half2 for kF16) for column strips of 4, 8 and
+// 16 columns, written to host memory `out` (3 descriptors).  False when the
+// frame size has no compile-time-planned kernels or the driver lacks TMA.
+bool encode_fp_tmaps(const void* spec, int dtype, int H, int W, void* out);
+constexpr size_t kFpTmapBytes = 3 * 128;
+
 }  // namespace prnu

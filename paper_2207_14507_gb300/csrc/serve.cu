@@ -311,7 +311,7 @@ struct Server::Impl {
       if (!fp_used[s]) {
         fp_used[s] = 1;
         fp_slots[f.get()] = {s, 1};
-        k_set_fpdesc<<<1, 1, 0, s_copy>>>(d_fpdesc + s, FpDesc{f->d_spec, f->dtype, f->d_scal + 2});
+        k_set_fpdesc<<<1, 1, 0, s_copy>>>(d_fpdesc + s, fp_desc(*f));
         PRNU_CUDA_TRY(cudaGetLastError());
         return s;
       }
