@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", choices=["plain", "batched", "precision", "serving"], default="plain",
                     help="plain = the 1080p metric line; the others print their own JSON record")
     ap.add_argument("--queries", type=int, default=16, help="serving: queries per run")
+    ap.add_argument("--wave", type=int, default=0,
+                    help="plain workload: candidates per wave after tuning (0 = the tuned value); for small profiles")
     ap.add_argument("--autotune-ms", type=float, default=5000.0,
                     help="time budget of the library autotuner run before the warm-up (0 = defaults)")
     return ap.parse_args()
@@ -96,9 +98,10 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel, H, W, dtype):
-    """DRAM bytes per candidate of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources; else None."""
+def counters_for(kernel, H, W, dtype):
+    """ncu counters per candidate of `kernel` (DRAM bytes, warp instructions)
+    from the committed summary profiles/traffic.json, if they were taken on the
+    current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
@@ -107,7 +110,7 @@ def traffic_for(kernel, H, W, dtype):
     e = d.get(f"{kernel}:{H}x{W}:{dtype}")
     if not e or e.get("csrc_digest") != csrc_digest():
         return None
-    return e.get("dram_bytes_per_candidate")
+    return e
 
 
 # --------------------------------------------------------------------------- clocks
@@ -257,6 +260,10 @@ def run_ours(args):
 
     tuning = ctx.prnu_autotune(H, W, fpd, budget_ms=args.autotune_ms) if args.autotune_ms > 0 \
         else ctx.prnu_get_tuning(H, W)
+    if args.wave > 0:
+        tuning = dict(tuning, wave=args.wave)
+        ctx.prnu_set_tuning(H, W, tuning["col_width"], tuning["pairs_per_block"], tuning["wave"], tuning["variant"],
+                            tuning["persistent"])
 
     def step():
         ctx.prnu_residual(frames_d, R, scale=scale, flags=flags)
@@ -330,11 +337,25 @@ def run_ours(args):
     dom = max(timed, key=lambda k: timed[k]["total_ms"])
     cands_total = ncand * args.steps
     achieved = kb[dom] * cands_total / (timed[dom]["total_ms"] / 1e3) / 1e9
-    traffic = traffic_for(dom, H, W, args.dtype)
+    per_launch = cands_total / timed[dom]["launches"]          # candidates one launch of `dom` processes
+    cnt = counters_for(dom, H, W, args.dtype)
+    traffic = round(cnt["dram_bytes_per_candidate"] * per_launch) if cnt else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": traffic, "algorithmic_bytes_per_candidate": kb[dom],
+            "candidates_per_launch": round(per_launch, 1),
             "share_of_step": round(timed[dom]["total_ms"] / (ms * args.steps), 3)}
+    # The same kernel against the instruction-issue roof: ncu's warp
+    # instructions per candidate x candidates/s over 4 issue slots per SM per clock.
+    issue = None
+    if cnt and cnt.get("warp_instructions_per_candidate"):
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk.summary() or {}).get("sm_mhz") or 2070.0   # median SM clock sampled in the timed region
+        slots = nsm * 4 * mhz * 1e6
+        rate = cnt["warp_instructions_per_candidate"] * cands_total / (timed[dom]["total_ms"] / 1e3)
+        issue = {"bound": "issue", "kernel": dom, "achieved": round(rate / 1e12, 4), "peak": round(slots / 1e12, 4),
+                 "unit": "Twarp-inst/s", "frac": round(rate / slots, 4),
+                 "warp_instructions_per_candidate": cnt["warp_instructions_per_candidate"]}
     pb = path_bytes(H, W, s_in, s_k)
     path_roof = {"bytes_per_candidate": pb, "achieved": round(pb * value / ws / 1e9, 1),
                  "frac": round(pb * value / ws / 1e9 / peak, 4)}
@@ -347,7 +368,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": dict(workload_config(args, H, W, F), tuning=tuning),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "path_roofline": path_roof,
-        "kernels": kernels, "clocks": clk.summary(),
+        "issue_roofline": issue, "kernels": kernels, "clocks": clk.summary(),
     }
 
     if rank == 0 and not args.no_extras:

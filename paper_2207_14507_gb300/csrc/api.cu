@@ -159,9 +159,11 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
       break;
     }
   }
-  t.ppb = 2;
+  // the planned kernels run one row pair per block best; waves of a few
+  // hundred candidates (a few GB of spectra) amortise the per-wave finalisation
+  t.ppb = find_fixed(H, W) ? 1 : 2;
   const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
-  t.wave = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)1 << 30) / per_item));
+  t.wave = (int)std::max<size_t>(1, std::min<size_t>(512, ((size_t)4 << 30) / per_item));
   return t;
 }
 

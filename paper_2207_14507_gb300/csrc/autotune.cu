@@ -61,7 +61,7 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
     const FixedShape* fs = find_fixed(H, W);
     const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
     std::vector<int> waves;
-    for (int w : {8, 16, 32, 64, 128})
+    for (int w : {16, 64, 128, 256, 512})
       if ((size_t)w * per_item < ctx->budget / 4) waves.push_back(w);
     if (waves.empty()) waves.push_back(1);
     // candidate configurations: generic kernels and every compile-time column
