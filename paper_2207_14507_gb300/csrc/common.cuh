@@ -28,7 +28,7 @@ struct FpDesc {
   const void* spec;    // packed [H][W/2] complex, float2 or __half2
   int dtype;                 // kF32 or kF16
   const float* inv_scale;    // device scalar: multiply the correlation by it to undo the storage scale
-  const void* tmaps;         // device CUtensorMap[3] of the spectrum (strips of 4, 8, 16 columns), or nullptr
+  const void* tmaps;         // device CUtensorMap[4] of the spectrum (strips of 2, 4, 8, 16 columns), or nullptr
 };
 
 // Per-row statistics of one candidate's correlation surface.

@@ -197,19 +197,36 @@ __device__ __forceinline__ void row_stage(const float2* __restrict__ in, float2*
   }
 }
 
-// Last stage of row plan SP (Ns = n/R, one butterfly per thread, t < n/R):
-// outputs x = t + r*Ns stay in registers.
+// Last stage of row plan SP (Ns = n/R): butterflies j = t + it*T, outputs
+// x = j + r*Ns stay in registers, v[it]; `last_valid` tells which are real.
+template <class SP, int T>
+struct RowLast {
+  using G = Stg<SP, SP::S - 1>;
+  static constexpr int R = G::R;
+  static constexpr int NS = G::NS;
+  static constexpr int IT = (G::NB + T - 1) / T;
+  static_assert(G::NB == G::NS && G::NB % 16 == 0, "last stage: k = j");
+  __device__ __forceinline__ static bool valid(int t, int it) { return G::NB % T == 0 || t + it * T < G::NB; }
+};
+
 template <class SP, int T, bool INV>
 __device__ __forceinline__ void row_stage_last(const float2* __restrict__ in, int t,
-                                               float2 (&v)[1][Stg<SP, SP::S - 1>::R]) {
-  using G = Stg<SP, SP::S - 1>;
-  static_assert(G::NB == G::NS && G::NB <= T && G::NB % 16 == 0, "last stage: one butterfly per thread");
-  constexpr int LB = G::NB / 16 * 18;
-  const float2* src = in + rp2(t);
+                                               float2 (&v)[RowLast<SP, T>::IT][RowLast<SP, T>::R]) {
+  using L = RowLast<SP, T>;
+  constexpr int LB = L::NS / 16 * 18;
 #pragma unroll
-  for (int r = 0; r < G::R; ++r) v[0][r] = src[r * LB];
-  twiddle_tab<G::R, G::NS, INV, 1>(v, t);
-  Dft<G::R, INV>::run(v[0]);
+  for (int it = 0; it < L::IT; ++it) {
+    if (!L::valid(t, it)) break;
+    const int j = t + it * T;
+    const float2* src = in + rp2(j);
+    float2 u[1][L::R];
+#pragma unroll
+    for (int r = 0; r < L::R; ++r) u[0][r] = src[r * LB];
+    twiddle_tab<L::R, L::NS, INV, 1>(u, j);
+    Dft<L::R, INV>::run(u[0]);
+#pragma unroll
+    for (int r = 0; r < L::R; ++r) v[it][r] = u[0][r];
+  }
 }
 
 // ---------------------------------------------------------------- column layout

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "fft_fixed.cuh"
@@ -180,7 +181,7 @@ __host__ __device__ constexpr int tma_box_rows(int H, int NC, int esize = 8) {
     if (H % br == 0 && (br * NC * esize) % 128 == 0) return br;
   return 0;
 }
-__host__ __device__ constexpr int fp_tmap_index(int NC) { return NC == 4 ? 0 : NC == 8 ? 1 : 2; }
+__host__ __device__ constexpr int fp_tmap_index(int NC) { return NC == 2 ? 0 : NC == 4 ? 1 : NC == 8 ? 2 : 3; }
 __host__ __device__ constexpr size_t col_fx_smem_fpt(int H, int nc) { return (size_t)H * (nc + 1) * sizeof(float2); }
 constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait before giving up
 
@@ -272,7 +273,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   __syncthreads();
   // The fingerprint strip: by TMA into the strip buffer, which is free now
   // (every thread holds its inputs), else by per-thread loads.
-  const bool fp_tma = FPT && fp.tmaps != nullptr;
+  const bool fp_tma = FPT && fp.tmaps != nullptr && NC * (fp.dtype == kF32 ? 8 : 4) >= 16;
   if constexpr (FPT) {
     if (fp_tma && t == 0) {
       const CUtensorMap* fm = reinterpret_cast<const CUtensorMap*>(fp.tmaps) + fp_tmap_index(NC);
@@ -444,7 +445,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
 // Holds barriers: every thread of the block calls it.
 template <class SP, int T, bool CG>
 __device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* pb, float2* A, float2* B, int t,
-                                                float2 (&v)[1][Stg<SP, SP::S - 1>::R]) {
+                                                float2 (&v)[RowLast<SP, T>::IT][RowLast<SP, T>::R]) {
   constexpr int W = SP::N, Wh = W / 2;
   using S0 = Stg<SP, 0>;
   static_assert(S0::R == 16 && SP::S >= 2 && SP::S <= 3, "row plans: radix 16 first, two or three stages");
@@ -484,20 +485,19 @@ __device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* 
     row_store16(A, t, u);
   }
   __syncthreads();
-  constexpr int NBL = Stg<SP, SP::S - 1>::NB;
   if constexpr (SP::S == 2) {
-    if (NBL == T || t < NBL) row_stage_last<SP, T, true>(A, t, v);
+    row_stage_last<SP, T, true>(A, t, v);
   } else {
     row_stage<SP, 1, T, true>(A, B, t);
     __syncthreads();
-    if (NBL == T || t < NBL) row_stage_last<SP, T, true>(B, t, v);
+    row_stage_last<SP, T, true>(B, t, v);
   }
 }
 
 template <class SP, int T, int PPB, bool CG = false>
 __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int bx, float2* smem, int tx) {
   constexpr int W = SP::N, Wh = W / 2, L = row_len2(W);
-  using GL = Stg<SP, SP::S - 1>;
+  using GL = RowLast<SP, T>;
   static_assert(PPB == 1 || T % 32 == 0, "row-pair groups must not share a warp (warp-level reductions)");
   const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
@@ -506,23 +506,25 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
   float2* B = A + L;
   RowRed* red = reinterpret_cast<RowRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
-  float2 v[1][GL::R];
+  float2 v[GL::IT][GL::R];
   row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, B, t, v);
   float ma = -INFINITY, mb = -INFINITY;
   int ia = INT_MAX, ib = INT_MAX;
   float sa = 0.f, sb = 0.f;
-  if (GL::NB == T || t < GL::NB) {
+#pragma unroll
+  for (int it = 0; it < GL::IT; ++it) {
+    if (!GL::valid(t, it)) break;
 #pragma unroll
     for (int r = 0; r < GL::R; ++r) {
-      const int x = t + r * GL::NS;
-      const float2 u = v[0][r];
+      const int x = t + it * T + r * GL::NS;
+      const float2 u = v[it][r];
       better_f(ma, ia, u.x, x);
       better_f(mb, ib, u.y, x);
       sa = fmaf(u.x, u.x, sa);
       sb = fmaf(u.y, u.y, sb);
     }
   }
-  row_stats_warp(ma, ia, mb, ib, sa, sb, t, red);
+  row_stats_warp_fast(ma, ia, mb, ib, sa, sb, t, red);
   __syncthreads();
   if (t == 0) row_stats_final(red, (T + 31) / 32, a.stats + (size_t)ws * H + 2 * pair);
 }
@@ -580,7 +582,7 @@ __device__ __forceinline__ void row_inverse_task(const PassArgs& a, int ws, int 
 template <class SP, int T, int PPB>
 __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws, float2* smem, int tx) {
   constexpr int W = SP::N, Wh = W / 2, L = row_len2(W), TB = T * PPB;
-  using SL = Stg<SP, SP::S - 1>;
+  using SL = RowLast<SP, T>;
   __shared__ int s_py, s_px, s_np;
   __shared__ float s_peak;
   __shared__ int s_pairs[2 * kHalfWindow + 1];
@@ -631,15 +633,19 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
     float2* A = smem + (size_t)grp * 2 * L;
     float2* B = A + L;
     const float2* pa = Z + (size_t)(2 * p) * Wh;
-    float2 V[1][SL::R];
+    float2 V[SL::IT][SL::R];
     row_inverse_fft<SP, T, true>(pa, pa + Wh, A, B, tg, V);
-    if (act && (SL::NB == T || tg < SL::NB)) {
+    if (act) {
 #pragma unroll
-      for (int r = 0; r < SL::R; ++r) {
-        const int x = tg + r * SL::NS;
-        if (cdist(x, px, W) <= kHalfWindow) continue;
-        if (cdist(2 * p, py, H) <= kHalfWindow) e += (double)V[0][r].x * V[0][r].x;
-        if (cdist(2 * p + 1, py, H) <= kHalfWindow) e += (double)V[0][r].y * V[0][r].y;
+      for (int it = 0; it < SL::IT; ++it) {
+        if (!SL::valid(tg, it)) break;
+#pragma unroll
+        for (int r = 0; r < SL::R; ++r) {
+          const int x = tg + it * T + r * SL::NS;
+          if (cdist(x, px, W) <= kHalfWindow) continue;
+          if (cdist(2 * p, py, H) <= kHalfWindow) e += (double)V[it][r].x * V[it][r].x;
+          if (cdist(2 * p + 1, py, H) <= kHalfWindow) e += (double)V[it][r].y * V[it][r].y;
+        }
       }
     }
     __syncthreads();
@@ -783,7 +789,8 @@ void allow(K k) {
   allow_max_dynamic_smem(k);
 }
 
-template <class RS, int RT, class CS>
+// RT threads per row pair in the row forward kernel, RTI in the row inverse
+template <class RS, int RT, class CS, int RTI = RT>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   // NC columns per block, CT threads, at least MINB resident blocks per SM
@@ -800,15 +807,16 @@ struct ShapeDef {
     FixedRow r{};
     r.ppb = PPB;
     r.threads = RT;
+    r.threads_inv = RTI;
     r.smem = row_fx_smem<W>(PPB);
     r.fwd[kF32] = (void*)k_row_forward_fx<kF32, RS, RT, PPB>;
     r.fwd[kF16] = (void*)k_row_forward_fx<kF16, RS, RT, PPB>;
     r.fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
-    r.inv = (void*)k_row_inverse_fx<RS, RT, PPB>;
+    r.inv = (void*)k_row_inverse_fx<RS, RTI, PPB>;
     allow(k_row_forward_fx<kF32, RS, RT, PPB>);
     allow(k_row_forward_fx<kF16, RS, RT, PPB>);
     allow(k_row_forward_fx<kBF16, RS, RT, PPB>);
-    allow(k_row_inverse_fx<RS, RT, PPB>);
+    allow(k_row_inverse_fx<RS, RTI, PPB>);
     return r;
   }
   // PRT threads per row pair (PRT * PPB per block, also the column task's
@@ -848,7 +856,7 @@ struct ShapeDef {
 std::vector<FixedShape> build_registry() {
   std::vector<FixedShape> v;
   {
-    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>>;
+    using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>, 160>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(), D::col<4, 240, 3, 0>(),
                          D::col<8, 480, 1, 1>()},
@@ -925,17 +933,21 @@ bool encode_spec_map(CUtensorMap* m, const float2* base, int W, long long rows, 
 
 }  // namespace
 
-static_assert(3 * sizeof(CUtensorMap) == kFpTmapBytes, "three 128-byte descriptors per fingerprint");
+static_assert(4 * sizeof(CUtensorMap) == kFpTmapBytes, "four 128-byte descriptors per fingerprint");
 
 bool encode_fp_tmaps(const void* spec, int dtype, int H, int W, void* out) {
   if (!find_fixed(H, W)) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const int es = dtype == kF32 ? 8 : 4;   // bytes per complex bin
-  const int ncs[3] = {4, 8, 16};
+  const int ncs[4] = {2, 4, 8, 16};
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     const int br = tma_box_rows(H, ncs[k], es);
+    if (ncs[k] * es < 16) {   // a box row narrower than 16 bytes: no descriptor (the kernel loads per thread)
+      memset(&m[k], 0, sizeof(CUtensorMap));
+      continue;
+    }
     if (br <= 0) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
     const cuuint64_t strides[1] = {(cuuint64_t)W * (es / 2)};
@@ -970,7 +982,7 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   }
   {
     ProfScope ps(lc, kKindRowInverse, s);
-    dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads * fr.ppb);
+    dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads_inv * fr.ppb);
     PRNU_CUDA_TRY(cudaLaunchKernel(fr.inv, g, b, args, fr.smem, s));
   }
   lc.n += 3;

@@ -22,7 +22,8 @@ struct FixedCol {
 // one instantiated pair of row kernels: row pairs per block, threads per pair
 struct FixedRow {
   int ppb;
-  int threads;
+  int threads;               // per row pair, forward kernel
+  int threads_inv;           // per row pair, inverse kernel
   size_t smem;
   void* fwd[3];              // by residual storage type
   void* inv;
@@ -81,10 +82,10 @@ void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape
 constexpr int kPersistSlots = 8;
 
 // TMA descriptors (CUtensorMap, 128 bytes each) of a fingerprint spectrum
-// [H][W/2] (float2 for kF32, __half2 for kF16) for column strips of 4, 8 and
-// 16 columns, written to host memory `out` (3 descriptors).  False when the
-// frame size has no compile-time-planned kernels or the driver lacks TMA.
+// [H][W/2] (float2 for kF32, __half2 for kF16) for column strips of 2, 4, 8
+// and 16 columns, written to host memory `out` (4 descriptors).  False when
+// the frame size has no compile-time-planned kernels or the driver lacks TMA.
 bool encode_fp_tmaps(const void* spec, int dtype, int H, int W, void* out);
-constexpr size_t kFpTmapBytes = 3 * 128;
+constexpr size_t kFpTmapBytes = 4 * 128;
 
 }  // namespace prnu
