@@ -345,8 +345,8 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
         launch_row_forward(a, true, nullptr, nullptr, s, c->launches);
         launch_col(a, 0, nullptr, nullptr, nullptr, s, c->launches);
         launch_row_inverse(a, nullptr, s, c->launches);
+        launch_finalize(a, s, c->launches);
       }
-      launch_finalize(a, s, c->launches);
     }
     if (fs) PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   } else {

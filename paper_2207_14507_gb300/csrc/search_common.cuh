@@ -104,24 +104,6 @@ __device__ __forceinline__ int float_key(float v) {
 }
 __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
-// row_stats_warp with the warp's max and first arg-max taken by the integer
-// warp reductions (max of the order-preserving key, then min index among the
-// lanes that hold it) and the energies by an FP32 butterfly over the lanes'
-// FP32 partials (32 terms; warps are combined in double by row_stats_final).
-__device__ __forceinline__ void row_stats_warp_fast(float ma, int ia, float mb, int ib, float sa, float sb, int t,
-                                                    RowRed* red) {
-  const int ka = __reduce_max_sync(0xffffffffu, float_key(ma));
-  const int kb = __reduce_max_sync(0xffffffffu, float_key(mb));
-  const int ja = __reduce_min_sync(0xffffffffu, float_key(ma) == ka ? ia : INT_MAX);
-  const int jb = __reduce_min_sync(0xffffffffu, float_key(mb) == kb ? ib : INT_MAX);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    sb += __shfl_xor_sync(0xffffffffu, sb, o);
-  }
-  if ((t & 31) == 0) red[t >> 5] = RowRed{key_float(ka), ja, key_float(kb), jb, sa, 0.f, sb, 0.f};
-}
-
 // Combine nw warps' RowRed (after a barrier) into the two rows' statistics.
 __device__ __forceinline__ void row_stats_final(const RowRed* red, int nw, RowStat* st) {
   RowRed r = red[0];

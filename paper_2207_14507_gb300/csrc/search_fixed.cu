@@ -508,6 +508,7 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
   float2 v[GL::IT][GL::R];
   row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, B, t, v);
+  // per thread: max, first arg-max and energy of each row over its outputs
   float ma = -INFINITY, mb = -INFINITY;
   int ia = INT_MAX, ib = INT_MAX;
   float sa = 0.f, sb = 0.f;
@@ -524,7 +525,19 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
       sb = fmaf(u.y, u.y, sb);
     }
   }
-  row_stats_warp_fast(ma, ia, mb, ib, sa, sb, t, red);
+  // across the warp: the max by an integer reduction of the order-preserving
+  // key, then the least index among the lanes that hold it; energies by an
+  // FP32 butterfly (warps are combined in double by row_stats_final)
+  const int ka = __reduce_max_sync(0xffffffffu, float_key(ma));
+  const int kb = __reduce_max_sync(0xffffffffu, float_key(mb));
+  ia = __reduce_min_sync(0xffffffffu, float_key(ma) == ka ? ia : INT_MAX);
+  ib = __reduce_min_sync(0xffffffffu, float_key(mb) == kb ? ib : INT_MAX);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if ((t & 31) == 0) red[t >> 5] = RowRed{key_float(ka), ia, key_float(kb), ib, sa, 0.f, sb, 0.f};
   __syncthreads();
   if (t == 0) row_stats_final(red, (T + 31) / 32, a.stats + (size_t)ws * H + 2 * pair);
 }
@@ -675,6 +688,14 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
     *result_of(a, is) = res;
   }
 }
+// One block per candidate of the wave: finalize_task with PPB row pairs of the
+// window recomputed at a time.
+template <class SP, int T, int PPB>
+__global__ void __launch_bounds__(T * PPB) k_finalize_fx(PassArgs a) {
+  extern __shared__ float4 smem4[];
+  finalize_task<SP, T, PPB>(a, blockIdx.x, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
+}
+
 //
 // One launch runs every phase of every candidate of a call.  Blocks take
 // tasks by an atomic ticket.  Ticket order is a skewed pipeline: step s holds
@@ -789,7 +810,11 @@ void allow(K k) {
   allow_max_dynamic_smem(k);
 }
 
+// row pairs of the 11-row window recomputed at once by the finalisation
+constexpr int kFinPairs = 3;
+
 // RT threads per row pair in the row forward kernel, RTI in the row inverse
+// (and in the finalisation)
 template <class RS, int RT, class CS, int RTI = RT>
 struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
@@ -813,6 +838,10 @@ struct ShapeDef {
     r.fwd[kF16] = (void*)k_row_forward_fx<kF16, RS, RT, PPB>;
     r.fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
     r.inv = (void*)k_row_inverse_fx<RS, RTI, PPB>;
+    r.fin = (void*)k_finalize_fx<RS, RTI, kFinPairs>;
+    r.fin_threads = RTI * kFinPairs;
+    r.fin_smem = row_fx_smem<W>(kFinPairs);
+    allow(k_finalize_fx<RS, RTI, kFinPairs>);
     allow(k_row_forward_fx<kF32, RS, RT, PPB>);
     allow(k_row_forward_fx<kF16, RS, RT, PPB>);
     allow(k_row_forward_fx<kBF16, RS, RT, PPB>);
@@ -985,7 +1014,11 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
     dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads_inv * fr.ppb);
     PRNU_CUDA_TRY(cudaLaunchKernel(fr.inv, g, b, args, fr.smem, s));
   }
-  lc.n += 3;
+  {
+    ProfScope ps(lc, kKindFinalize, s);
+    PRNU_CUDA_TRY(cudaLaunchKernel(fr.fin, dim3(a.nitems), dim3(fr.fin_threads), args, fr.fin_smem, s));
+  }
+  lc.n += 4;
 }
 
 void launch_persistent(const PassArgs& a, const PersistArgs& p, const FixedShape& fs, int sm_count, cudaStream_t s,

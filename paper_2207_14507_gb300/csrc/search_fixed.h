@@ -27,6 +27,9 @@ struct FixedRow {
   size_t smem;
   void* fwd[3];              // by residual storage type
   void* inv;
+  void* fin;                 // per-candidate PCE (one block per candidate)
+  int fin_threads;
+  size_t fin_smem;
 };
 
 // the persistent kernel of a shape: row pairs per task, columns per task,
@@ -71,7 +74,7 @@ const FixedShape* find_fixed(int H, int W);
 // whether the row kernels chosen for `ppb` pairs per block tile H/2 row pairs exactly
 bool fixed_supports(const FixedShape& fs, int H, int ppb);
 
-// row forward, column pass and row inverse of one wave (a.nitems candidates)
+// row forward, column pass, row inverse and finalisation of one wave (a.nitems candidates)
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc);
 
 // every phase of p.G candidates (items 0..G-1 of a) in one persistent launch;

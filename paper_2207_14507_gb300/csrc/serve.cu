@@ -539,8 +539,8 @@ struct Server::Impl {
       launch_row_forward(a, true, nullptr, nullptr, s_comp, ctx->launches);
       launch_col(a, 0, nullptr, nullptr, nullptr, s_comp, ctx->launches);
       launch_row_inverse(a, nullptr, s_comp, ctx->launches);
+      launch_finalize(a, s_comp, ctx->launches);
     }
-    launch_finalize(a, s_comp, ctx->launches);
     PRNU_CUDA_TRY(cudaEventRecord(slot.ev, s_comp));
     st.server_launches += 4;
     st.candidates_done += count;
