@@ -278,6 +278,20 @@ int prnu_profile_begin(prnu_ctx* ctx);
  * kind into out[0..max) (max >= 1); *n_out receives the number of kinds seen. */
 int prnu_profile_end(prnu_ctx* ctx, prnu_kernel_stat* out, int max, int* n_out);
 
+/* ---------------------------------------------------------------- failure injection (tests) */
+
+/* Test hook; the paper has no counterpart.  With key
+ * PRNU_DEBUG_STALL_DEVICE_WAITS and value 1, every bounded device-side wait of
+ * the compile-time-planned kernels (the column pass's TMA barrier, the
+ * persistent kernel's dependency counts) waits for one arrival more than will
+ * ever come: each such wait runs out (about a second), the kernel raises the
+ * context's device error flag and abandons its candidate, the results of that
+ * call are undefined, and the next search call on the context fails with
+ * PRNU_EDEVICE_ABORT.  The context stays usable.  Value 0 turns it off.
+ * Errors: PRNU_EINVAL (NULL context, unknown key). */
+enum { PRNU_DEBUG_STALL_DEVICE_WAITS = 1 };
+int prnu_debug_set(prnu_ctx* ctx, int key, int value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libprnu.so")
 PRNU_OK, PRNU_EINVAL, PRNU_ENOMEM, PRNU_ECUDA, PRNU_EAGAIN, PRNU_ETIMEOUT, PRNU_ENOTFOUND, PRNU_EDEVICE_ABORT = range(8)
 PRNU_F32, PRNU_F16, PRNU_BF16 = 0, 1, 2
 PRNU_WEIGHT_BY_INTENSITY, PRNU_NORMALISE = 1, 2
+PRNU_DEBUG_STALL_DEVICE_WAITS = 1
 STATUS_NAMES = {0: "PRNU_OK", 1: "PRNU_EINVAL", 2: "PRNU_ENOMEM", 3: "PRNU_ECUDA", 4: "PRNU_EAGAIN",
                 5: "PRNU_ETIMEOUT", 6: "PRNU_ENOTFOUND", 7: "PRNU_EDEVICE_ABORT"}
 
@@ -92,6 +93,7 @@ _SIGNATURES = {
     "prnu_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(prnu_tuning), _P]),
     "prnu_profile_begin": (C.c_int, [_P]),
     "prnu_profile_end": (C.c_int, [_P, C.POINTER(prnu_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
+    "prnu_debug_set": (C.c_int, [_P, C.c_int, C.c_int]),
 }
 EXPORTED = tuple(_SIGNATURES)
 
@@ -290,6 +292,9 @@ class Context:
         t = prnu_tuning()
         _check(lib().prnu_get_tuning(self.h, H, W, C.byref(t)), "prnu_get_tuning")
         return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant, persistent=t.persistent)
+
+    def prnu_debug_set(self, key, value):
+        _check(lib().prnu_debug_set(self.h, key, value), "prnu_debug_set")
 
     def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave, variant=0, persistent=0):
         t = prnu_tuning(col_width, pairs_per_block, wave, variant, persistent)

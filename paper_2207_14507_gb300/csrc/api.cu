@@ -257,6 +257,14 @@ static std::vector<FpDesc> fp_descs(const SearchCall& call) {
   return d;
 }
 
+// A bounded device-side wait (a TMA copy of the column pass, a dependency of
+// the persistent kernel) gave up: clear both flags and fail the call.
+[[noreturn]] static void report_device_abort(prnu_ctx* c, cudaStream_t s, const char* what) {
+  *c->h_err = 0;
+  PRNU_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+  throw Error{PRNU_EDEVICE_ABORT, what};
+}
+
 void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, double* d_all, bool naive,
                     cudaStream_t s) {
   const int H = call.H, W = call.W, Wh = W / 2;
@@ -276,11 +284,8 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   }
   const int slots = persistent ? kPersistSlots : wave;
 
-  if (*c->h_err) {   // a persistent launch or a TMA wait of an earlier asynchronous call gave up
-    *c->h_err = 0;
-    PRNU_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    throw Error{PRNU_EDEVICE_ABORT, "a device-side wait of an earlier call timed out; its results are invalid"};
-  }
+  if (*c->h_err)   // a bounded wait of an earlier asynchronous call gave up
+    report_device_abort(c, s, "a bounded device-side wait of an earlier call timed out; its results are invalid");
   PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->last_done, 0));
   for (auto& f : call.fps) PRNU_CUDA_TRY(cudaStreamWaitEvent(s, f->ready, 0));
   ensure_buf(c, c->ws_items, sizeof(WorkItem) * std::max(n, 1));
@@ -322,6 +327,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.prow = prow;
   a.pcol = pcol;
   a.err = c->d_err;
+  a.stall = c->debug_stall;
   a.pairs_per_block = naive ? 2 : tn.ppb;
   a.col_log2 = tn.col_log2;
   a.row_threads = rowT;
@@ -439,10 +445,7 @@ static int search_common(prnu_ctx* ctx, const void* d_resid, int dtype, const fl
     if (!dev_out) {
       PRNU_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(prnu_result) * (size_t)F * P, cudaMemcpyDeviceToHost, s));
       PRNU_CUDA_TRY(cudaStreamSynchronize(s));
-      if (*ctx->h_err) {
-        *ctx->h_err = 0;
-        throw Error{PRNU_EDEVICE_ABORT, "a device-side wait of the persistent kernel timed out"};
-      }
+      if (*ctx->h_err) report_device_abort(ctx, s, "a bounded device-side wait timed out; the results are invalid");
     }
   });
 }
@@ -788,6 +791,15 @@ int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
     out->wave = t.wave;
     out->variant = t.variant;
     out->persistent = t.persistent;
+  });
+}
+
+int prnu_debug_set(prnu_ctx* ctx, int key, int value) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(key == PRNU_DEBUG_STALL_DEVICE_WAITS, "unknown debug key");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->debug_stall = value ? 1 : 0;
   });
 }
 

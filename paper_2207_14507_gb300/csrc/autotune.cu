@@ -133,8 +133,9 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
         PRNU_CUDA_TRY(cudaEventElapsedTime(&m, e0, e1));
         ms = std::min(ms, m);
       }
-      if (*ctx->h_err) {   // a persistent launch gave up: never pick it
+      if (*ctx->h_err) {   // a bounded device-side wait gave up: never pick this configuration
         *ctx->h_err = 0;
+        PRNU_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
         continue;
       }
       if (ms < best_ms) {

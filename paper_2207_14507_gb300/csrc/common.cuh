@@ -77,6 +77,7 @@ struct PassArgs {
   CandResult* const* result_ptrs;
   const void* const* frame_ptrs;
   int* err;                   // device flag set when a bounded device-side wait gives up (may be nullptr)
+  int stall;                  // test hook: 1 = every bounded wait expects one arrival too many
 };
 
 __device__ __forceinline__ WorkItem item_of(const PassArgs& a, int slot) {

@@ -199,6 +199,7 @@ struct prnu_ctx {
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up
+  int debug_stall = 0;            // prnu_debug_set(PRNU_DEBUG_STALL_DEVICE_WAITS)
   std::vector<char> h_stage;      // staging for host->device descriptors
   char* h_pinned = nullptr;
   size_t h_pinned_bytes = 0;

@@ -221,7 +221,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     }
     __syncthreads();
     if (t == 0) {
-      mbar_expect_tx(&s_bar, H * NC * 8);
+      mbar_expect_tx(&s_bar, H * NC * 8 + (a.stall ? 16 : 0));   // the test hook waits for bytes that never come
 #pragma unroll 1
       for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, ws * H + b * BR, &s_bar);
     }
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(RT * PPB, RT * PPB <= 384 ? 2 : 1)
           dep = p.ri_done + g;
           need = NRI;
         }
-        s_ok = dep ? wait_count(dep, need, p.error) : 1;
+        s_ok = dep ? wait_count(dep, need + a.stall, p.error) : 1;   // the test hook waits for one count too many
       }
       __syncthreads();
       const bool ok = s_ok;

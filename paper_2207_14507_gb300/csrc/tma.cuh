@@ -29,20 +29,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// One poll: true once phase `phase` has completed; while it has not, the
+// thread may be suspended for up to about 1 us (suspend-time hint) first.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(1000u)
       : "memory");
   return ok != 0;
 }
 
-// Wait for phase `phase` of the barrier, at most `limit` polls (each poll
-// blocks for a hardware-chosen interval, well under a microsecond).
+// Wait for phase `phase` of the barrier, at most `limit` polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, long long limit) {
   for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, phase)) return true;
