@@ -117,6 +117,52 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
     row_store16(A, t, v);
   }
   __syncthreads();
+  float2* o0 = a.spec + ((size_t)ws * H + y0) * Wh;
+  float2* o1 = o0 + Wh;
+  using LS = Stg<SP, SP::S - 1>;
+  constexpr bool kShflSplit = SP::S == 3 && LS::NB == T && T % 32 == 0 && LS::R % 2 == 0;
+  if constexpr (kShflSplit) {
+    // The last stage with butterflies j and Ns - j on partner lanes l and
+    // l ^ 16 of one warp (j = 0 and Ns/2, their own mirrors, share lane pair
+    // 0): output x = j + r*Ns has its mirror W - x at r' = R-1-r of butterfly
+    // Ns - j, so the split of z = G_a + i G_b takes the mirror bins by shuffle
+    // instead of a shared-memory round trip.
+    row_stage<SP, 1, T, false>(A, B, t);
+    __syncthreads();
+    constexpr int R = LS::R, NS = LS::NS, LB = NS / 16 * 18;
+    const int p = (t >> 5) * 16 + (t & 15), h = (t >> 4) & 1;
+    const int j = p == 0 ? (h ? NS / 2 : 0) : (h ? NS - p : p);
+    float2 v[1][R];
+    const float2* src = B + rp2(j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[0][r] = src[r * LB];
+    twiddle_tab<R, NS, false, 1>(v, j);
+    Dft<R, false>::run(v[0]);
+    float2 m[R / 2];
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      m[r].x = __shfl_xor_sync(0xffffffffu, v[0][R - 1 - r].x, 16);
+      m[r].y = __shfl_xor_sync(0xffffffffu, v[0][R - 1 - r].y, 16);
+    }
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      const int x = j + r * NS;   // < W/2
+      const float2 zk = v[0][r];
+      float2 P, Q;
+      if (j == 0 && r == 0) {     // bin 0 packs (DC, Nyquist); the Nyquist bin W/2 is r = R/2 here
+        const float2 zn = v[0][R / 2];
+        P = make_float2(zk.x, zn.x);
+        Q = make_float2(zk.y, zn.y);
+      } else {
+        const float2 zm = j == 0 ? v[0][R - r] : j == NS / 2 ? v[0][R - 1 - r] : m[r];
+        P = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        Q = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+      }
+      o0[x] = P;
+      o1[x] = Q;
+    }
+    return;
+  }
   const float2* res = B;
   row_stage<SP, 1, T, false>(A, B, t);
   __syncthreads();
@@ -127,8 +173,6 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
   }
   // split z = G_a + i G_b into the two rows' half spectra (packed: bin 0
   // holds (DC, Nyquist))
-  float2* o0 = a.spec + ((size_t)ws * H + y0) * Wh;
-  float2* o1 = o0 + Wh;
   constexpr int MI = (Wh + T - 1) / T;
   const float2* rk = res + rp2(t);
   const float2* rm = res - t + 2 * ((-t) >> 4);   // + rp2(X) gives rp2(X - t) for X = 0 mod 16
