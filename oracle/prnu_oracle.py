@@ -11,6 +11,8 @@ What it computes (arXiv 2207.14507):
 * circular cross-correlation over all shifts, C(d) = sum_x X(x) K0(x + d)
 * PCE with an 11x11 cyclic exclusion around the signed peak         (Eq. 3)
 * exhaustive search over the (lambda, theta) grid, arg-max PCE      (Sec. 3.2, Eq. 8)
+* the iterative breadth-first correction: progressively narrower
+  (lambda, theta) neighbourhoods of the previous estimate          (Sec. 3.2, Eq. 8)
 
 Everything is float64 NumPy, written as the plain definition; the only library
 primitives are numpy's FFTs (for the correlation) and array arithmetic.
@@ -34,6 +36,7 @@ __all__ = [
     "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
+    "correction_nodes", "correction",
 ]
 
 # Eq. 3: the exclusion neighbourhood D around the correlation peak is 11 x 11, cyclic.
@@ -258,3 +261,63 @@ def grid_search(residuals, fingerprints, grid, windows=None, on_candidate=None):
             row.append(b)
         best.append(row)
     return best, all_pce
+
+
+# ----------------------------------------------------------------------------- correction (Sec. 3.2, Eq. 8)
+
+# Reading of Eq. 8, whose printed step sizes (0.01^-n, 0.1^-n) would widen the
+# neighbourhoods: iteration n searches lambda(n-1) + a * 0.01 * 10^-(n-1) and
+# theta(n-1) + b * 0.1 * 10^-(n-1) degrees for a, b in -5..5, except that the
+# first iteration takes theta on the denser grid of the text, b in -50..50
+# (-5..5 degrees in steps of 0.1 around the start).  Node values are float32,
+# rounded once from the float64 sum of the float32 centre and a * float32(step).
+CORR_HALF = 5
+CORR_HALF_TH1 = 50
+
+
+def _corr_step(n: int):
+    return _f32(0.01 * 10.0 ** -(n - 1)), _f32(0.1 * 10.0 ** -(n - 1))
+
+
+def correction_nodes(lam_c: float, th_c: float, n: int, th_half1: int = CORR_HALF_TH1):
+    """Scale and angle nodes of iteration n (1-based) around the centre
+    (lam_c, th_c): returns (lams, ths), float values of float32 nodes."""
+    sl, st = _corr_step(n)
+    hb = th_half1 if n == 1 else CORR_HALF
+    lams = [_f32(float(np.float32(lam_c)) + a * sl) for a in range(-CORR_HALF, CORR_HALF + 1)]
+    ths = [_f32(float(np.float32(th_c)) + b * st) for b in range(-hb, hb + 1)]
+    return lams, ths
+
+
+def correction(R: np.ndarray, K0: np.ndarray, lam0: float = 1.0, th0: float = 0.0, max_iter: int = 3,
+               th_half1: int = CORR_HALF_TH1, K0_spectrum=None):
+    """The correction operator of Sec. 3.2 for one frame residual R and one
+    fingerprint term K0: at each iteration an exhaustive search over the
+    iteration's nodes (ties to the lowest index, scale-major); stop when the
+    best node is the previous estimate (the centre) or after max_iter
+    iterations.  Returns (best, iters, path): best = dict of the highest PCE
+    seen over all iterations (earliest on ties) with lam, th_deg, cand (index in
+    its iteration's node grid), iter (1-based); path = the estimate after each
+    iteration."""
+    if K0_spectrum is None:
+        K0_spectrum = np.fft.rfft2(K0)
+    lam_c, th_c = _f32(lam0), _f32(th0)
+    best, path = None, []
+    n = 0
+    for n in range(1, max_iter + 1):
+        lams, ths = correction_nodes(lam_c, th_c, n, th_half1)
+        nb = len(ths)
+        it_best = None
+        for a, lam in enumerate(lams):
+            for b, th in enumerate(ths):
+                r = score(R, K0, lam, th, K0_spectrum)
+                if it_best is None or r["pce"] > it_best["pce"]:
+                    it_best = dict(r, lam=lam, th_deg=th, cand=a * nb + b, iter=n)
+        if best is None or it_best["pce"] > best["pce"]:
+            best = it_best
+        path.append((it_best["lam"], it_best["th_deg"]))
+        centre = CORR_HALF * nb + (nb - 1) // 2
+        if it_best["cand"] == centre:
+            break
+        lam_c, th_c = it_best["lam"], it_best["th_deg"]
+    return best, n, path

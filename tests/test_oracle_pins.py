@@ -330,3 +330,69 @@ def test_fingerprint_term_makes_correlation_blind_to_offsets():
     X = rng.standard_normal((24, 30))
     K0 = oracle.fingerprint_term(rng.standard_normal((24, 30)) + 0.7)
     np.testing.assert_allclose(oracle.xcorr(X + 42.0, K0), oracle.xcorr(X, K0), atol=1e-9)
+
+
+# ------------------------------------------------------------------ iterative correction (Sec. 3.2, Eq. 8)
+
+def test_correction_nodes_are_centred_and_spaced_by_the_iteration_step():
+    """Iteration n searches 11 scales spaced 0.01*10^-(n-1) and angles spaced
+    0.1*10^-(n-1) degrees around the previous estimate (101 angles, -5..5
+    degrees, at n = 1); the centre node is the previous estimate exactly."""
+    lam_c, th_c = float(np.float32(1.0234)), float(np.float32(-0.37))
+    for n, (sl, st) in ((1, (0.01, 0.1)), (2, (0.001, 0.01)), (3, (1e-4, 1e-3))):
+        lams, ths = oracle.correction_nodes(lam_c, th_c, n)
+        nb = 101 if n == 1 else 11
+        assert len(lams) == 11 and len(ths) == nb
+        assert lams[5] == lam_c and ths[(nb - 1) // 2] == th_c
+        np.testing.assert_allclose(np.diff(lams), sl, rtol=0, atol=2.5e-7)   # float32 nodes near 1
+        np.testing.assert_allclose(np.diff(ths), st, rtol=0, atol=1e-6)
+        assert all(np.float32(v) == v for v in lams + ths)
+
+
+def _planted(lam, th, sy, sx, H=256, W=256):
+    K = synth.fingerprint_field(H, W, synth.rng_for(1, 0))   # stream 0: the fingerprint
+    frame = synth.make_frames(K, np.array([[lam, th, sy, sx]], np.float64), 1)[0]
+    return oracle.prnu_residual(frame)[0], oracle.fingerprint_term(K)
+
+
+def _check_correction_path(best, iters, path, max_iter=3):
+    """The stopping rule and monotonicity: the search stops early only when an
+    iteration returns its centre; every iteration includes its centre, so the
+    best PCE never falls below the first iteration's."""
+    assert 1 <= iters <= max_iter and len(path) == iters
+    if iters < max_iter:
+        assert path[-1] == path[-2]
+    for k in range(1, iters - 1):
+        assert path[k] != path[k - 1]
+
+
+def test_correction_recovers_a_planted_lattice_transform():
+    """A frame stabilised with a scale and angle that are nodes of the first
+    iteration: the first iteration finds them and the shift exactly; the finer
+    iterations follow the PCE maximum (which the bilinear generator leaves a
+    fraction of a node step away) and stay within one second-iteration step of
+    the planted values."""
+    lams, ths = oracle.correction_nodes(1.0, 0.0, 1, th_half1=5)
+    R, K0 = _planted(lams[7], ths[8], 3, -5)                # lambda 1.02, theta 0.3 degrees
+    best, iters, path = oracle.correction(R, K0, th_half1=5)
+    _check_correction_path(best, iters, path)
+    assert path[0] == (lams[7], ths[8])
+    first = oracle.correction(R, K0, max_iter=1, th_half1=5)[0]
+    assert (first["lam"], first["th_deg"], first["dy"], first["dx"]) == (lams[7], ths[8], 3, -5)
+    assert (best["dy"], best["dx"]) == (3, -5) and best["pce"] >= first["pce"] > 60
+    assert abs(best["lam"] - lams[7]) <= 0.001 and abs(best["th_deg"] - ths[8]) <= 0.01
+
+
+def test_correction_narrows_onto_an_off_lattice_transform():
+    """Scale and angle between the nodes of the first iteration: later
+    iterations move the estimate to within one second-iteration step of the
+    planted values and never lower the best PCE."""
+    lam, th = 1.0137, -0.262
+    R, K0 = _planted(lam, th, -2, 4)
+    best, iters, path = oracle.correction(R, K0, th_half1=5)
+    _check_correction_path(best, iters, path)
+    assert iters >= 2
+    assert abs(best["lam"] - lam) <= 0.001 and abs(best["th_deg"] - th) <= 0.01
+    assert (best["dy"], best["dx"]) == (-2, 4)
+    first = oracle.correction(R, K0, max_iter=1, th_half1=5)[0]
+    assert best["pce"] >= first["pce"]
