@@ -164,6 +164,35 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
                           const prnu_grid* grid, const prnu_window* windows,
                           prnu_result* out, double* d_all_pce, prnu_stream stream);
 
+/* The correction operator of Sec. 3.2: for every (frame f, fingerprint p)
+ * pair a breadth-first search over (lambda, theta) that maximises the PCE.
+ * Iteration n (1-based) searches, around the previous estimate
+ * (lambda(n-1), theta(n-1)), the nodes
+ *     lambda(n-1) + a * 0.01 * 10^-(n-1),        a in -5..5,
+ *     theta(n-1)  + b * 0.1 * 10^-(n-1) degrees, b in -5..5
+ *     (b in -th_half1..th_half1 at n = 1: the text's denser first angle grid,
+ *      -5..5 degrees in steps of 0.1 for th_half1 = 50),
+ * each node the float32 rounding of the double sum centre + a * float32(step);
+ * that is the reading of Eq. 8, whose printed steps 0.01^-n and 0.1^-n would
+ * widen the neighbourhoods.  An iteration keeps its node of highest PCE (ties
+ * to the lowest index, scale-major); the search stops when that node is its
+ * centre (the estimate did not change) or after max_iter iterations, and
+ * returns the best PCE seen over all iterations (the earliest on ties).
+ * Every iteration runs the hot path of eis_grid_search over all pairs still
+ * searching.
+ *  d_resid, dtype, d_scale, F, H, W, fp_handles, P: as eis_grid_search.
+ *  init_lam, init_th: host float [F*P] start estimates (index f*P + p), or NULL
+ *      for lambda(0) = 1 and theta(0) = 0.
+ *  max_iter >= 1 (the paper uses 3); th_half1 >= 0 (0 selects 50).
+ *  out:   host prnu_result [F*P]: the best node (lam, th_deg, shift, PCE);
+ *         cand_idx = a'*nb + b' within the node grid of the iteration that
+ *         found it (a', b' >= 0, nb = 2*th_half1 + 1 at n = 1, else 11).
+ *  iters: host int [F*P], iterations run per pair, or NULL.
+ * Synchronous (waits for `stream`).  Errors as eis_grid_search. */
+int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                   const uint64_t* fp_handles, int P, const float* init_lam, const float* init_th,
+                   int max_iter, int th_half1, prnu_result* out, int* iters, prnu_stream stream);
+
 /* PCE of one aligned pair (Eq. 3, no warp): d_X device float [H][W] against the
  * cached fingerprint `fp_handle`.  Host outputs; any of them may be NULL.
  * Synchronous (waits for `stream`). */

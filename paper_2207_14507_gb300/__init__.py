@@ -80,6 +80,8 @@ _SIGNATURES = {
                                   C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "eis_correction": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int,
+                                 _P, _P, C.c_int, C.c_int, _P, _P, _P]),
     "pce_score": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                             C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
     "pce_score_noalloc": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
@@ -210,6 +212,28 @@ class Context:
 
     def prnu_fingerprint_release(self, handle: int):
         _check(lib().prnu_fingerprint_release(self.h, handle), "prnu_fingerprint_release")
+
+    def eis_correction(self, resid, fp_handles, init_lam=None, init_th=None, max_iter=3, th_half1=50, scale=None,
+                       stream=None):
+        """The iterative correction of Sec. 3.2 for every (frame, fingerprint)
+        pair.  resid: CUDA tensor [F, H, W]; init_lam, init_th: array-likes of
+        F*P start estimates or None (1 and 0).  Returns (results [F, P] of
+        RESULT_DTYPE, iterations run [F, P])."""
+        import torch
+        F, H, W = resid.shape
+        dt = {torch.float32: PRNU_F32, torch.float16: PRNU_F16, torch.bfloat16: PRNU_BF16}[resid.dtype]
+        P = len(fp_handles)
+        hs = (C.c_uint64 * max(P, 1))(*fp_handles)
+        out = np.zeros((F, P), dtype=RESULT_DTYPE)
+        its = np.zeros((F, P), dtype=np.int32)
+        il = None if init_lam is None else np.ascontiguousarray(np.asarray(init_lam, np.float32).reshape(F * P))
+        it_ = None if init_th is None else np.ascontiguousarray(np.asarray(init_th, np.float32).reshape(F * P))
+        _check(lib().eis_correction(self.h, _ptr(resid), dt, _ptr(scale), F, H, W, hs, P,
+                                    None if il is None else il.ctypes.data_as(_P),
+                                    None if it_ is None else it_.ctypes.data_as(_P), max_iter, th_half1,
+                                    out.ctypes.data_as(_P), its.ctypes.data_as(_P), _stream(stream)),
+               "eis_correction")
+        return out, its
 
     def eis_grid_search(self, resid, fp_handles, grid, windows=None, scale=None, out=None, all_pce=None,
                         stream=None, naive=False):

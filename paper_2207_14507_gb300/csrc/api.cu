@@ -450,11 +450,128 @@ static int search_common(prnu_ctx* ctx, const void* d_resid, int dtype, const fl
   });
 }
 
+// One item per node of a (frame, fingerprint) pair's node grid lams x ths.
+static void add_pair_items(SearchCall& call, int f, int p, int group, const std::vector<float>& lams,
+                           const std::vector<float>& ths) {
+  const int nb = (int)ths.size();
+  for (int a = 0; a < (int)lams.size(); ++a) {
+    const double L = (double)lams[a];
+    PRNU_CHECK_ARG(L > 0 && std::isfinite(L), "correction scales must be positive");
+    for (int b = 0; b < nb; ++b) {
+      const double t = (double)ths[b] * 3.14159265358979323846 / 180.0;
+      const double cs = cos(t), sn = sin(t);
+      WorkItem it;
+      it.frame = f;
+      it.fp = p;
+      it.cand = a * nb + b;
+      it.group = group;
+      it.a11 = (float)(cs / L);
+      it.a12 = (float)(sn / L);
+      it.a21 = (float)(-sn / L);
+      it.a22 = (float)(cs / L);
+      it.lam = lams[a];
+      it.th_deg = ths[b];
+      call.items.push_back(it);
+    }
+  }
+}
+
 }  // namespace prnu
 
 using namespace prnu;
 
 extern "C" {
+
+int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                   const uint64_t* fp_handles, int P, const float* init_lam, const float* init_th, int max_iter,
+                   int th_half1, prnu_result* out, int* iters, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 0 && P >= 0, "F and P must be >= 0");
+    if (F == 0 || P == 0) return;
+    PRNU_CHECK_ARG(d_resid && fp_handles && out, "NULL argument");
+    PRNU_CHECK_ARG(dtype == kF32 || dtype == kF16 || dtype == kBF16, "unknown residual dtype");
+    PRNU_CHECK_ARG(max_iter >= 1, "max_iter must be >= 1");
+    PRNU_CHECK_ARG(th_half1 >= 0 && th_half1 <= 4096, "th_half1 must be in 0..4096");
+    validate_shape(H, W);
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int kHalf = 5;
+    const int hb1 = th_half1 ? th_half1 : 50;
+    const int G = F * P;
+    std::vector<std::shared_ptr<Fingerprint>> fps;
+    for (int p = 0; p < P; ++p) {
+      auto f = find_fp(ctx, fp_handles[p]);
+      PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs from the frames");
+      fps.push_back(f);
+    }
+    std::vector<float> cl(G), ct(G);
+    for (int g = 0; g < G; ++g) {
+      cl[g] = init_lam ? init_lam[g] : 1.0f;
+      ct[g] = init_th ? init_th[g] : 0.0f;
+      PRNU_CHECK_ARG(std::isfinite(cl[g]) && cl[g] > 0 && std::isfinite(ct[g]), "bad start estimate");
+    }
+    std::vector<prnu_result> best(G);
+    std::vector<char> have(G, 0), active(G, 1);
+    std::vector<int> run(G, 0);
+    ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * (size_t)G);
+    prnu_result* d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
+    std::vector<prnu_result> res;
+    for (int n = 1; n <= max_iter; ++n) {
+      // float32 steps 0.01 * 10^-(n-1) and 0.1 * 10^-(n-1) degrees
+      const float sl = (float)(0.01 * std::pow(10.0, -(n - 1))), st = (float)(0.1 * std::pow(10.0, -(n - 1)));
+      const int hb = n == 1 ? hb1 : kHalf;
+      SearchCall call;
+      call.resid = d_resid;
+      call.rdtype = dtype;
+      call.scale = d_scale;
+      call.F = F;
+      call.H = H;
+      call.W = W;
+      call.fps = fps;
+      call.cmax = (2 * kHalf + 1) * (2 * hb + 1);
+      std::vector<int> who;   // active pair of each group of this iteration
+      for (int g = 0; g < G; ++g) {
+        if (!active[g]) continue;
+        std::vector<float> lams, ths;
+        for (int a = -kHalf; a <= kHalf; ++a) lams.push_back((float)((double)cl[g] + (double)a * (double)sl));
+        for (int b = -hb; b <= hb; ++b) ths.push_back((float)((double)ct[g] + (double)b * (double)st));
+        call.group_start.push_back((int)call.items.size());
+        add_pair_items(call, g / P, g % P, (int)who.size(), lams, ths);
+        who.push_back(g);
+      }
+      if (who.empty()) break;
+      call.group_start.push_back((int)call.items.size());
+      enqueue_search(ctx, call, d_out, nullptr, false, s);
+      res.resize(who.size());
+      PRNU_CUDA_TRY(cudaMemcpyAsync(res.data(), d_out, sizeof(prnu_result) * who.size(), cudaMemcpyDeviceToHost, s));
+      PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*ctx->h_err) report_device_abort(ctx, s, "a bounded device-side wait timed out; the results are invalid");
+      const int nb = 2 * hb + 1, centre = kHalf * nb + hb;
+      for (size_t k = 0; k < who.size(); ++k) {
+        const int g = who[k];
+        const prnu_result& r = res[k];
+        ++run[g];
+        if (!have[g] || r.pce > best[g].pce) {
+          best[g] = r;
+          have[g] = 1;
+        }
+        if (r.cand_idx == centre || r.cand_idx < 0) {
+          active[g] = 0;   // the estimate did not change
+        } else {
+          cl[g] = r.lam;
+          ct[g] = r.th_deg;
+        }
+      }
+    }
+    for (int g = 0; g < G; ++g) {
+      out[g] = best[g];
+      if (iters) iters[g] = run[g];
+    }
+  });
+}
+
 
 const char* prnu_last_error(void) { return g_last_error.c_str(); }
 
