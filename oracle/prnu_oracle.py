@@ -7,6 +7,8 @@ What it computes (arXiv 2207.14507):
   denoiser of Sec. 2.2 by a 3x3 Wiener filter), weighted by the frame
   intensity, R = I * W(I), the fingerprint-matching term of Eq. 2/3;
 * fingerprint term K0 = K - mean(K)                                 (Eq. 1, 3)
+* reference fingerprint from L frames,
+  K = (sum_l I_l W(I_l)) / (sum_l I_l^2), pixel-wise                (Eq. 2)
 * inverse similarity warp of R, bilinear, zero outside the frame    (Eq. 4, Sec. 3.2)
 * circular cross-correlation over all shifts, C(d) = sum_x X(x) K0(x + d)
 * PCE with an 11x11 cyclic exclusion around the signed peak         (Eq. 3)
@@ -36,7 +38,7 @@ __all__ = [
     "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
-    "correction_nodes", "correction",
+    "correction_nodes", "correction", "fingerprint_estimate",
 ]
 
 # Eq. 3: the exclusion neighbourhood D around the correlation peak is 11 x 11, cyclic.
@@ -321,3 +323,21 @@ def correction(R: np.ndarray, K0: np.ndarray, lam0: float = 1.0, th0: float = 0.
             break
         lam_c, th_c = it_best["lam"], it_best["th_deg"]
     return best, n, path
+
+
+# ----------------------------------------------------------------------------- fingerprint estimation (Eq. 2)
+
+def fingerprint_estimate(frames) -> np.ndarray:
+    """Eq. 2: the reference fingerprint of a device from L of its frames,
+    K = (sum_l I_l * W(I_l)) / (sum_l I_l * I_l), every operation pixel-wise,
+    with W the residual of ``prnu_residual``; 0 where the denominator is 0."""
+    num = None
+    den = None
+    for frame in frames:
+        I = np.asarray(frame, dtype=np.float64)
+        R = prnu_residual(I, weight_by_intensity=True)[0]          # I * W(I)
+        num = R if num is None else num + R
+        den = I * I if den is None else den + I * I
+    out = np.zeros_like(num)
+    np.divide(num, den, out=out, where=den > 0)
+    return out

@@ -396,3 +396,40 @@ def test_correction_narrows_onto_an_off_lattice_transform():
     assert (best["dy"], best["dx"]) == (-2, 4)
     first = oracle.correction(R, K0, max_iter=1, th_half1=5)[0]
     assert best["pce"] >= first["pce"]
+
+
+# ------------------------------------------------------------------ fingerprint estimation (Eq. 2)
+
+def _flat_frames(L, H=128, W=128, seed=5):
+    """Bright, slowly varying frames of one sensor (multiplicative PRNU K, sensor
+    noise of 2 grey levels), the frames Eq. 2 is meant for."""
+    rng = np.random.default_rng(seed)
+    K = synth.fingerprint_field(H, W, rng)
+    yy, xx = np.mgrid[0:H, 0:W]
+    frames = []
+    for l in range(L):
+        base = 120 + 40 * np.sin(0.01 * (xx + 3 * l)) * np.cos(0.013 * (yy - 2 * l))
+        frames.append(np.clip(np.round(base * (1 + K) + rng.normal(0, 2, (H, W))), 0, 255))
+    return K, frames
+
+
+def test_fingerprint_estimate_recovers_the_sensor_pattern():
+    """Eq. 2 on 16 flat frames: the estimate correlates with the planted PRNU."""
+    K, frames = _flat_frames(16)
+    Kh = oracle.fingerprint_estimate(frames)
+    assert np.corrcoef(Kh.ravel(), K.ravel())[0, 1] > 0.85
+
+
+def test_fingerprint_estimate_is_a_ratio_of_sums():
+    """Repeating every frame changes neither sum's ratio; scaling every frame by
+    a constant changes neither (the residual is homogeneous of degree 1); the
+    frame order does not matter; a pixel dark in every frame gives 0."""
+    _, frames = _flat_frames(3)
+    Kh = oracle.fingerprint_estimate(frames)
+    np.testing.assert_allclose(oracle.fingerprint_estimate(frames + frames), Kh, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oracle.fingerprint_estimate([2.0 * f for f in frames]), Kh, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oracle.fingerprint_estimate(frames[::-1]), Kh, rtol=0, atol=1e-15)
+    dark = [f.copy() for f in frames]
+    for f in dark:
+        f[10, 20] = 0.0
+    assert oracle.fingerprint_estimate(dark)[10, 20] == 0.0
