@@ -115,6 +115,18 @@ uint64_t prnu_launch_count(const prnu_ctx* ctx);
 int prnu_residual(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch,
                   int flags, int out_dtype, void* d_out, float* d_scale, prnu_stream stream);
 
+/* Reference fingerprint of a device from L of its frames (Eq. 2):
+ *     K = (sum_l I_l * W(I_l)) / (sum_l I_l * I_l),   every operation pixel-wise,
+ * W the residual of prnu_residual (3x3 Wiener, per-frame noise power); 0 where
+ * every frame is 0.  Sums in double; frames are taken 16 at a time.
+ *  d_frames: device uint8, frame l row y at d_frames + (l*H + y)*pitch, pitch >= W
+ *            (0 means W).
+ *  d_K:      device float [H][W], written.
+ * H, W >= 1, L >= 1.  Asynchronous on `stream`.
+ * Errors: PRNU_EINVAL (sizes, NULL), PRNU_ENOMEM (workspace over the budget). */
+int prnu_fingerprint_estimate(prnu_ctx* ctx, const uint8_t* d_frames, int L, int H, int W, size_t pitch,
+                              float* d_K, prnu_stream stream);
+
 /* Fingerprint term (Eq. 1-3): cache the 2-D spectrum of K0 = K - mean(K) on the
  * device, in the library's packed half-spectrum layout, stored as FP32 or FP16
  * (store_dtype PRNU_F32 | PRNU_F16; PRNU_BF16 is stored as FP16).  d_K: device

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "prnu_residual": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int, C.c_int, _P, _P, _P]),
     "prnu_fingerprint_term": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), _P]),
     "prnu_fingerprint_release": (C.c_int, [_P, C.c_uint64]),
+    "prnu_fingerprint_estimate": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, _P, _P]),
     "eis_grid_search": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int,
                                   C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
@@ -212,6 +213,17 @@ class Context:
 
     def prnu_fingerprint_release(self, handle: int):
         _check(lib().prnu_fingerprint_release(self.h, handle), "prnu_fingerprint_release")
+
+    def prnu_fingerprint_estimate(self, frames, out=None, pitch=0, stream=None):
+        """Eq. 2 reference fingerprint from frames (CUDA uint8 [L, H, W]); returns
+        (or fills) a CUDA float32 tensor [H, W]."""
+        import torch
+        L, H, W = frames.shape
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=frames.device)
+        _check(lib().prnu_fingerprint_estimate(self.h, _ptr(frames), L, H, W, pitch, _ptr(out), _stream(stream)),
+               "prnu_fingerprint_estimate")
+        return out
 
     def eis_correction(self, resid, fp_handles, init_lam=None, init_th=None, max_iter=3, th_half1=50, scale=None,
                        stream=None):

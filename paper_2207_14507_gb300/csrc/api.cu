@@ -635,7 +635,7 @@ int prnu_destroy(prnu_ctx* ctx) {
     }
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
-                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad})
+                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     ctx_free(ctx, ctx->d_err, sizeof(int));
@@ -674,6 +674,44 @@ int prnu_residual(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, s
       scale = reinterpret_cast<float*>(reinterpret_cast<char*>(partials) + ((sizeof(double) * np + 255) & ~(size_t)255));
     launch_residual(d_frames, F, H, W, pitch, flags, out_dtype, d_out, scale, acc, partials, (int)np, s,
                     ctx->launches);
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+  });
+}
+
+int prnu_fingerprint_estimate(prnu_ctx* ctx, const uint8_t* d_frames, int L, int H, int W, size_t pitch, float* d_K,
+                              prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && d_frames && d_K, "NULL argument");
+    PRNU_CHECK_ARG(L >= 1, "L must be >= 1");
+    PRNU_CHECK_ARG(H >= 1 && W >= 1 && (long long)H * W <= (1LL << 26), "bad frame size");
+    if (pitch == 0) pitch = (size_t)W;
+    PRNU_CHECK_ARG(pitch >= (size_t)W, "pitch < W");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    constexpr int kChunk = 16;
+    const size_t n = (size_t)H * W;
+    const int C0 = std::min(L, kChunk);
+    const size_t rb = (sizeof(float) * n * C0 + 255) / 256 * 256, db = (sizeof(double) * n + 255) / 256 * 256;
+    ensure_buf(ctx, ctx->ws_fpest, rb + 2 * db);
+    char* base = reinterpret_cast<char*>(ctx->ws_fpest.p);
+    float* R = reinterpret_cast<float*>(base);
+    double* num = reinterpret_cast<double*>(base + rb);
+    double* den = reinterpret_cast<double*>(base + rb + db);
+    const size_t np = residual_partials_needed(C0, H, W);
+    ensure_buf(ctx, ctx->ws_resid, sizeof(unsigned long long) * C0 + 256 + sizeof(double) * np);
+    auto* acc = reinterpret_cast<unsigned long long*>(ctx->ws_resid.p);
+    auto* partials = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->ws_resid.p) +
+                                               ((sizeof(unsigned long long) * C0 + 255) & ~(size_t)255));
+    for (int l0 = 0; l0 < L; l0 += kChunk) {
+      const int Lc = std::min(kChunk, L - l0);
+      const uint8_t* fr = d_frames + (size_t)l0 * H * pitch;
+      launch_residual(fr, Lc, H, W, pitch, PRNU_WEIGHT_BY_INTENSITY, kF32, R, nullptr, acc, partials,
+                      (int)residual_partials_needed(Lc, H, W), s, ctx->launches);
+      launch_fp_estimate_accumulate(R, fr, pitch, Lc, H, W, num, den, l0 == 0, s, ctx->launches);
+    }
+    launch_fp_estimate_divide(num, den, d_K, n, s, ctx->launches);
     PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
   });
 }

@@ -137,6 +137,11 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
                      float* scale, unsigned long long* acc, double* partials, int max_partials, cudaStream_t s,
                      LaunchCounter& lc, const ResidLayout* lay = nullptr);
 size_t residual_partials_needed(int F, int H, int W);
+// Eq. 2 accumulation over Lc residuals R [Lc][H][W] (R = I W(I)) and their frames
+void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
+                                   double* num, double* den, bool first, cudaStream_t s, LaunchCounter& lc);
+void launch_fp_estimate_divide(const double* num, const double* den, float* K, size_t n, cudaStream_t s,
+                               LaunchCounter& lc);
 // dense [F][H][W] residuals -> the zero-bordered layout the compile-time-planned
 // kernels read (row pitch W + 3, pixel (0, 0) at W + 4, (H + 3)(W + 3) per frame)
 void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc);
@@ -195,7 +200,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist, ws_pad;
+      ws_persist, ws_pad, ws_fpest;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up

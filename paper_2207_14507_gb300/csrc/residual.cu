@@ -156,7 +156,46 @@ void apply_dispatch(int dtype, dim3 g, dim3 b, cudaStream_t s, const uint8_t* fr
     k_resid_apply<kBF16, MODE><<<g, b, 0, s>>>(frames, pitch, H, W, acc, weight, out, partials, scale, l);
 }
 
+// Eq. 2 sums over a chunk of Lc frames: num += sum_l R_l (R = I W(I)),
+// den += sum_l I_l^2, in double (first: start from zero).
+__global__ void k_fp_accumulate(const float* __restrict__ R, const uint8_t* __restrict__ frames, size_t pitch, int Lc,
+                                int H, int W, double* __restrict__ num, double* __restrict__ den, int first) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W) return;
+  const size_t p = (size_t)y * W + x;
+  double a = first ? 0.0 : num[p], b = first ? 0.0 : den[p];
+  for (int l = 0; l < Lc; ++l) {
+    a += (double)R[(size_t)l * H * W + p];
+    const double I = (double)frames[((size_t)l * H + y) * pitch + x];
+    b += I * I;
+  }
+  num[p] = a;
+  den[p] = b;
+}
+
+__global__ void k_fp_divide(const double* __restrict__ num, const double* __restrict__ den, float* __restrict__ K,
+                            size_t n) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) K[i] = den[i] > 0.0 ? (float)(num[i] / den[i]) : 0.f;
+}
+
 }  // namespace
+
+void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
+                                   double* num, double* den, bool first, cudaStream_t s, LaunchCounter& lc) {
+  ProfScope ps(lc, kKindResidual, s);
+  k_fp_accumulate<<<dim3((W + 255) / 256, H), 256, 0, s>>>(R, frames, pitch, Lc, H, W, num, den, first ? 1 : 0);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
+
+void launch_fp_estimate_divide(const double* num, const double* den, float* K, size_t n, cudaStream_t s,
+                               LaunchCounter& lc) {
+  ProfScope ps(lc, kKindResidual, s);
+  k_fp_divide<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(num, den, K, n);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
 
 void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc) {
   if (F == 0) return;

@@ -404,3 +404,30 @@ def test_autotune_picks_a_valid_configuration(ctx, prnu):
     best, ref = _oracle_search(wl)
     _assert_all_close(got, ref, FP32_TOL)
     _assert_best_equal(res, best)
+
+
+def test_fingerprint_estimate_matches_oracle(ctx, prnu):
+    """Eq. 2 through the C ABI: 20 frames (two chunks of the 16-frame
+    accumulation) of a non-square size given with a row pitch, against the
+    oracle pixel by pixel; and the estimate scores the sensor's frames."""
+    rng = np.random.default_rng(11)
+    L, H, W = 20, 96, 150
+    K = synth.fingerprint_field(H, W, rng)
+    yy, xx = np.mgrid[0:H, 0:W]
+    frames = np.empty((L, H, W), np.uint8)
+    for l in range(L):
+        base = 120 + 40 * np.sin(0.01 * (xx + 3 * l)) * np.cos(0.013 * (yy - 2 * l))
+        frames[l] = np.clip(np.round(base * (1 + K) + rng.normal(0, 2, (H, W))), 0, 255)
+    pitched = np.zeros((L, H, W + 10), np.uint8)
+    pitched[:, :, :W] = frames
+    d = torch.from_numpy(pitched).to(DEV)
+    Kd = torch.empty((H, W), device=DEV)
+    lib = prnu.lib()
+    rc = lib.prnu_fingerprint_estimate(ctx.h, prnu._ptr(d), L, H, W, W + 10, prnu._ptr(Kd), prnu._stream(None))
+    assert rc == prnu.PRNU_OK
+    got = Kd.cpu().numpy().astype(np.float64)
+    ref = oracle.fingerprint_estimate(frames)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert np.corrcoef(got.ravel(), K.ravel())[0, 1] > 0.85
+    same = ctx.prnu_fingerprint_estimate(torch.from_numpy(frames).to(DEV))     # dense frames, binding
+    np.testing.assert_array_equal(same.cpu().numpy(), Kd.cpu().numpy())
