@@ -15,6 +15,8 @@ What it computes (arXiv 2207.14507):
 * exhaustive search over the (lambda, theta) grid, arg-max PCE      (Sec. 3.2, Eq. 8)
 * the iterative breadth-first correction: progressively narrower
   (lambda, theta) neighbourhoods of the previous estimate          (Sec. 3.2, Eq. 8)
+* the EIS inversion of a video segment with the co-registration
+  supplied, the PCE vector gamma and its thresholded mean          (Algorithm 1, Sec. 3.2)
 
 Everything is float64 NumPy, written as the plain definition; the only library
 primitives are numpy's FFTs (for the correlation) and array arithmetic.
@@ -38,7 +40,7 @@ __all__ = [
     "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
-    "correction_nodes", "correction", "fingerprint_estimate",
+    "correction_nodes", "correction", "fingerprint_estimate", "similarity_from_homography", "invert_video", "TAU",
 ]
 
 # Eq. 3: the exclusion neighbourhood D around the correlation peak is 11 x 11, cyclic.
@@ -341,3 +343,55 @@ def fingerprint_estimate(frames) -> np.ndarray:
     out = np.zeros_like(num)
     np.divide(num, den, out=out, where=den > 0)
     return out
+
+
+# ----------------------------------------------------------------------------- EIS inversion (Algorithm 1)
+
+# Decision threshold on the mean of gamma: the paper's tau for a false-positive
+# rate of about 0.05 (Table 1).
+TAU = 19.5
+
+
+def similarity_from_homography(Hm):
+    """(lam, th_deg) of the similarity lam * Rot(th) nearest (Frobenius) to the
+    linear part of the homography Hm (3x3, acting on (column, row, 1)), via the
+    polar decomposition M = R S: R = U V^T is the closest rotation and lam the
+    mean singular value.  Sec. 3.2 keeps only scale and rotation of the
+    initialising transform.  This is the forward map of the correction node
+    (lam, th), i.e. the inverse of warp_matrix(lam, th).  det(M) > 0 only."""
+    Hm = np.asarray(Hm, dtype=np.float64).reshape(3, 3)
+    M = Hm[:2, :2] / Hm[2, 2]
+    if not np.linalg.det(M) > 0:
+        raise ValueError("linear part is not orientation preserving")
+    U, S, Vt = np.linalg.svd(M)
+    R = U @ Vt
+    return float(S.mean()), float(np.rad2deg(np.arctan2(R[1, 0], R[0, 0])))
+
+
+def invert_video(residuals, K0, homographies=None, max_iter: int = 3, th_half1: int = CORR_HALF_TH1,
+                 tau: float = TAU):
+    """Algorithm 1 with the co-registration supplied by the caller.
+
+    residuals: [F] frame residuals, frame 0 the anchor; K0: fingerprint term.
+    homographies: None, or [F] 3x3 homographies H_v that co-register frame v
+    with the corrected previous frame (entry 0 unused).  The anchor is
+    corrected from (1, 0).  Frame v >= 1 is corrected from the similarity of
+    H_v (rounded to float32) if its PCE warped by it exceeds its PCE unwarped,
+    else from (1, 0).  gamma[v] is the best PCE of the correction; the
+    decision is mean(gamma) > tau.
+    Returns dict(gamma, mean, decision, best (per frame), from_reg (per frame))."""
+    FK = np.fft.rfft2(K0)
+    gamma, bests, from_reg = [], [], []
+    for v, R in enumerate(residuals):
+        lam0, th0, use = 1.0, 0.0, False
+        if v > 0 and homographies is not None:
+            rl, rt = similarity_from_homography(homographies[v])
+            rl, rt = _f32(rl), _f32(rt)
+            if score(R, K0, rl, rt, FK)["pce"] > score(R, K0, 1.0, 0.0, FK)["pce"]:
+                lam0, th0, use = rl, rt, True
+        best, _, _ = correction(R, K0, lam0, th0, max_iter, th_half1, FK)
+        gamma.append(best["pce"])
+        bests.append(best)
+        from_reg.append(use)
+    m = float(np.mean(gamma))
+    return dict(gamma=gamma, mean=m, decision=m > tau, best=bests, from_reg=from_reg)
