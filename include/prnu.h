@@ -205,6 +205,55 @@ int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d
                    const uint64_t* fp_handles, int P, const float* init_lam, const float* init_th,
                    int max_iter, int th_half1, prnu_result* out, int* iters, prnu_stream stream);
 
+/* (lambda, theta) of the similarity nearest to a homography's linear part: the
+ * start estimate the correction takes from a co-registration (Sec. 3.2, "a
+ * vector t_init is derived").  Hm: host double [3][3], row-major, acting on
+ * (x = column, y = row, 1) so that the registered frame is H applied to the
+ * frame; with M = the upper-left 2x2 of Hm / Hm[2][2],
+ *     a = (m00 + m11) / 2,  b = (m10 - m01) / 2,
+ *     lambda = hypot(a, b),  theta = atan2(b, a) in degrees,
+ * the least-squares fit of lambda * Rot(theta).  The translation and the
+ * projective terms are dropped, as the correction assumes (Sec. 3.2).  This is
+ * the convention of the correction's warp: the node (lambda, theta) maps the
+ * frame forward by lambda * Rot(theta) about the frame centre.
+ * PRNU_EINVAL for a non-finite entry, Hm[2][2] == 0 or a zero linear part. */
+int similarity_from_homography(const double* Hm, float* lam, float* th_deg);
+
+/* Algorithm 1 (SIFT-aided EIS inversion) with the co-registration supplied by
+ * the caller, and the decision of Sec. 3.2: for a segment of F frames
+ * (frame 0 the anchor I_A, frames 1..F-1 the successive P_v) and one
+ * fingerprint,
+ *   - the anchor is corrected from (1, 0);
+ *   - frame v >= 1 is scored unwarped (the node (1, 0)) and co-registered (the
+ *     node similarity_from_homography(H_v)); the correction starts from the
+ *     co-registration if that PCE is strictly higher, else from (1, 0);
+ *   - gamma[v] = the highest PCE its correction found;
+ *   - the decision is mean(gamma) > tau (the paper's tau = 19.5 is set for a
+ *     false-positive rate of about 0.05 on its 1080p videos, Table 1).
+ * H_v co-registers P_v with the corrected previous frame (the paper's
+ * coregistration operator, SIFT keypoints and DEGENSAC: host-side, not in this
+ * library; the caller builds the corrected frame from best[v-1]).  Given every
+ * H_v the frames are independent, so both PCE tests run as one batched search
+ * and the corrections as one batched correction.  The registered frame's PCE
+ * uses the similarity part of H_v only: its translation moves the correlation
+ * peak, which the search over all cyclic shifts finds anyway.
+ *  d_resid, dtype, d_scale, H, W: as eis_grid_search, F >= 1 frames.
+ *  fp_handle:    the reference fingerprint (size H x W).
+ *  homographies: host double [F][3][3] row-major (entry 0 unused), or NULL to
+ *                start every frame from (1, 0).
+ *  max_iter, th_half1: as eis_correction (the paper: 3 and 50).
+ *  gamma:      host double [F], the PCE vector.
+ *  mean_gamma: host double, or NULL.  decision: host int (1 = the video comes
+ *              from the fingerprint's camera), or NULL.
+ *  best:       host prnu_result [F] (the node of gamma[v]), or NULL.
+ *  from_reg:   host int [F], 1 where the correction started from H_v, or NULL.
+ * Synchronous (waits for `stream`).  Errors as eis_correction, plus
+ * PRNU_EINVAL for a homography similarity_from_homography rejects. */
+int eis_invert_video(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                     uint64_t fp_handle, const double* homographies, int max_iter, int th_half1, double tau,
+                     double* gamma, double* mean_gamma, int* decision, prnu_result* best, int* from_reg,
+                     prnu_stream stream);
+
 /* PCE of one aligned pair (Eq. 3, no warp): d_X device float [H][W] against the
  * cached fingerprint `fp_handle`.  Host outputs; any of them may be NULL.
  * Synchronous (waits for `stream`). */

@@ -83,6 +83,10 @@ _SIGNATURES = {
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_correction": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int,
                                  _P, _P, C.c_int, C.c_int, _P, _P, _P]),
+    "similarity_from_homography": (C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "eis_invert_video": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_uint64, _P, C.c_int,
+                                   C.c_int, C.c_double, _P, C.POINTER(C.c_double), C.POINTER(C.c_int), _P, _P,
+                                   _P]),
     "pce_score": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                             C.POINTER(C.c_int), C.POINTER(C.c_float), _P]),
     "pce_score_noalloc": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
@@ -151,6 +155,16 @@ def make_windows(windows):
     for i, (a, b, c, d) in enumerate(w):
         arr[i] = prnu_window(int(a), int(b), int(c), int(d))
     return arr
+
+
+def similarity_from_homography(Hm):
+    """(lambda, theta in degrees) of the similarity nearest to the linear part
+    of a 3x3 homography acting on (column, row, 1)."""
+    hm = np.ascontiguousarray(np.asarray(Hm, np.float64).reshape(9))
+    lam, th = C.c_float(0.0), C.c_float(0.0)
+    _check(lib().similarity_from_homography(hm.ctypes.data_as(_P), C.byref(lam), C.byref(th)),
+           "similarity_from_homography")
+    return lam.value, th.value
 
 
 def pce_score_noalloc(X, K, stream=None) -> dict:
@@ -246,6 +260,29 @@ class Context:
                                     out.ctypes.data_as(_P), its.ctypes.data_as(_P), _stream(stream)),
                "eis_correction")
         return out, its
+
+    def eis_invert_video(self, resid, fp_handle, homographies=None, max_iter=3, th_half1=50, tau=19.5,
+                         scale=None, stream=None):
+        """Algorithm 1 with the co-registration supplied, and the decision of
+        Sec. 3.2.  resid: CUDA tensor [F, H, W], frame 0 the anchor;
+        homographies: array-like [F, 3, 3] (entry 0 unused) or None.  Returns
+        dict(gamma [F], mean, decision, best [F] of RESULT_DTYPE, from_reg [F])."""
+        import torch
+        F, H, W = resid.shape
+        dt = {torch.float32: PRNU_F32, torch.float16: PRNU_F16, torch.bfloat16: PRNU_BF16}[resid.dtype]
+        hm = None if homographies is None else np.ascontiguousarray(
+            np.asarray(homographies, np.float64).reshape(F * 9))
+        gamma = np.zeros(F, np.float64)
+        best = np.zeros(F, dtype=RESULT_DTYPE)
+        from_reg = np.zeros(F, np.int32)
+        mean, dec = C.c_double(0.0), C.c_int(0)
+        _check(lib().eis_invert_video(self.h, _ptr(resid), dt, _ptr(scale), F, H, W, fp_handle,
+                                      None if hm is None else hm.ctypes.data_as(_P), max_iter, th_half1, tau,
+                                      gamma.ctypes.data_as(_P), C.byref(mean), C.byref(dec),
+                                      best.ctypes.data_as(_P), from_reg.ctypes.data_as(_P), _stream(stream)),
+               "eis_invert_video")
+        return dict(gamma=gamma, mean=mean.value, decision=bool(dec.value), best=best,
+                    from_reg=from_reg.astype(bool))
 
     def eis_grid_search(self, resid, fp_handles, grid, windows=None, scale=None, out=None, all_pce=None,
                         stream=None, naive=False):

@@ -482,6 +482,79 @@ using namespace prnu;
 
 extern "C" {
 
+// The iterative correction of Sec. 3.2 (Eq. 8) for every (frame, fingerprint)
+// pair g = f*P + p from the start estimate (cl[g], ct[g]): exhaustive search over
+// the node grid around the current estimate, steps 0.01 * 10^-(n-1) in lambda and
+// 0.1 * 10^-(n-1) degrees in theta, until the best node is the centre or after
+// max_iter levels.  out[g] = the best node of all levels; iters[g] (optional) =
+// the levels run.  Caller holds ctx->mu and the device.
+static void run_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H,
+                           int W, const std::vector<std::shared_ptr<Fingerprint>>& fps, std::vector<float> cl,
+                           std::vector<float> ct, int max_iter, int th_half1, prnu_result* out, int* iters,
+                           cudaStream_t s) {
+  constexpr int kHalf = 5;
+  const int P = (int)fps.size();
+  const int hb1 = th_half1 ? th_half1 : 50;
+  const int G = F * P;
+  std::vector<prnu_result> best(G);
+  std::vector<char> have(G, 0), active(G, 1);
+  std::vector<int> run(G, 0);
+  ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * (size_t)G);
+  prnu_result* d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
+  std::vector<prnu_result> res;
+  for (int n = 1; n <= max_iter; ++n) {
+    // float32 steps 0.01 * 10^-(n-1) and 0.1 * 10^-(n-1) degrees
+    const float sl = (float)(0.01 * std::pow(10.0, -(n - 1))), st = (float)(0.1 * std::pow(10.0, -(n - 1)));
+    const int hb = n == 1 ? hb1 : kHalf;
+    SearchCall call;
+    call.resid = d_resid;
+    call.rdtype = dtype;
+    call.scale = d_scale;
+    call.F = F;
+    call.H = H;
+    call.W = W;
+    call.fps = fps;
+    call.cmax = (2 * kHalf + 1) * (2 * hb + 1);
+    std::vector<int> who;   // active pair of each group of this iteration
+    for (int g = 0; g < G; ++g) {
+      if (!active[g]) continue;
+      std::vector<float> lams, ths;
+      for (int a = -kHalf; a <= kHalf; ++a) lams.push_back((float)((double)cl[g] + (double)a * (double)sl));
+      for (int b = -hb; b <= hb; ++b) ths.push_back((float)((double)ct[g] + (double)b * (double)st));
+      call.group_start.push_back((int)call.items.size());
+      add_pair_items(call, g / P, g % P, (int)who.size(), lams, ths);
+      who.push_back(g);
+    }
+    if (who.empty()) break;
+    call.group_start.push_back((int)call.items.size());
+    enqueue_search(ctx, call, d_out, nullptr, false, s);
+    res.resize(who.size());
+    PRNU_CUDA_TRY(cudaMemcpyAsync(res.data(), d_out, sizeof(prnu_result) * who.size(), cudaMemcpyDeviceToHost, s));
+    PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*ctx->h_err) report_device_abort(ctx, s, "a bounded device-side wait timed out; the results are invalid");
+    const int nb = 2 * hb + 1, centre = kHalf * nb + hb;
+    for (size_t k = 0; k < who.size(); ++k) {
+      const int g = who[k];
+      const prnu_result& r = res[k];
+      ++run[g];
+      if (!have[g] || r.pce > best[g].pce) {
+        best[g] = r;
+        have[g] = 1;
+      }
+      if (r.cand_idx == centre || r.cand_idx < 0) {
+        active[g] = 0;   // the estimate did not change
+      } else {
+        cl[g] = r.lam;
+        ct[g] = r.th_deg;
+      }
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    out[g] = best[g];
+    if (iters) iters[g] = run[g];
+  }
+}
+
 int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
                    const uint64_t* fp_handles, int P, const float* init_lam, const float* init_th, int max_iter,
                    int th_half1, prnu_result* out, int* iters, prnu_stream stream) {
@@ -497,8 +570,6 @@ int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d
     DeviceGuard dg(ctx->device);
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    constexpr int kHalf = 5;
-    const int hb1 = th_half1 ? th_half1 : 50;
     const int G = F * P;
     std::vector<std::shared_ptr<Fingerprint>> fps;
     for (int p = 0; p < P; ++p) {
@@ -512,16 +583,58 @@ int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d
       ct[g] = init_th ? init_th[g] : 0.0f;
       PRNU_CHECK_ARG(std::isfinite(cl[g]) && cl[g] > 0 && std::isfinite(ct[g]), "bad start estimate");
     }
-    std::vector<prnu_result> best(G);
-    std::vector<char> have(G, 0), active(G, 1);
-    std::vector<int> run(G, 0);
-    ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * (size_t)G);
-    prnu_result* d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
-    std::vector<prnu_result> res;
-    for (int n = 1; n <= max_iter; ++n) {
-      // float32 steps 0.01 * 10^-(n-1) and 0.1 * 10^-(n-1) degrees
-      const float sl = (float)(0.01 * std::pow(10.0, -(n - 1))), st = (float)(0.1 * std::pow(10.0, -(n - 1)));
-      const int hb = n == 1 ? hb1 : kHalf;
+    run_correction(ctx, d_resid, dtype, d_scale, F, H, W, fps, std::move(cl), std::move(ct), max_iter, th_half1,
+                   out, iters, s);
+  });
+}
+
+// (lambda, theta) of the similarity nearest to the linear part of a homography
+static void similarity_of(const double* Hm, float* lam, float* th_deg) {
+  for (int i = 0; i < 9; ++i) PRNU_CHECK_ARG(std::isfinite(Hm[i]), "non-finite homography entry");
+  PRNU_CHECK_ARG(Hm[8] != 0.0, "homography with h33 = 0");
+  // linear part M (x = column, y = row), projected on {[a, -b], [b, a]}:
+  // a = lambda cos(theta), b = lambda sin(theta)
+  const double m00 = Hm[0] / Hm[8], m01 = Hm[1] / Hm[8], m10 = Hm[3] / Hm[8], m11 = Hm[4] / Hm[8];
+  const double a = 0.5 * (m00 + m11), b = 0.5 * (m10 - m01);
+  const double L = std::hypot(a, b);
+  PRNU_CHECK_ARG(L > 0 && std::isfinite(L), "homography without a similarity part");
+  *lam = (float)L;
+  *th_deg = (float)(std::atan2(b, a) * 180.0 / 3.14159265358979323846);
+}
+
+int similarity_from_homography(const double* Hm, float* lam, float* th_deg) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(Hm && lam && th_deg, "NULL argument");
+    similarity_of(Hm, lam, th_deg);
+  });
+}
+
+int eis_invert_video(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale, int F, int H, int W,
+                     uint64_t fp_handle, const double* homographies, int max_iter, int th_half1, double tau,
+                     double* gamma, double* mean_gamma, int* decision, prnu_result* best, int* from_reg,
+                     prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 1, "F must be >= 1 (the anchor)");
+    PRNU_CHECK_ARG(d_resid && gamma, "NULL argument");
+    PRNU_CHECK_ARG(dtype == kF32 || dtype == kF16 || dtype == kBF16, "unknown residual dtype");
+    PRNU_CHECK_ARG(max_iter >= 1, "max_iter must be >= 1");
+    PRNU_CHECK_ARG(th_half1 >= 0 && th_half1 <= 4096, "th_half1 must be in 0..4096");
+    PRNU_CHECK_ARG(std::isfinite(tau), "tau must be finite");
+    validate_shape(H, W);
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto f = find_fp(ctx, fp_handle);
+    PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs from the frames");
+    const std::vector<std::shared_ptr<Fingerprint>> fps{f};
+    std::vector<float> cl(F, 1.0f), ct(F, 0.0f);
+    std::vector<int> use(F, 0);
+    if (homographies && F > 1) {
+      // the co-registered frame against the frame itself: one single-node
+      // group each, (lambda_v, theta_v) from H_v and the identity (1, 0)
+      std::vector<float> rl(F), rt(F);
+      for (int v = 1; v < F; ++v) similarity_of(homographies + 9 * (size_t)v, &rl[v], &rt[v]);
       SearchCall call;
       call.resid = d_resid;
       call.rdtype = dtype;
@@ -530,45 +643,44 @@ int eis_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d
       call.H = H;
       call.W = W;
       call.fps = fps;
-      call.cmax = (2 * kHalf + 1) * (2 * hb + 1);
-      std::vector<int> who;   // active pair of each group of this iteration
-      for (int g = 0; g < G; ++g) {
-        if (!active[g]) continue;
-        std::vector<float> lams, ths;
-        for (int a = -kHalf; a <= kHalf; ++a) lams.push_back((float)((double)cl[g] + (double)a * (double)sl));
-        for (int b = -hb; b <= hb; ++b) ths.push_back((float)((double)ct[g] + (double)b * (double)st));
-        call.group_start.push_back((int)call.items.size());
-        add_pair_items(call, g / P, g % P, (int)who.size(), lams, ths);
-        who.push_back(g);
+      call.cmax = 1;
+      for (int v = 1; v < F; ++v) {
+        for (int k = 0; k < 2; ++k) {
+          const int grp = 2 * (v - 1) + k;
+          call.group_start.push_back((int)call.items.size());
+          add_pair_items(call, v, 0, grp, {k == 0 ? rl[v] : 1.0f}, {k == 0 ? rt[v] : 0.0f});
+        }
       }
-      if (who.empty()) break;
       call.group_start.push_back((int)call.items.size());
+      const int ng = 2 * (F - 1);
+      ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * (size_t)ng);
+      prnu_result* d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
       enqueue_search(ctx, call, d_out, nullptr, false, s);
-      res.resize(who.size());
-      PRNU_CUDA_TRY(cudaMemcpyAsync(res.data(), d_out, sizeof(prnu_result) * who.size(), cudaMemcpyDeviceToHost, s));
+      std::vector<prnu_result> res(ng);
+      PRNU_CUDA_TRY(cudaMemcpyAsync(res.data(), d_out, sizeof(prnu_result) * ng, cudaMemcpyDeviceToHost, s));
       PRNU_CUDA_TRY(cudaStreamSynchronize(s));
       if (*ctx->h_err) report_device_abort(ctx, s, "a bounded device-side wait timed out; the results are invalid");
-      const int nb = 2 * hb + 1, centre = kHalf * nb + hb;
-      for (size_t k = 0; k < who.size(); ++k) {
-        const int g = who[k];
-        const prnu_result& r = res[k];
-        ++run[g];
-        if (!have[g] || r.pce > best[g].pce) {
-          best[g] = r;
-          have[g] = 1;
-        }
-        if (r.cand_idx == centre || r.cand_idx < 0) {
-          active[g] = 0;   // the estimate did not change
-        } else {
-          cl[g] = r.lam;
-          ct[g] = r.th_deg;
+      for (int v = 1; v < F; ++v) {
+        if (res[2 * (v - 1)].pce > res[2 * (v - 1) + 1].pce) {
+          cl[v] = rl[v];
+          ct[v] = rt[v];
+          use[v] = 1;
         }
       }
     }
-    for (int g = 0; g < G; ++g) {
-      out[g] = best[g];
-      if (iters) iters[g] = run[g];
+    std::vector<prnu_result> out(F);
+    run_correction(ctx, d_resid, dtype, d_scale, F, H, W, fps, std::move(cl), std::move(ct), max_iter, th_half1,
+                   out.data(), nullptr, s);
+    double sum = 0.0;
+    for (int v = 0; v < F; ++v) {
+      gamma[v] = out[v].pce;
+      sum += out[v].pce;
+      if (best) best[v] = out[v];
+      if (from_reg) from_reg[v] = use[v];
     }
+    const double m = sum / (double)F;
+    if (mean_gamma) *mean_gamma = m;
+    if (decision) *decision = m > tau ? 1 : 0;
   });
 }
 

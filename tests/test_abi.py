@@ -63,3 +63,30 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(p, "_lib", None)
     with pytest.raises(RuntimeError):
         p.lib()
+
+
+def test_similarity_from_homography_matches_the_oracle(libpath):
+    """Host-only entry point (no CUDA call): the start estimate the library
+    derives from a co-registration equals the oracle's polar-decomposition fit,
+    and malformed homographies are rejected with PRNU_EINVAL."""
+    import numpy as np
+    import paper_2207_14507_gb300 as p
+    from oracle import prnu_oracle as oracle
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        lam, th = rng.uniform(0.8, 1.2), rng.uniform(-20, 20)
+        t = np.deg2rad(th)
+        Hm = np.array([[lam * np.cos(t), -lam * np.sin(t), rng.uniform(-50, 50)],
+                       [lam * np.sin(t), lam * np.cos(t), rng.uniform(-50, 50)], [0, 0, 1.0]])
+        Hm[:2, :2] += rng.normal(0, 0.02, (2, 2))
+        Hm[2, :2] = rng.normal(0, 1e-4, 2)
+        Hm *= rng.uniform(0.5, 2.0)
+        l_c, t_c = p.similarity_from_homography(Hm)
+        l_o, t_o = oracle.similarity_from_homography(Hm)
+        # both round a double to float32; the doubles differ in the last bits
+        assert abs(l_c - np.float32(l_o)) <= np.spacing(np.float32(l_o))
+        assert abs(t_c - np.float32(t_o)) <= np.spacing(np.float32(t_o))
+    for bad in (np.zeros((3, 3)), np.array([[0, 0, 1], [0, 0, 1], [0, 0, 1.0]]),
+                np.array([[np.nan, 0, 0], [0, 1, 0], [0, 0, 1.0]])):
+        with pytest.raises(p.PrnuError, match="PRNU_EINVAL"):
+            p.similarity_from_homography(bad)
