@@ -84,8 +84,8 @@ def test_similarity_from_homography_matches_the_oracle(libpath):
         l_c, t_c = p.similarity_from_homography(Hm)
         l_o, t_o = oracle.similarity_from_homography(Hm)
         # both round a double to float32; the doubles differ in the last bits
-        assert abs(l_c - np.float32(l_o)) <= np.spacing(np.float32(l_o))
-        assert abs(t_c - np.float32(t_o)) <= np.spacing(np.float32(t_o))
+        assert abs(l_c - np.float32(l_o)) <= abs(np.spacing(np.float32(l_o)))
+        assert abs(t_c - np.float32(t_o)) <= abs(np.spacing(np.float32(t_o)))
     for bad in (np.zeros((3, 3)), np.array([[0, 0, 1], [0, 0, 1], [0, 0, 1.0]]),
                 np.array([[np.nan, 0, 0], [0, 1, 0], [0, 0, 1.0]])):
         with pytest.raises(p.PrnuError, match="PRNU_EINVAL"):
