@@ -407,18 +407,24 @@ def run_ours(args):
 
 # --------------------------------------------------------------------------- other workloads
 
-def _timed_steps(step, steps, warmup, dev):
+def _timed_steps(step, steps, warmup, dev, ctx=None):
+    """ms per step over `steps` timed steps after `warmup` untimed ones; with
+    `ctx`, also the library's per-kernel profile of the timed steps only."""
     import torch
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ctx is not None:
+        ctx.prnu_profile_begin()
     e0.record()
     for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize(dev)
-    return e0.elapsed_time(e1) / steps
+    prof = ctx.prnu_profile_end() if ctx is not None else None
+    ms = e0.elapsed_time(e1) / steps
+    return (ms, prof) if ctx is not None else ms
 
 
 def run_batched(args):
@@ -447,9 +453,7 @@ def run_batched(args):
         ctx.eis_grid_search(R, [h], wl.grid, windows=win, out=out_d)
         ctx.prnu_fingerprint_release(h)
 
-    ctx.prnu_profile_begin()
-    ms = _timed_steps(step, args.steps, args.warmup, dev)
-    prof = ctx.prnu_profile_end()
+    ms, prof = _timed_steps(step, args.steps, args.warmup, dev, ctx)
     value = ncand / (ms / 1e3)
     # the plain per-candidate path on the first 4 frames' windows (same inputs)
     h = ctx.prnu_fingerprint_term(K_d)
@@ -581,9 +585,7 @@ def run_precision(args):
             res["r"] = ctx.eis_grid_search(R, [h], wl.grid, scale=scale)
             ctx.prnu_fingerprint_release(h)
 
-        ctx.prnu_profile_begin()
-        ms = _timed_steps(step, args.steps, args.warmup, dev)
-        prof = ctx.prnu_profile_end()
+        ms, prof = _timed_steps(step, args.steps, args.warmup, dev, ctx)
         value = ncand / (ms / 1e3)
         pce = res["r"]["pce"][:, 0]
         legs[name] = {"value": round(value, 1), "ms_per_step": round(ms, 1),

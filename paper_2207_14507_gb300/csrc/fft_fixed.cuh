@@ -197,6 +197,35 @@ __device__ __forceinline__ void row_stage(const float2* __restrict__ in, float2*
   }
 }
 
+// Stage I (>= 1) of row plan SP in place on `buf`, one butterfly per thread
+// (NB <= T): every thread loads its inputs, the block synchronises, then every
+// thread stores its outputs.  One row buffer instead of two, for one more
+// barrier.  Called by every thread of the block.
+template <class SP, int I, int T, bool INV>
+__device__ __forceinline__ void row_stage_ip(float2* buf, int t) {
+  using G = Stg<SP, I>;
+  static_assert(G::NB % 16 == 0 && G::NS % 16 == 0 && T % 16 == 0, "row stages need 16-element blocks");
+  static_assert(G::NB <= T, "in-place row stages hold one butterfly per thread");
+  constexpr int LB = G::NB / 16 * 18, LS = G::NS / 16 * 18;
+  const bool act = G::NB == T || t < G::NB;
+  const int j = t;
+  const int k = (G::NB == G::NS) ? j : j % G::NS;
+  float2 v[1][G::R];
+  if (act) {
+    const float2* src = buf + rp2(j);
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) v[0][r] = src[r * LB];
+  }
+  __syncthreads();
+  if (act) {
+    twiddle_tab<G::R, G::NS, INV, 1>(v, k);
+    Dft<G::R, INV>::run(v[0]);
+    float2* dst = buf + rp2((j - k) * G::R + k);
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) dst[r * LS] = v[0][r];
+  }
+}
+
 // Last stage of row plan SP (Ns = n/R): butterflies j = t + it*T, outputs
 // x = j + r*Ns stay in registers, v[it]; `last_valid` tells which are real.
 template <class SP, int T>

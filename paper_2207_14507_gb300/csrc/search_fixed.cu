@@ -54,7 +54,7 @@ __device__ __forceinline__ float4 ld_spec4(const float4* p) {
 
 template <int W>
 __host__ __device__ constexpr size_t row_fx_smem(int ppb) {
-  return (size_t)ppb * 2 * row_len2(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
+  return (size_t)ppb * row_len2(W) * sizeof(float2) + (size_t)ppb * 32 * sizeof(WarpRed);
 }
 __host__ __device__ constexpr size_t col_fx_smem(int H, int nc) { return (size_t)H * nc * sizeof(float2); }
 
@@ -90,8 +90,7 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
   const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
-  float2* A = smem + (size_t)grp * 2 * L;
-  float2* B = A + L;
+  float2* A = smem + (size_t)grp * L;   // the row pair's buffer; stages 1.. run in place
   const WorkItem it = item_of(a, is);
   size_t base;
   const void* Rf = frame_of(a, it.frame, &base);
@@ -127,13 +126,13 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
     // 0): output x = j + r*Ns has its mirror W - x at r' = R-1-r of butterfly
     // Ns - j, so the split of z = G_a + i G_b takes the mirror bins by shuffle
     // instead of a shared-memory round trip.
-    row_stage<SP, 1, T, false>(A, B, t);
+    row_stage_ip<SP, 1, T, false>(A, t);
     __syncthreads();
     constexpr int R = LS::R, NS = LS::NS, LB = NS / 16 * 18;
     const int p = (t >> 5) * 16 + (t & 15), h = (t >> 4) & 1;
     const int j = p == 0 ? (h ? NS / 2 : 0) : (h ? NS - p : p);
     float2 v[1][R];
-    const float2* src = B + rp2(j);
+    const float2* src = A + rp2(j);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[0][r] = src[r * LB];
     twiddle_tab<R, NS, false, 1>(v, j);
@@ -163,13 +162,12 @@ __device__ __forceinline__ void row_forward_body(const PassArgs& a, int is, int 
     }
     return;
   }
-  const float2* res = B;
-  row_stage<SP, 1, T, false>(A, B, t);
+  const float2* res = A;
+  row_stage_ip<SP, 1, T, false>(A, t);
   __syncthreads();
   if constexpr (SP::S == 3) {
-    row_stage<SP, 2, T, false>(B, A, t);
+    row_stage_ip<SP, 2, T, false>(A, t);
     __syncthreads();
-    res = A;
   }
   // split z = G_a + i G_b into the two rows' half spectra (packed: bin 0
   // holds (DC, Nyquist))
@@ -488,7 +486,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
 // outputs x = t + r*Ns_last of the last stage in v (v.x row a, v.y row b).
 // Holds barriers: every thread of the block calls it.
 template <class SP, int T, bool CG>
-__device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* pb, float2* A, float2* B, int t,
+__device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* pb, float2* A, int t,
                                                 float2 (&v)[RowLast<SP, T>::IT][RowLast<SP, T>::R]) {
   constexpr int W = SP::N, Wh = W / 2;
   using S0 = Stg<SP, 0>;
@@ -529,13 +527,11 @@ __device__ __forceinline__ void row_inverse_fft(const float2* pa, const float2* 
     row_store16(A, t, u);
   }
   __syncthreads();
-  if constexpr (SP::S == 2) {
-    row_stage_last<SP, T, true>(A, t, v);
-  } else {
-    row_stage<SP, 1, T, true>(A, B, t);
+  if constexpr (SP::S == 3) {
+    row_stage_ip<SP, 1, T, true>(A, t);
     __syncthreads();
-    row_stage_last<SP, T, true>(B, t, v);
   }
+  row_stage_last<SP, T, true>(A, t, v);
 }
 
 template <class SP, int T, int PPB, bool CG = false>
@@ -546,12 +542,11 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
   const int grp = tx / T, t = tx - grp * T;
   const int H = a.H;
   const int pair = bx * PPB + grp;
-  float2* A = smem + (size_t)grp * 2 * L;
-  float2* B = A + L;
-  RowRed* red = reinterpret_cast<RowRed*>(smem + (size_t)PPB * 2 * L) + grp * 32;
+  float2* A = smem + (size_t)grp * L;
+  RowRed* red = reinterpret_cast<RowRed*>(smem + (size_t)PPB * L) + grp * 32;
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
   float2 v[GL::IT][GL::R];
-  row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, B, t, v);
+  row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, t, v);
   // per thread: max, first arg-max and energy of each row over its outputs
   float ma = -INFINITY, mb = -INFINITY;
   int ia = INT_MAX, ib = INT_MAX;
@@ -648,7 +643,7 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
   const WorkItem it = item_of(a, is);
   const RowStat* st = a.stats + (size_t)ws * H;
   const float2* Z = a.spec + (size_t)ws * H * Wh;
-  WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * 2 * L);
+  WarpRed* red = reinterpret_cast<WarpRed*>(smem + (size_t)PPB * L);
   constexpr int NW = TB / 32;
   const int w = t >> 5;
 
@@ -687,11 +682,10 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
     const int k = r0 + grp;
     const bool act = k < np;
     const int p = act ? s_pairs[k] : 0;
-    float2* A = smem + (size_t)grp * 2 * L;
-    float2* B = A + L;
+    float2* A = smem + (size_t)grp * L;
     const float2* pa = Z + (size_t)(2 * p) * Wh;
     float2 V[SL::IT][SL::R];
-    row_inverse_fft<SP, T, true>(pa, pa + Wh, A, B, tg, V);
+    row_inverse_fft<SP, T, true>(pa, pa + Wh, A, tg, V);
     if (act) {
 #pragma unroll
       for (int it = 0; it < SL::IT; ++it) {
