@@ -13,6 +13,8 @@ What it computes (arXiv 2207.14507):
 * circular cross-correlation over all shifts, C(d) = sum_x X(x) K0(x + d)
 * PCE with an 11x11 cyclic exclusion around the signed peak         (Eq. 3)
 * exhaustive search over the (lambda, theta) grid, arg-max PCE      (Sec. 3.2, Eq. 8)
+* the frame-literal variant: per candidate, warp the frame and take
+  the residual of the warped frame                                  (Sec. 3.2)
 * the iterative breadth-first correction: progressively narrower
   (lambda, theta) neighbourhoods of the previous estimate          (Sec. 3.2, Eq. 8)
 * the EIS inversion of a video segment with the co-registration
@@ -40,6 +42,7 @@ __all__ = [
     "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
+    "literal_residual", "score_literal", "grid_search_literal",
     "correction_nodes", "correction", "fingerprint_estimate", "similarity_from_homography", "invert_video", "TAU",
 ]
 
@@ -230,6 +233,48 @@ def score(R: np.ndarray, K0: np.ndarray, lam: float, theta_deg: float, K0_spectr
     """PCE of one candidate: warp, correlate, Eq. 3."""
     X = inverse_warp(R, lam, theta_deg)
     return pce(xcorr(X, K0, K0_spectrum))
+
+
+# ----------------------------------------------------------------------------- frame-literal variant (Sec. 3.2)
+
+def literal_residual(frame: np.ndarray, lam: float, theta_deg: float, weight_by_intensity: bool = True):
+    """Sec. 3.2 as printed: warp the frame I by the candidate, X = inverse_warp(I),
+    then take the residual of X, R = X * W(X) (or W(X)), with W the same 3x3
+    Wiener residual as for frames (borders replicated, noise power the mean
+    local variance of X)."""
+    X = inverse_warp(np.asarray(frame, dtype=np.float64), lam, theta_deg)
+    Wx, _ = wiener_residual(X)
+    return X * Wx if weight_by_intensity else Wx
+
+
+def score_literal(frame, K0, lam: float, theta_deg: float, weight_by_intensity: bool = True, K0_spectrum=None):
+    """PCE of one candidate of the frame-literal variant: the residual of the
+    warped frame, correlated with K0 as it stands (no further warp), Eq. 3."""
+    R = literal_residual(frame, lam, theta_deg, weight_by_intensity)
+    return pce(xcorr(R, K0, K0_spectrum))
+
+
+def grid_search_literal(frames, fingerprints, grid, windows=None, weight_by_intensity: bool = True):
+    """grid_search with score_literal: best[f][p] and all_pce as grid_search."""
+    F, P = len(frames), len(fingerprints)
+    all_pce = np.full((F, P, grid.nlam * grid.nth), np.nan)
+    spectra = [np.fft.rfft2(K0) for K0 in fingerprints]
+    best = []
+    for f in range(F):
+        win = None if windows is None else tuple(int(v) for v in windows[f])
+        cands = candidate_list(grid, win)
+        Rs = [(idx, lam, th, literal_residual(frames[f], lam, th, weight_by_intensity)) for idx, lam, th in cands]
+        row = []
+        for p in range(P):
+            b = None
+            for idx, lam, th, R in Rs:
+                r = pce(xcorr(R, fingerprints[p], spectra[p]))
+                all_pce[f, p, idx] = r["pce"]
+                if b is None or r["pce"] > b["pce"]:
+                    b = dict(r, lam=lam, th_deg=th, cand=idx)
+            row.append(b)
+        best.append(row)
+    return best, all_pce
 
 
 # ----------------------------------------------------------------------------- search (Sec. 3.2)

@@ -511,3 +511,55 @@ def test_invert_video_uses_the_registration_and_decides():
     assert blind["from_reg"] == [False] * 4
     other = oracle.fingerprint_term(synth.fingerprint_field(128, 128, np.random.default_rng(99)))
     assert not oracle.invert_video(Rs, other, hs, max_iter=2, th_half1=5, tau=tau)["decision"]
+
+
+# ------------------------------------------------------------------ frame-literal variant (Sec. 3.2)
+
+def test_literal_residual_at_identity_is_the_frame_residual():
+    """At (1, 0) the warped frame is the frame itself, so the literal residual
+    is the pinned per-frame residual, weighted and plain."""
+    wl = synth.make_workload(1, F=1, on_grid=True)
+    fr = wl.frames[0]
+    for w in (True, False):
+        np.testing.assert_array_equal(oracle.literal_residual(fr, 1.0, 0.0, w),
+                                      oracle.prnu_residual(fr, weight_by_intensity=w)[0])
+
+
+@pytest.mark.parametrize("n", [33, 65])
+def test_literal_residual_commutes_with_a_quarter_turn(n):
+    """The 3x3 window, the replicated border and the frame's noise power are
+    invariant under a quarter turn, so warping the frame by 90 degrees and then
+    taking the residual equals turning the frame's residual."""
+    fr = np.random.default_rng(n).integers(0, 256, (n, n)).astype(np.uint8)
+    for w in (True, False):
+        R = oracle.prnu_residual(fr, weight_by_intensity=w)[0]
+        np.testing.assert_allclose(oracle.literal_residual(fr, 1.0, 90.0, w), np.rot90(R, -1), atol=1e-9, rtol=0)
+        np.testing.assert_allclose(oracle.literal_residual(fr, 1.0, -90.0, w), np.rot90(R, 1), atol=1e-9, rtol=0)
+
+
+def test_literal_residual_weighting_is_the_warped_intensity():
+    wl = synth.make_workload(1, F=1, on_grid=True)
+    fr = wl.frames[0]
+    X = oracle.inverse_warp(fr.astype(np.float64), 1.02, -0.6)
+    np.testing.assert_allclose(oracle.literal_residual(fr, 1.02, -0.6, True),
+                               X * oracle.literal_residual(fr, 1.02, -0.6, False), rtol=1e-12, atol=1e-9)
+
+
+def test_literal_search_recovers_planted_on_grid():
+    """The frame-literal variant finds every planted on-grid node and shift of
+    the 256x256 workload (3x3 windows around the planted nodes), and another
+    camera's fingerprint stays far below."""
+    wl = synth.make_workload(1, on_grid=True)
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    K1 = oracle.fingerprint_term(synth.fingerprint_field(256, 256, np.random.default_rng(99)))
+    win = []
+    for lam, th, _, _ in wl.planted:
+        i = int(round((np.float32(lam) - np.float32(wl.grid.lam0)) / np.float32(wl.grid.dlam)))
+        j = int(round((np.float32(th) - np.float32(wl.grid.th0_deg)) / np.float32(wl.grid.dth_deg)))
+        win.append([max(i - 1, 0), min(i + 1, wl.grid.nlam - 1), max(j - 1, 0), min(j + 1, wl.grid.nth - 1)])
+    best, _ = oracle.grid_search_literal(wl.frames, [K0, K1], wl.grid, windows=np.array(win))
+    for f, (lam, th, sy, sx) in enumerate(wl.planted):
+        b = best[f][0]
+        assert b["lam"] == pytest.approx(lam, abs=0) and b["th_deg"] == pytest.approx(th, abs=0)
+        assert (b["dy"], b["dx"]) == (sy, sx) and b["pce"] > 1000
+        assert best[f][1]["pce"] < 60
