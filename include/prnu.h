@@ -176,6 +176,27 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
                           const prnu_grid* grid, const prnu_window* windows,
                           prnu_result* out, double* d_all_pce, prnu_stream stream);
 
+/* The grid search as Sec. 3.2 literally states it: for every candidate the
+ * FRAME is warped and the residual is extracted from the warped frame, instead
+ * of warping a residual computed once per frame (eis_grid_search).  For frame f
+ * and candidate (lambda, theta):
+ *     X(p) = bilinear(I_f, c + Rot(-theta)(p - c) / lambda), taps outside 0,
+ *     W(X) = X - Wiener3x3(X) (3x3 moments, borders replicated, noise power
+ *            the mean local variance of X), R = X * W(X) with
+ *            PRNU_WEIGHT_BY_INTENSITY, else R = W(X) (the plain Eq. 3 term),
+ * then R is correlated with the fingerprint and scored by PCE as in
+ * eis_grid_search (identity warp).  Every candidate costs one more pass over
+ * the frame than eis_grid_search.
+ *  d_frames: device uint8 [F][H][W], row pitch `pitch` bytes (0 = W).
+ *  flags:    0 or PRNU_WEIGHT_BY_INTENSITY.
+ *  fp_handles, P, grid, windows: as eis_grid_search.
+ *  out:      prnu_result [F*P], host or device memory.
+ * FP32 arithmetic and storage.  Synchronous (waits for `stream`).  Errors as
+ * eis_grid_search; PRNU_EINVAL for other flags. */
+int eis_grid_search_frames(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags,
+                           const uint64_t* fp_handles, int P, const prnu_grid* grid, const prnu_window* windows,
+                           prnu_result* out, prnu_stream stream);
+
 /* The correction operator of Sec. 3.2: for every (frame f, fingerprint p)
  * pair a breadth-first search over (lambda, theta) that maximises the PCE.
  * Iteration n (1-based) searches, around the previous estimate

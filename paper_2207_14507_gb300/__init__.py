@@ -81,6 +81,9 @@ _SIGNATURES = {
                                   C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "eis_grid_search_frames": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int,
+                                         C.POINTER(C.c_uint64), C.c_int, C.POINTER(prnu_grid),
+                                         C.POINTER(prnu_window), _P, _P]),
     "eis_correction": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int,
                                  _P, _P, C.c_int, C.c_int, _P, _P, _P]),
     "similarity_from_homography": (C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
@@ -260,6 +263,26 @@ class Context:
                                     out.ctypes.data_as(_P), its.ctypes.data_as(_P), _stream(stream)),
                "eis_correction")
         return out, its
+
+    def eis_grid_search_frames(self, frames, fp_handles, grid, windows=None, flags=PRNU_WEIGHT_BY_INTENSITY,
+                               pitch=0, out=None, stream=None):
+        """The frame-literal grid search of Sec. 3.2 (warp the frame, extract
+        the residual per candidate).  frames: CUDA uint8 tensor [F, H, W] (row
+        pitch `pitch` bytes, 0 = W).  Returns results [F, P] of RESULT_DTYPE
+        (or fills `out`, a host array or a CUDA byte tensor)."""
+        F, H, W = frames.shape[0], frames.shape[1], frames.shape[2]
+        P = len(fp_handles)
+        hs = (C.c_uint64 * max(P, 1))(*fp_handles)
+        g = make_grid(grid)
+        win = make_windows(windows)
+        host = out is None
+        if host:
+            out = np.zeros((F, P), dtype=RESULT_DTYPE)
+        ptr = out.ctypes.data_as(_P) if isinstance(out, np.ndarray) else _ptr(out)
+        _check(lib().eis_grid_search_frames(self.h, _ptr(frames), F, H, W, pitch, flags, hs, P, C.byref(g), win,
+                                            ptr, _stream(stream)),
+               "eis_grid_search_frames")
+        return out
 
     def eis_invert_video(self, resid, fp_handle, homographies=None, max_iter=3, th_half1=50, tau=19.5,
                          scale=None, stream=None):

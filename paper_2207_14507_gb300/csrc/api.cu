@@ -295,9 +295,12 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   ensure_buf(c, c->ws_spec, (size_t)slots * H * Wh * sizeof(float2));
   ensure_buf(c, c->ws_stats, (size_t)slots * H * sizeof(RowStat));
   if (persistent) ensure_buf(c, c->ws_persist, sizeof(int) * (2 + 4 * (size_t)n));
-  // the compile-time-planned kernels read the residuals in the zero-bordered layout
-  const ResidLayout lay = fs ? padded_layout(H, W) : dense_layout(H, W);
-  if (fs) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 ? 4 : 2));
+  // the compile-time-planned kernels read the residuals in the zero-bordered
+  // layout; residuals rendered in it already (prepadded) serve both paths
+  PRNU_CHECK_ARG(!call.prepadded || (call.rdtype == kF32 && !naive), "prepadded residuals are FP32, planned or generic");
+  const ResidLayout lay = (fs || call.prepadded) ? padded_layout(H, W) : dense_layout(H, W);
+  const bool pad = fs && !call.prepadded;
+  if (pad) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 ? 4 : 2));
   std::vector<FpDesc> fd = fp_descs(call);
   Stager st(c);
   st.add(c->ws_items.p, call.items.data(), call.items.size());
@@ -307,7 +310,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
 
   PassArgs a{};
   a.resid = call.resid;
-  if (fs) {
+  if (pad) {
     launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches);
     a.resid = c->ws_pad.p;
   }
@@ -747,7 +750,8 @@ int prnu_destroy(prnu_ctx* ctx) {
     }
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
-                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest})
+                         &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest,
+                         &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     ctx_free(ctx, ctx->d_err, sizeof(int));
@@ -931,6 +935,131 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
                           prnu_result* out, double* d_all_pce, prnu_stream stream) {
   return search_common(ctx, d_resid, dtype, d_scale, F, H, W, fp_handles, P, grid, windows, out, d_all_pce, stream,
                        true);
+}
+
+// The frame-literal search of Sec. 3.2: per candidate the frame is warped and
+// its residual extracted (launch_literal_residuals, into the zero-bordered
+// layout), then the search runs on those residuals with the identity warp.
+// Candidates are rendered in chunks of at most kLitChunkBytes of residuals;
+// every fingerprint of a frame searches the same renders.  The best per
+// (frame, fingerprint) is kept over the chunks on the host: a higher PCE
+// replaces it, so ties keep the lowest candidate index.
+static constexpr size_t kLitChunkBytes = (size_t)2 << 30;   // and as much again for the warped frames
+
+int eis_grid_search_frames(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags,
+                           const uint64_t* fp_handles, int P, const prnu_grid* grid, const prnu_window* windows,
+                           prnu_result* out, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 0 && P >= 0, "F and P must be >= 0");
+    if (F == 0 || P == 0) return;
+    PRNU_CHECK_ARG(d_frames && fp_handles && grid && out, "NULL argument");
+    PRNU_CHECK_ARG((flags & ~PRNU_WEIGHT_BY_INTENSITY) == 0, "flags: only PRNU_WEIGHT_BY_INTENSITY applies");
+    validate_shape(H, W);
+    if (pitch == 0) pitch = (size_t)W;
+    PRNU_CHECK_ARG(pitch >= (size_t)W, "pitch must be >= W");
+    PRNU_CHECK_ARG(pitch * (size_t)H <= (size_t)INT_MAX, "a frame must span at most 2^31 - 1 bytes");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<std::shared_ptr<Fingerprint>> fps;
+    for (int p = 0; p < P; ++p) {
+      auto f = find_fp(ctx, fp_handles[p]);
+      PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs from the frames");
+      fps.push_back(f);
+    }
+    SearchCall all;
+    build_items(*grid, windows, F, P, all);
+    // renders: the candidates of fingerprint 0 of each frame (every fingerprint
+    // of a frame has the same window)
+    std::vector<WorkItem> renders;
+    std::vector<int> render0(F + 1, 0);
+    for (int f = 0; f < F; ++f) {
+      render0[f] = (int)renders.size();
+      for (int i = all.group_start[(size_t)f * P]; i < all.group_start[(size_t)f * P + 1]; ++i)
+        renders.push_back(all.items[i]);
+    }
+    render0[F] = (int)renders.size();
+    const ResidLayout lay = padded_layout(H, W);
+    const size_t per = lay.fpitch * sizeof(float);
+    // residuals and warped frames of a chunk: at most a quarter each of what the budget leaves
+    const size_t used = ctx->used.load(), avail = ctx->budget > used ? ctx->budget - used : 0;
+    const size_t cap = std::min(kLitChunkBytes, avail / 4);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, renders.size()));
+    ensure_buf(ctx, ctx->ws_lit, per * (size_t)chunk);
+    ensure_buf(ctx, ctx->ws_litx, sizeof(float) * (size_t)H * W * chunk);
+    ensure_buf(ctx, ctx->ws_litpart, sizeof(double) * (literal_partials_needed(chunk, H, W) + (size_t)chunk));
+    ensure_buf(ctx, ctx->ws_renders, sizeof(WorkItem) * (size_t)chunk);
+    float* d_lit = reinterpret_cast<float*>(ctx->ws_lit.p);
+    double* d_part = reinterpret_cast<double*>(ctx->ws_litpart.p);
+    float* d_nu2 = reinterpret_cast<float*>(d_part + literal_partials_needed(chunk, H, W));
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    PRNU_CUDA_TRY(cudaMemsetAsync(d_lit, 0, per * (size_t)chunk, s));   // the zero border, never written after
+    std::vector<prnu_result> best((size_t)F * P);
+    std::vector<char> have((size_t)F * P, 0);
+    std::vector<prnu_result> res;
+    const int weight = (flags & PRNU_WEIGHT_BY_INTENSITY) ? 1 : 0;
+    for (int r0 = 0; r0 < (int)renders.size(); r0 += chunk) {
+      const int r1 = std::min<int>((int)renders.size(), r0 + chunk);
+      {
+        Stager st(ctx);
+        st.add(ctx->ws_renders.p, renders.data() + r0, (size_t)(r1 - r0));
+        st.flush(s);
+      }
+      launch_literal_residuals(d_frames, pitch, H, W, reinterpret_cast<const WorkItem*>(ctx->ws_renders.p), r1 - r0,
+                               weight, d_lit, lay, reinterpret_cast<float*>(ctx->ws_litx.p), d_part, d_nu2, s,
+                               ctx->launches);
+      SearchCall call;
+      call.resid = d_lit;
+      call.rdtype = kF32;
+      call.scale = nullptr;
+      call.F = r1 - r0;
+      call.H = H;
+      call.W = W;
+      call.fps = fps;
+      call.cmax = all.cmax;
+      call.prepadded = true;
+      std::vector<int> gid;   // (frame, fingerprint) pair of each local group
+      for (int f = 0; f < F; ++f) {
+        const int a = std::max(r0, render0[f]), b = std::min(r1, render0[f + 1]);
+        if (a >= b) continue;
+        for (int p = 0; p < P; ++p) {
+          call.group_start.push_back((int)call.items.size());
+          for (int r = a; r < b; ++r) {
+            WorkItem it = renders[r];
+            it.frame = r - r0;
+            it.fp = p;
+            it.group = (int)gid.size();
+            it.a11 = it.a22 = 1.f;
+            it.a12 = it.a21 = 0.f;
+            call.items.push_back(it);
+          }
+          gid.push_back(f * P + p);
+        }
+      }
+      call.group_start.push_back((int)call.items.size());
+      ensure_buf(ctx, ctx->ws_out, sizeof(prnu_result) * gid.size());
+      prnu_result* d_out = reinterpret_cast<prnu_result*>(ctx->ws_out.p);
+      enqueue_search(ctx, call, d_out, nullptr, false, s);
+      res.resize(gid.size());
+      PRNU_CUDA_TRY(cudaMemcpyAsync(res.data(), d_out, sizeof(prnu_result) * gid.size(), cudaMemcpyDeviceToHost, s));
+      PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*ctx->h_err) report_device_abort(ctx, s, "a bounded device-side wait timed out; the results are invalid");
+      for (size_t k = 0; k < gid.size(); ++k) {
+        const int g = gid[k];
+        if (!have[g] || res[k].pce > best[g].pce) {
+          best[g] = res[k];
+          have[g] = 1;
+        }
+      }
+    }
+    if (is_device_pointer(out)) {
+      PRNU_CUDA_TRY(cudaMemcpyAsync(out, best.data(), sizeof(prnu_result) * best.size(), cudaMemcpyHostToDevice, s));
+      PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+      std::copy(best.begin(), best.end(), out);
+    }
+  });
 }
 
 int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W, double* pce, int* dy, int* dx,

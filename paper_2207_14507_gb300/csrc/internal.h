@@ -137,6 +137,15 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
                      float* scale, unsigned long long* acc, double* partials, int max_partials, cudaStream_t s,
                      LaunchCounter& lc, const ResidLayout* lay = nullptr);
 size_t residual_partials_needed(int F, int H, int W);
+// frame-literal residuals (Sec. 3.2): for render r of renders[nr] (frame
+// index, similarity a11..a22) the residual of the warped uint8 frame, FP32,
+// into out[r * lay.fpitch + lay.roff + y * lay.rpitch + x]; partials: at least
+// literal_partials_needed(nr, H, W) doubles; nu2: nr floats; X: nr*H*W floats
+// (the warped frames, scratch)
+void launch_literal_residuals(const uint8_t* frames, size_t pitch, int H, int W, const WorkItem* renders, int nr,
+                              int weight, float* out, const ResidLayout& lay, float* X, double* partials, float* nu2,
+                              cudaStream_t s, LaunchCounter& lc);
+size_t literal_partials_needed(int nr, int H, int W);
 // Eq. 2 accumulation over Lc residuals R [Lc][H][W] (R = I W(I)) and their frames
 void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
                                    double* num, double* den, bool first, cudaStream_t s, LaunchCounter& lc);
@@ -200,7 +209,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist, ws_pad, ws_fpest;
+      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up
@@ -230,6 +239,7 @@ struct SearchCall {
   std::vector<WorkItem> items;
   std::vector<int> group_start;   // [F*P + 1]
   int cmax;
+  bool prepadded = false;         // resid is FP32 in padded_layout already (zero border included)
 };
 void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call);
 void validate_shape(int H, int W);

@@ -80,9 +80,15 @@ __global__ void k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, 
   const int f = blockIdx.z;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   const uint8_t* fr = frames + (size_t)f * H * pitch;
-  const double nu2d = (double)acc[f] / (81.0 * (double)H * (double)W);
-  const float nu2 = (float)nu2d;
-  const float nu2x81 = (float)(81.0 * nu2d);
+  __shared__ float s_nu2[2];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {   // once per block: the FP64 pipe is narrow
+    const double nu2d = (double)acc[f] / (81.0 * (double)H * (double)W);
+    s_nu2[0] = (float)nu2d;
+    s_nu2[1] = (float)(81.0 * nu2d);
+  }
+  __syncthreads();
+  const float nu2 = s_nu2[0];
+  const float nu2x81 = s_nu2[1];
   float r = 0.f;
   if (x < W && y < H) {
     int s1, s2, xc;
@@ -92,12 +98,12 @@ __global__ void k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, 
     if (MODE == 0) store_store_type<DT>(out, o, r);
     if (MODE == 2) store_store_type<DT>(out, o, r * scale[f]);
   }
-  if (MODE == 1) {
-    double v = (double)r * (double)r;
+  if (MODE == 1) {   // float within a warp, double across warps and blocks
+    float v = r * r;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int tid = threadIdx.y * kBX + threadIdx.x;
-    if ((tid & 31) == 0) part[tid >> 5] = v;
+    if ((tid & 31) == 0) part[tid >> 5] = (double)v;
     __syncthreads();
     if (tid == 0) {
       double s = 0;
@@ -179,6 +185,183 @@ __global__ void k_fp_divide(const double* __restrict__ num, const double* __rest
   if (i < n) K[i] = den[i] > 0.0 ? (float)(num[i] / den[i]) : 0.f;
 }
 
+
+// ---------------------------------------------------------------- frame-literal residuals (Sec. 3.2)
+//
+// The paper warps the frame for every candidate and extracts the residual of
+// the warped frame.  For render r (source frame f, similarity a11..a22):
+//   X(p)  = bilinear(I_f, c + A (p - c)), each tap outside the frame 0,
+//   W(X)  = X - Wiener3x3(X), 3x3 moments with replicated borders, noise power
+//           nu2 = mean over the frame of the local variances of X,
+//   R     = X W(X) (PRNU_WEIGHT_BY_INTENSITY) or W(X).
+// X is not an integer image, so the moments are taken in float from the
+// differences to the window's centre (d = x_k - x_c: mean m1 = sum d / 9,
+// variance sum d^2 / 9 - m1^2), which keeps the cancellation small.  A block
+// warps its 32x8 tile plus a one-pixel halo into shared memory; halo pixels
+// outside the frame are the warped values at the clamped position (the
+// replicated border).
+
+constexpr int kLX = 32, kLY = 32, kLR = 4, kLTX = kLX + 2, kLTY = kLY + 2;   // 32 x 8 threads, 4 rows each
+static_assert(kLY == 8 * kLR, "a thread covers kLR rows of the tile");
+
+// uint8 -> float without a conversion instruction: the byte in the low
+// mantissa bits of 2^23 (exact for every byte value)
+__device__ __forceinline__ float u8f(uint32_t v) { return __int_as_float(0x4B000000u | v) - 8388608.f; }
+
+__device__ __forceinline__ float warp_u8(const uint8_t* __restrict__ fr, int pitch, int H, int W, const WorkItem& it,
+                                         float cx, float cy, int x, int y) {
+  const float dx = (float)x - cx, dy = (float)y - cy;
+  const float qx = fmaf(it.a11, dx, fmaf(it.a12, dy, cx));
+  const float qy = fmaf(it.a21, dx, fmaf(it.a22, dy, cy));
+  const float fx0 = floorf(qx), fy0 = floorf(qy);
+  // every tap outside (also keeps the int conversion in range)
+  if (!(fx0 >= -1.f && fx0 <= (float)(W - 1) && fy0 >= -1.f && fy0 <= (float)(H - 1))) return 0.f;
+  const float fx = qx - fx0, fy = qy - fy0;
+  const int x0 = (int)fx0, y0 = (int)fy0;
+  const bool xa = x0 >= 0, xb = x0 + 1 < W, ya = y0 >= 0, yb = y0 + 1 < H;
+  const uint8_t* r0 = fr + (ya ? y0 : 0) * pitch;
+  const uint8_t* r1 = fr + (yb ? y0 + 1 : 0) * pitch;
+  const float v00 = (ya && xa) ? u8f(__ldg(r0 + x0)) : 0.f;
+  const float v01 = (ya && xb) ? u8f(__ldg(r0 + x0 + 1)) : 0.f;
+  const float v10 = (yb && xa) ? u8f(__ldg(r1 + x0)) : 0.f;
+  const float v11 = (yb && xb) ? u8f(__ldg(r1 + x0 + 1)) : 0.f;
+  const float top = fmaf(fx, v01, (1.f - fx) * v00), bot = fmaf(fx, v11, (1.f - fx) * v10);
+  return fmaf(fy, bot, (1.f - fy) * top);
+}
+
+// the warped tile with its halo, tile[(ty + 1) * kLTX + tx + 1] = X(x, y)
+__device__ __forceinline__ void warp_tile(const uint8_t* __restrict__ frames, size_t pitch, int H, int W,
+                                          const WorkItem& it, float* tile) {
+  const uint8_t* fr = frames + (size_t)it.frame * H * pitch;
+  const float cx = 0.5f * (float)(W - 1), cy = 0.5f * (float)(H - 1);
+  const int tid = threadIdx.y * kLX + threadIdx.x;
+  const int x0 = blockIdx.x * kLX - 1, y0 = blockIdx.y * kLY - 1;
+#pragma unroll
+  for (int k0 = 0; k0 < kLTX * kLTY; k0 += kLX * 8) {
+    const int k = k0 + tid;
+    if (k < kLTX * kLTY) {
+      const int sy = k / kLTX, sx = k - sy * kLTX;
+      const int y = min(max(y0 + sy, 0), H - 1), x = min(max(x0 + sx, 0), W - 1);
+      tile[k] = warp_u8(fr, (int)pitch, H, W, it, cx, cy, x, y);
+    }
+  }
+  __syncthreads();
+}
+
+// centre value, window mean offset m1 and population variance of tile pixel (tx, ty)
+__device__ __forceinline__ void tile_moments(const float* tile, int tx, int ty, float* xc, float* m1, float* var) {
+  const float c = tile[(ty + 1) * kLTX + tx + 1];
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const float d = tile[(ty + dy) * kLTX + tx + dx] - c;
+      s1 += d;
+      s2 = fmaf(d, d, s2);
+    }
+  const float m = s1 * (1.f / 9.f);
+  *xc = c;
+  *m1 = m;
+  *var = fmaf(-m, m, s2 * (1.f / 9.f));
+}
+
+// per block: sum of the local variances of its pixels (double), one slot per
+// block; the warped frame itself to X[r][H][W] for the second pass
+__global__ void __launch_bounds__(kLX * 8) k_lit_moments(const uint8_t* __restrict__ frames, size_t pitch, int H,
+                                                         int W, const WorkItem* __restrict__ renders,
+                                                         double* __restrict__ partials, float* __restrict__ X) {
+  __shared__ float tile[kLTX * kLTY];
+  __shared__ double part[8];
+  const WorkItem it = renders[blockIdx.z];
+  warp_tile(frames, pitch, H, W, it, tile);
+  const int tx = threadIdx.x, x = blockIdx.x * kLX + tx;
+  if (x < W) {
+    float* xo = X + (size_t)blockIdx.z * H * W + x;
+#pragma unroll
+    for (int k = 0; k < kLR; ++k) {
+      const int ty = threadIdx.y + 8 * k, y = blockIdx.y * kLY + ty;
+      if (y < H) xo[(size_t)y * W] = tile[(ty + 1) * kLTX + tx + 1];
+    }
+  }
+  // float within a warp (128 terms), double across warps and blocks: the FP64
+  // pipe is a small fraction of the FP32 one, so it takes one add per warp
+  float v = 0.f;
+#pragma unroll
+  for (int k = 0; k < kLR; ++k) {
+    const int ty = threadIdx.y + 8 * k, y = blockIdx.y * kLY + ty;
+    if (x < W && y < H) {
+      float c, m, var;
+      tile_moments(tile, tx, ty, &c, &m, &var);
+      v += var;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (tx == 0) part[threadIdx.y] = (double)v;
+  __syncthreads();
+  if (threadIdx.y == 0 && tx == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += part[k];
+    partials[(size_t)blockIdx.z * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// one block per render: nu2 = (fixed-order sum of the block partials) / (H W)
+__global__ void k_lit_noise(const double* __restrict__ partials, int nblk, int H, int W, float* __restrict__ nu2) {
+  __shared__ double part[32];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += partials[(size_t)r * nblk + k];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += part[k];
+    nu2[r] = (float)(t / ((double)H * (double)W));
+  }
+}
+
+// R of every pixel into out[r * lay.fpitch + lay.roff + y * lay.rpitch + x] (float)
+// (the tile and its replicated halo read back from X, the first pass's warped frame)
+__global__ void __launch_bounds__(kLX * 8) k_lit_apply(const float* __restrict__ X, int H, int W,
+                                                       const float* __restrict__ nu2, int weight,
+                                                       float* __restrict__ out, ResidLayout lay) {
+  __shared__ float tile[kLTX * kLTY];
+  {
+    const float* xr = X + (size_t)blockIdx.z * H * W;
+    const int tid = threadIdx.y * kLX + threadIdx.x;
+    const int x0 = blockIdx.x * kLX - 1, y0 = blockIdx.y * kLY - 1;
+#pragma unroll
+    for (int k0 = 0; k0 < kLTX * kLTY; k0 += kLX * 8) {
+      const int k = k0 + tid;
+      if (k < kLTX * kLTY) {
+        const int sy = k / kLTX, sx = k - sy * kLTX;
+        const int y = min(max(y0 + sy, 0), H - 1), x = min(max(x0 + sx, 0), W - 1);
+        tile[k] = __ldg(xr + (size_t)y * W + x);
+      }
+    }
+    __syncthreads();
+  }
+  const int tx = threadIdx.x, x = blockIdx.x * kLX + tx;
+  if (x >= W) return;
+  const float n2 = nu2[blockIdx.z];
+  float* o = out + (size_t)blockIdx.z * lay.fpitch + lay.roff + x;
+#pragma unroll
+  for (int k = 0; k < kLR; ++k) {
+    const int ty = threadIdx.y + 8 * k, y = blockIdx.y * kLY + ty;
+    if (y >= H) break;
+    float c, m, var;
+    tile_moments(tile, tx, ty, &c, &m, &var);
+    const float den = fmaxf(var, n2);
+    const float gain = den > 0.f ? __fdividef(fmaxf(var - n2, 0.f), den) : 1.f;
+    const float w = -m * (1.f - gain);   // x - (mu + (x - mu) gain), x - mu = -m1
+    o[(size_t)y * lay.rpitch] = weight ? c * w : w;
+  }
+}
+
 }  // namespace
 
 void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
@@ -208,6 +391,26 @@ void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out
                                            reinterpret_cast<uint16_t*>(out));
   PRNU_CUDA_TRY(cudaGetLastError());
   lc.n++;
+}
+
+
+void launch_literal_residuals(const uint8_t* frames, size_t pitch, int H, int W, const WorkItem* renders, int nr,
+                              int weight, float* out, const ResidLayout& lay, float* X, double* partials,
+                              float* nu2, cudaStream_t s, LaunchCounter& lc) {
+  if (nr == 0) return;
+  ProfScope ps(lc, kKindResidual, s);
+  const dim3 b(kLX, 8), g((W + kLX - 1) / kLX, (H + kLY - 1) / kLY, nr);
+  k_lit_moments<<<g, b, 0, s>>>(frames, pitch, H, W, renders, partials, X);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  k_lit_noise<<<nr, 256, 0, s>>>(partials, (int)(g.x * g.y), H, W, nu2);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  k_lit_apply<<<g, b, 0, s>>>(X, H, W, nu2, weight, out, lay);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n += 3;
+}
+
+size_t literal_partials_needed(int nr, int H, int W) {
+  return (size_t)nr * ((W + kLX - 1) / kLX) * ((H + kLY - 1) / kLY);
 }
 
 size_t residual_partials_needed(int F, int H, int W) {
