@@ -9,6 +9,7 @@ What it computes (arXiv 2207.14507):
 * fingerprint term K0 = K - mean(K)                                 (Eq. 1, 3)
 * reference fingerprint from L frames,
   K = (sum_l I_l W(I_l)) / (sum_l I_l^2), pixel-wise                (Eq. 2)
+* the fingerprint down-scaled and cropped to the video geometry     (Sec. 3)
 * inverse similarity warp of R, bilinear, zero outside the frame    (Eq. 4, Sec. 3.2)
 * circular cross-correlation over all shifts, C(d) = sum_x X(x) K0(x + d)
 * PCE with an 11x11 cyclic exclusion around the signed peak         (Eq. 3)
@@ -43,7 +44,7 @@ __all__ = [
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
     "literal_residual", "score_literal", "grid_search_literal",
-    "correction_nodes", "correction", "fingerprint_estimate", "similarity_from_homography", "invert_video", "TAU",
+    "correction_nodes", "correction", "fingerprint_estimate", "resize_weights", "fingerprint_resize", "similarity_from_homography", "invert_video", "TAU",
 ]
 
 # Eq. 3: the exclusion neighbourhood D around the correlation peak is 11 x 11, cyclic.
@@ -388,6 +389,43 @@ def fingerprint_estimate(frames) -> np.ndarray:
     out = np.zeros_like(num)
     np.divide(num, den, out=out, where=den > 0)
     return out
+
+
+# ----------------------------------------------------------------------------- fingerprint geometry (Sec. 3)
+
+def resize_weights(n_in: int, scale: float, first: int, n_out: int) -> np.ndarray:
+    """[n_out, n_in] weights of output samples first .. first + n_out - 1 of a
+    1-D signal of n_in samples resized by `scale`: output sample o sits at
+    input position u = (o + 0.5) / scale - 0.5 (pixel centres aligned); its
+    weights follow the tent max(0, 1 - |j - u| * a), a = min(scale, 1) (the
+    tent widened by 1/scale when shrinking, so that every input sample
+    contributes), normalised to sum 1; input indices beyond the ends take the
+    end sample (replicated border)."""
+    a = min(float(scale), 1.0)
+    Wm = np.zeros((n_out, n_in))
+    for r in range(n_out):
+        u = (first + r + 0.5) / scale - 0.5
+        lo, hi = int(np.floor(u - 1.0 / a)), int(np.ceil(u + 1.0 / a))
+        w = {}
+        for j in range(lo, hi + 1):
+            t = max(0.0, 1.0 - abs(j - u) * a)
+            if t > 0.0:
+                jj = min(max(j, 0), n_in - 1)
+                w[jj] = w.get(jj, 0.0) + t
+        tot = sum(w.values())
+        for jj, t in w.items():
+            Wm[r, jj] = t / tot
+    return Wm
+
+
+def fingerprint_resize(K: np.ndarray, scale: float, y0: int, x0: int, H: int, W: int) -> np.ndarray:
+    """The fingerprint resized by `scale` (separable, resize_weights along
+    rows and columns) and cropped to H x W from (y0, x0) of the resized grid:
+    the image fingerprint brought to a video's geometry."""
+    K = np.asarray(K, dtype=np.float64)
+    Wy = resize_weights(K.shape[0], scale, y0, H)
+    Wx = resize_weights(K.shape[1], scale, x0, W)
+    return Wy @ K @ Wx.T
 
 
 # ----------------------------------------------------------------------------- EIS inversion (Algorithm 1)

@@ -563,3 +563,43 @@ def test_literal_search_recovers_planted_on_grid():
         assert b["lam"] == pytest.approx(lam, abs=0) and b["th_deg"] == pytest.approx(th, abs=0)
         assert (b["dy"], b["dx"]) == (sy, sx) and b["pce"] > 1000
         assert best[f][1]["pce"] < 60
+
+
+# ------------------------------------------------------------------ fingerprint geometry (Sec. 3)
+
+def test_resize_identity_is_a_crop():
+    K = np.random.default_rng(4).standard_normal((40, 56))
+    np.testing.assert_array_equal(oracle.fingerprint_resize(K, 1.0, 3, 5, 30, 44), K[3:33, 5:49])
+
+
+def test_resize_half_is_the_1331_filter():
+    """scale 1/2: output o sits at 2o + 1/2 between inputs 2o and 2o + 1, the
+    tent of half-width 2 gives them 3/4 and their outer neighbours 1/4, i.e.
+    the binomial filter [1, 3, 3, 1] / 8 (replicated at the ends)."""
+    Wm = oracle.resize_weights(16, 0.5, 0, 8)
+    for o in range(1, 7):
+        np.testing.assert_allclose(Wm[o, 2 * o - 1:2 * o + 3], [1 / 8, 3 / 8, 3 / 8, 1 / 8], rtol=0, atol=1e-15)
+        assert Wm[o].sum() == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(Wm[0, :3], [4 / 8, 3 / 8, 1 / 8], atol=1e-15)     # index -1 replicated onto 0
+
+
+def test_resize_keeps_constants_and_is_separable():
+    rng = np.random.default_rng(5)
+    a, b = rng.standard_normal(75), rng.standard_normal(101)
+    for s in (0.48, 0.75, 1.6):
+        C = oracle.fingerprint_resize(np.full((75, 101), 2.5), s, 1, 2, 20, 30)
+        np.testing.assert_allclose(C, 2.5, rtol=1e-14)
+        R = oracle.fingerprint_resize(np.outer(a, b), s, 1, 2, 20, 30)
+        ra = oracle.resize_weights(75, s, 1, 20) @ a
+        rb = oracle.resize_weights(101, s, 2, 30) @ b
+        np.testing.assert_allclose(R, np.outer(ra, rb), rtol=1e-12, atol=1e-14)
+
+
+def test_resize_upscale_is_linear_interpolation():
+    """scale 2 (no widening): outputs 2k + 1 and 2k + 2 sit at k + 1/4 and
+    k + 3/4, linear interpolation between inputs k and k + 1."""
+    x = np.arange(10.0) ** 2
+    y = oracle.resize_weights(10, 2.0, 0, 20) @ x
+    for k in range(8):
+        assert y[2 * k + 1] == pytest.approx(0.75 * x[k] + 0.25 * x[k + 1], abs=1e-12)
+        assert y[2 * k + 2] == pytest.approx(0.25 * x[k] + 0.75 * x[k + 1], abs=1e-12)
