@@ -176,6 +176,25 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
                           const prnu_grid* grid, const prnu_window* windows,
                           prnu_result* out, double* d_all_pce, prnu_stream stream);
 
+/* The reference fingerprint brought to a video's geometry: down-scaled (or
+ * up-scaled) by `scale` and cropped (Sec. 3: the fingerprint estimated from
+ * images must be down-scaled and cropped before it tests video frames; the
+ * paper gives no resampling, this is the antialiased bilinear one).  Output
+ * sample o of an axis sits at input position u = (o + first + 0.5)/scale - 0.5;
+ * its weights are the tent max(0, 1 - |j - u| a), a = min(scale, 1) (widened by
+ * 1/scale when shrinking), normalised, indices beyond the ends replicated;
+ * rows and columns separably.
+ *  d_Kin:  device float [Hin][Win], row pitch in_pitch elements (0 = Win).
+ *  scale:  in [1/64, 64]; the resized fingerprint has round(Hin*scale) x
+ *          round(Win*scale) samples.
+ *  y0, x0: top-left of the crop in the resized fingerprint; the H x W crop
+ *          must lie inside it.
+ *  d_Kout: device float [H][W] (dense), may not overlap d_Kin.
+ * FP32 accumulation of FP32 weights computed in double.  Synchronous.
+ * PRNU_EINVAL for a scale or crop out of range. */
+int prnu_fingerprint_resize(prnu_ctx* ctx, const float* d_Kin, int Hin, int Win, size_t in_pitch, double scale,
+                            int y0, int x0, float* d_Kout, int H, int W, prnu_stream stream);
+
 /* The grid search as Sec. 3.2 literally states it: for every candidate the
  * FRAME is warped and the residual is extracted from the warped frame, instead
  * of warping a residual computed once per frame (eis_grid_search).  For frame f

@@ -81,6 +81,8 @@ _SIGNATURES = {
                                   C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "prnu_fingerprint_resize": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.c_double, C.c_int, C.c_int, _P,
+                                          C.c_int, C.c_int, _P]),
     "eis_grid_search_frames": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int,
                                          C.POINTER(C.c_uint64), C.c_int, C.POINTER(prnu_grid),
                                          C.POINTER(prnu_window), _P, _P]),
@@ -263,6 +265,18 @@ class Context:
                                     out.ctypes.data_as(_P), its.ctypes.data_as(_P), _stream(stream)),
                "eis_correction")
         return out, its
+
+    def prnu_fingerprint_resize(self, K, scale, y0, x0, H, W, out=None, stream=None):
+        """The fingerprint K (CUDA float tensor [Hin, Win], rows may be
+        strided) resized by `scale` and cropped to H x W from (y0, x0)."""
+        import torch
+        Hin, Win = K.shape
+        assert K.dtype == torch.float32 and K.stride(1) == 1
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=K.device)
+        _check(lib().prnu_fingerprint_resize(self.h, _ptr(K), Hin, Win, K.stride(0), float(scale), y0, x0, _ptr(out),
+                                             H, W, _stream(stream)), "prnu_fingerprint_resize")
+        return out
 
     def eis_grid_search_frames(self, frames, fp_handles, grid, windows=None, flags=PRNU_WEIGHT_BY_INTENSITY,
                                pitch=0, out=None, stream=None):

@@ -751,7 +751,7 @@ int prnu_destroy(prnu_ctx* ctx) {
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
                          &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest,
-                         &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders})
+                         &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders, &ctx->ws_resize})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     ctx_free(ctx, ctx->d_err, sizeof(int));
@@ -1059,6 +1059,75 @@ int eis_grid_search_frames(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H,
     } else {
       std::copy(best.begin(), best.end(), out);
     }
+  });
+}
+
+// Taps of output samples first .. first + n - 1 of a length-n_in axis resized
+// by `scale`: sample o at input position u = (o + 0.5) / scale - 0.5, tent
+// weights max(0, 1 - |j - u| a) with a = min(scale, 1), indices clamped to the
+// axis, normalised; T taps per sample (zero weight beyond its support).
+static void resize_taps(int n_in, double scale, int first, int n, int T, std::vector<float>& w, std::vector<int>& idx) {
+  const double a = std::min(scale, 1.0);
+  w.assign((size_t)n * T, 0.f);
+  idx.assign((size_t)n * T, 0);
+  for (int o = 0; o < n; ++o) {
+    const double u = ((double)(first + o) + 0.5) / scale - 0.5;
+    const int lo = (int)std::floor(u - 1.0 / a);
+    std::vector<double> ws;
+    std::vector<int> js;
+    double tot = 0.0;
+    for (int j = lo; j <= lo + T - 1; ++j) {
+      const double t = 1.0 - std::fabs((double)j - u) * a;
+      if (t <= 0.0) continue;
+      const int jj = std::min(std::max(j, 0), n_in - 1);
+      ws.push_back(t);
+      js.push_back(jj);
+      tot += t;
+    }
+    for (size_t k = 0; k < ws.size(); ++k) {
+      w[(size_t)o * T + k] = (float)(ws[k] / tot);
+      idx[(size_t)o * T + k] = js[k];
+    }
+  }
+}
+
+int prnu_fingerprint_resize(prnu_ctx* ctx, const float* d_Kin, int Hin, int Win, size_t in_pitch, double scale,
+                            int y0, int x0, float* d_Kout, int H, int W, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx && d_Kin && d_Kout, "NULL argument");
+    PRNU_CHECK_ARG(Hin >= 1 && Win >= 1 && H >= 1 && W >= 1, "sizes must be >= 1");
+    PRNU_CHECK_ARG(std::isfinite(scale) && scale >= 1.0 / 64 && scale <= 64.0, "scale must be in [1/64, 64]");
+    if (in_pitch == 0) in_pitch = (size_t)Win;
+    PRNU_CHECK_ARG(in_pitch >= (size_t)Win, "in_pitch must be >= Win");
+    const long long Hs = std::llround((double)Hin * scale), Ws = std::llround((double)Win * scale);
+    PRNU_CHECK_ARG(y0 >= 0 && x0 >= 0 && y0 + (long long)H <= Hs && x0 + (long long)W <= Ws,
+                   "the crop must lie inside the resized fingerprint");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // taps per sample: the tent spans (u - 1/a, u + 1/a), at most floor(2/a) + 2 integers
+    const int T = (int)std::floor(2.0 / std::min(scale, 1.0)) + 2;
+    std::vector<float> wy, wx;
+    std::vector<int> iy, ix;
+    resize_taps(Hin, scale, y0, H, T, wy, iy);
+    resize_taps(Win, scale, x0, W, T, wx, ix);
+    const size_t nwy = wy.size(), nwx = wx.size();
+    ensure_buf(ctx, ctx->ws_resize, (nwy + nwx) * (sizeof(float) + sizeof(int)) + 1024);
+    char* base = reinterpret_cast<char*>(ctx->ws_resize.p);
+    float* d_wy = reinterpret_cast<float*>(base);
+    float* d_wx = d_wy + nwy;
+    int* d_iy = reinterpret_cast<int*>(d_wx + nwx);
+    int* d_ix = d_iy + nwy;
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    Stager st(ctx);
+    st.add(d_wy, wy.data(), nwy);
+    st.add(d_wx, wx.data(), nwx);
+    st.add(d_iy, iy.data(), nwy);
+    st.add(d_ix, ix.data(), nwx);
+    st.flush(s);
+    launch_fp_resize(d_Kin, in_pitch, d_wy, d_iy, d_wx, d_ix, T, H, W, d_Kout, s, ctx->launches);
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+    PRNU_CUDA_TRY(cudaStreamSynchronize(s));
   });
 }
 

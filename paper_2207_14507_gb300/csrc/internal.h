@@ -146,6 +146,9 @@ void launch_literal_residuals(const uint8_t* frames, size_t pitch, int H, int W,
                               int weight, float* out, const ResidLayout& lay, float* X, double* partials, float* nu2,
                               cudaStream_t s, LaunchCounter& lc);
 size_t literal_partials_needed(int nr, int H, int W);
+// fingerprint resampling with T taps per axis: weights and (clamped) indices per output row and column
+void launch_fp_resize(const float* K, size_t pitch, const float* wy, const int* iy, const float* wx, const int* ix,
+                      int T, int H, int W, float* out, cudaStream_t s, LaunchCounter& lc);
 // Eq. 2 accumulation over Lc residuals R [Lc][H][W] (R = I W(I)) and their frames
 void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
                                    double* num, double* den, bool first, cudaStream_t s, LaunchCounter& lc);
@@ -209,7 +212,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders;
+      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders, ws_resize;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up

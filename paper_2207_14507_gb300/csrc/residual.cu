@@ -362,6 +362,25 @@ __global__ void __launch_bounds__(kLX * 8) k_lit_apply(const float* __restrict__
   }
 }
 
+// Fingerprint resampling: out(y, x) = sum_a sum_b wy[y][a] wx[x][b] K(iy[y][a], ix[x][b]),
+// T taps per axis (unused taps have weight 0 and index 0).
+__global__ void k_fp_resize(const float* __restrict__ K, size_t pitch, const float* __restrict__ wy,
+                            const int* __restrict__ iy, const float* __restrict__ wx, const int* __restrict__ ix,
+                            int T, int H, int W, float* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W) return;
+  float acc = 0.f;
+  for (int a = 0; a < T; ++a) {
+    const float w = wy[(size_t)y * T + a];
+    if (w == 0.f) continue;
+    const float* row = K + (size_t)iy[(size_t)y * T + a] * pitch;
+    float r = 0.f;
+    for (int b = 0; b < T; ++b) r = fmaf(wx[(size_t)x * T + b], __ldg(row + ix[(size_t)x * T + b]), r);
+    acc = fmaf(w, r, acc);
+  }
+  out[(size_t)y * W + x] = acc;
+}
+
 }  // namespace
 
 void launch_fp_estimate_accumulate(const float* R, const uint8_t* frames, size_t pitch, int Lc, int H, int W,
@@ -450,4 +469,14 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
   }
 }
 
+}  // namespace prnu
+
+namespace prnu {
+void launch_fp_resize(const float* K, size_t pitch, const float* wy, const int* iy, const float* wx, const int* ix,
+                      int T, int H, int W, float* out, cudaStream_t s, LaunchCounter& lc) {
+  ProfScope ps(lc, kKindResidual, s);
+  k_fp_resize<<<dim3((W + 127) / 128, H), 128, 0, s>>>(K, pitch, wy, iy, wx, ix, T, H, W, out);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
 }  // namespace prnu
