@@ -6,6 +6,9 @@ What it computes (arXiv 2207.14507):
   with F a 3x3 local Wiener filter (the workloads replace the wavelet
   denoiser of Sec. 2.2 by a 3x3 Wiener filter), weighted by the frame
   intensity, R = I * W(I), the fingerprint-matching term of Eq. 2/3;
+* the wavelet-domain residual of Mihcak's denoiser (the paper's
+  denoiser, Sec. 2.2): 4-level orthonormal 8-tap Daubechies
+  transform, local-variance Wiener shrinkage of the detail bands     (Sec. 2.2)
 * fingerprint term K0 = K - mean(K)                                 (Eq. 1, 3)
 * reference fingerprint from L frames,
   K = (sum_l I_l W(I_l)) / (sum_l I_l^2), pixel-wise                (Eq. 2)
@@ -41,6 +44,7 @@ import numpy as np
 
 __all__ = [
     "EXCLUSION", "local_moments_3x3", "wiener_residual", "prnu_residual",
+    "DB8", "dwt2_level", "idwt2_level", "dwt2", "idwt2", "mihcak_shrink", "wavelet_residual", "prnu_residual_wavelet",
     "fingerprint_term", "grid_lambda", "grid_theta", "warp_matrix", "inverse_warp",
     "xcorr", "pce", "score", "grid_search", "candidate_list", "ncc_peak",
     "literal_residual", "score_literal", "grid_search_literal",
@@ -102,6 +106,123 @@ def prnu_residual(frame: np.ndarray, weight_by_intensity: bool = True, normalise
         s = 1.0 / np.sqrt(ms) if ms > 0 else 1.0
         R = R * s
     return R, s
+
+
+# ----------------------------------------------------------------------------- Mihcak denoiser (Sec. 2.2)
+
+# Daubechies' orthonormal scaling filter with 4 vanishing moments (8 taps),
+# normalised to sum sqrt(2).  The wavelet filter is g[k] = (-1)^k h[7 - k].
+DB8 = np.array([0.2303778133088964, 0.7148465705529154, 0.6308807679298587, -0.0279837694168599,
+                -0.1870348117190931, 0.0308413818355607, 0.0328830116668852, -0.0105974017850690])
+WAVELET_LEVELS = 4
+
+
+def _wavelet_filter(h):
+    return np.array([(-1) ** k * h[len(h) - 1 - k] for k in range(len(h))])
+
+
+def _analysis_1d(x, axis):
+    """Periodic analysis along `axis`: a[n] = sum_k h[k] x[2n + k], d[n] = sum_k g[k] x[2n + k]."""
+    g = _wavelet_filter(DB8)
+    a = np.zeros_like(np.take(x, np.arange(0, x.shape[axis], 2), axis=axis))
+    d = np.zeros_like(a)
+    for k in range(len(DB8)):
+        xs = np.take(np.roll(x, -k, axis=axis), np.arange(0, x.shape[axis], 2), axis=axis)
+        a += DB8[k] * xs
+        d += g[k] * xs
+    return a, d
+
+
+def _synthesis_1d(a, d, axis):
+    """The transpose of _analysis_1d (its inverse, the filters being orthonormal)."""
+    g = _wavelet_filter(DB8)
+    shape = list(a.shape)
+    shape[axis] *= 2
+    x = np.zeros(shape)
+    up_a, up_d = np.zeros(shape), np.zeros(shape)
+    idx = [slice(None)] * len(shape)
+    idx[axis] = slice(0, None, 2)
+    up_a[tuple(idx)] = a
+    up_d[tuple(idx)] = d
+    for k in range(len(DB8)):
+        x += DB8[k] * np.roll(up_a, k, axis=axis) + g[k] * np.roll(up_d, k, axis=axis)
+    return x
+
+
+def dwt2_level(X):
+    """One level of the separable 2-D transform (rows, then columns):
+    returns (LL, (LH, HL, HH)) with L/H the row filter first."""
+    L, Hh = _analysis_1d(X, axis=1)
+    LL, LH = _analysis_1d(L, axis=0)
+    HL, HH = _analysis_1d(Hh, axis=0)
+    return LL, (LH, HL, HH)
+
+
+def idwt2_level(LL, bands):
+    LH, HL, HH = bands
+    L = _synthesis_1d(LL, LH, axis=0)
+    Hh = _synthesis_1d(HL, HH, axis=0)
+    return _synthesis_1d(L, Hh, axis=1)
+
+
+def dwt2(X, levels: int = WAVELET_LEVELS):
+    """Multi-level transform of the approximation band: (LL, [bands of level 1, 2, ...])."""
+    details = []
+    A = np.asarray(X, dtype=np.float64)
+    for _ in range(levels):
+        A, b = dwt2_level(A)
+        details.append(b)
+    return A, details
+
+
+def idwt2(A, details):
+    for b in reversed(details):
+        A = idwt2_level(A, b)
+    return A
+
+
+def mihcak_shrink(c, sigma0: float):
+    """The noise part of one detail band: c sigma0^2 / (s2 + sigma0^2), where
+    s2 = min over W in {3, 5, 7, 9} of max(0, mean of c^2 over the W x W window
+    - sigma0^2), the window mean over W^2 positions with zeros outside the
+    band.  Where s2 + sigma0^2 = 0 the noise part is 0."""
+    c = np.asarray(c, dtype=np.float64)
+    c2 = c * c
+    s2 = None
+    for Wn in (3, 5, 7, 9):
+        r = Wn // 2
+        P = np.pad(c2, r)
+        acc = np.zeros_like(c2)
+        for dy in range(Wn):
+            for dx in range(Wn):
+                acc += P[dy:dy + c.shape[0], dx:dx + c.shape[1]]
+        v = np.maximum(acc / (Wn * Wn) - sigma0 ** 2, 0.0)
+        s2 = v if s2 is None else np.minimum(s2, v)
+    den = s2 + sigma0 ** 2
+    return np.where(den > 0, c * sigma0 ** 2 / np.where(den > 0, den, 1.0), 0.0)
+
+
+def wavelet_residual(I, sigma0: float = 3.0, levels: int = WAVELET_LEVELS):
+    """W(I) = I - F(I) with F Mihcak's denoiser: the frame mirrored at its
+    bottom and right edges up to multiples of 2^levels, the detail bands of
+    every level replaced by their noise parts (mihcak_shrink), the
+    approximation band by 0, the inverse transform cropped back to the frame
+    (the transform is linear, so this is the frame minus its denoised version)."""
+    I = np.asarray(I, dtype=np.float64)
+    H, W = I.shape
+    m = 2 ** levels
+    Hp, Wp = -(-H // m) * m, -(-W // m) * m
+    P = np.pad(I, ((0, Hp - H), (0, Wp - W)), mode="symmetric")
+    A, det = dwt2(P, levels)
+    det = [tuple(mihcak_shrink(b, sigma0) for b in lv) for lv in det]
+    return idwt2(np.zeros_like(A), det)[:H, :W]
+
+
+def prnu_residual_wavelet(frame, sigma0: float = 3.0, weight_by_intensity: bool = True):
+    """R = I * W(I) (or W(I)) with the wavelet residual."""
+    I = np.asarray(frame, dtype=np.float64)
+    Wr = wavelet_residual(I, sigma0)
+    return I * Wr if weight_by_intensity else Wr
 
 
 def fingerprint_term(K: np.ndarray) -> np.ndarray:

@@ -603,3 +603,76 @@ def test_resize_upscale_is_linear_interpolation():
     for k in range(8):
         assert y[2 * k + 1] == pytest.approx(0.75 * x[k] + 0.25 * x[k + 1], abs=1e-12)
         assert y[2 * k + 2] == pytest.approx(0.25 * x[k] + 0.75 * x[k + 1], abs=1e-12)
+
+
+# ------------------------------------------------------------------ Mihcak wavelet denoiser (Sec. 2.2)
+
+def test_db8_filter_is_orthonormal_with_four_vanishing_moments():
+    h = oracle.DB8
+    assert h.sum() == pytest.approx(np.sqrt(2), abs=1e-14)
+    for m in range(4):
+        assert np.dot(h[:8 - 2 * m], h[2 * m:]) == pytest.approx(1.0 if m == 0 else 0.0, abs=1e-14)
+    g = np.array([(-1) ** k * h[7 - k] for k in range(8)])
+    k = np.arange(8.0)
+    for p in range(4):
+        assert np.sum(k ** p * g) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_dwt2_reconstructs_and_keeps_energy():
+    X = np.random.default_rng(12).standard_normal((48, 80))
+    A, det = oracle.dwt2(X, 4)
+    assert A.shape == (3, 5) and det[0][0].shape == (24, 40)
+    np.testing.assert_allclose(oracle.idwt2(A, det), X, atol=1e-12, rtol=0)
+    e = (A ** 2).sum() + sum((b ** 2).sum() for lv in det for b in lv)
+    assert e == pytest.approx((X ** 2).sum(), rel=1e-12)
+
+
+def test_dwt2_of_a_constant():
+    """Every level multiplies a constant by sum(h)^2 = 2 and leaves no detail."""
+    A, det = oracle.dwt2(np.full((32, 48), 3.0), 4)
+    np.testing.assert_allclose(A, 48.0, rtol=1e-13)
+    assert max(np.abs(b).max() for lv in det for b in lv) < 1e-12
+
+
+def test_mihcak_shrink_of_an_isolated_coefficient():
+    """A lone coefficient c: every window's mean of c^2 is c^2/W^2, the
+    smallest (W = 9) sets s2 = max(0, c^2/81 - sigma0^2); its noise part is
+    c sigma0^2 / (s2 + sigma0^2) and the zeros around it stay 0."""
+    band = np.zeros((30, 30))
+    band[15, 15] = 90.0
+    n = oracle.mihcak_shrink(band, 3.0)
+    assert n[15, 15] == pytest.approx(90.0 * 9.0 / 100.0, rel=1e-14)   # s2 = 100 - 9
+    n[15, 15] = 0.0
+    assert not n.any()
+    band[15, 15] = 20.0                                                 # c^2/81 < sigma0^2: s2 = 0
+    assert oracle.mihcak_shrink(band, 3.0)[15, 15] == pytest.approx(20.0, rel=1e-14)
+
+
+def test_wavelet_residual_limits():
+    """sigma0 = 0 denoises nothing (W = 0); a huge sigma0 removes every
+    detail (W = frame - its approximation band); a constant frame has W = 0."""
+    fr = synth.make_workload(1, F=1, on_grid=True).frames[0][:100, :120]
+    assert np.abs(oracle.wavelet_residual(fr, 0.0)).max() == 0.0
+    P = np.pad(fr.astype(np.float64), ((0, 12), (0, 8)), mode="symmetric")
+    A, det = oracle.dwt2(P, 4)
+    smooth = oracle.idwt2(A, [tuple(np.zeros_like(b) for b in lv) for lv in det])[:100, :120]
+    np.testing.assert_allclose(oracle.wavelet_residual(fr, 1e7), fr - smooth, atol=1e-6, rtol=0)
+    assert np.abs(oracle.wavelet_residual(np.full((40, 56), 77, np.uint8), 3.0)).max() < 1e-10
+
+
+def test_wavelet_residual_recovers_planted_on_grid():
+    """The search on wavelet residuals finds the planted nodes and shifts of
+    the 256x256 workload (3x3 windows around them)."""
+    wl = synth.make_workload(1, on_grid=True)
+    K0 = oracle.fingerprint_term(wl.fingerprints[0])
+    R = [oracle.prnu_residual_wavelet(f) for f in wl.frames]
+    win = []
+    for lam, th, _, _ in wl.planted:
+        i = int(round((np.float32(lam) - np.float32(wl.grid.lam0)) / np.float32(wl.grid.dlam)))
+        j = int(round((np.float32(th) - np.float32(wl.grid.th0_deg)) / np.float32(wl.grid.dth_deg)))
+        win.append([max(i - 1, 0), min(i + 1, wl.grid.nlam - 1), max(j - 1, 0), min(j + 1, wl.grid.nth - 1)])
+    best, _ = oracle.grid_search(R, [K0], wl.grid, windows=np.array(win))
+    for f, (lam, th, sy, sx) in enumerate(wl.planted):
+        b = best[f][0]
+        assert (b["lam"], b["th_deg"]) == (pytest.approx(lam, abs=0), pytest.approx(th, abs=0))
+        assert (b["dy"], b["dx"]) == (sy, sx) and b["pce"] > 1000
