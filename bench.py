@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-extras", action="store_true", help="skip the naive-path and CPU-oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["plain", "batched", "precision", "serving", "correction", "literal"],
+    ap.add_argument("--workload", choices=["plain", "batched", "precision", "serving", "correction", "literal",
+                                                 "denoisers"],
                     default="plain",
                     help="plain = the 1080p metric line; the others print their own JSON record")
     ap.add_argument("--queries", type=int, default=16, help="serving: queries per run")
@@ -626,6 +627,44 @@ def run_literal(args):
     ctx.close()
 
 
+def run_denoisers(args):
+    """The two residual extractors on the full-HD workload's 30 frames: the 3x3
+    Wiener filter (prnu_residual) and Mihcak's wavelet denoiser
+    (prnu_residual_wavelet, sigma0 = 3), FP32 output.  Reports frames/s of
+    each, the Wiener kernel's HBM fraction (one uint8 read and one FP32
+    write per pixel), and the FP64 oracle's frames/s for each on one core."""
+    import torch
+    import oracle
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    wl = synth.make_workload(2, F=args.frames)
+    F, H, W = wl.frames.shape
+    ctx = prnu.Context(0)
+    frames_d = torch.from_numpy(wl.frames).to(dev)
+    R = torch.empty((F, H, W), device=dev)
+    ms_w = _timed_steps(lambda: ctx.prnu_residual(frames_d, R), args.steps, max(args.warmup, 3), dev)
+    ms_v = _timed_steps(lambda: ctx.prnu_residual_wavelet(frames_d, R, 3.0), args.steps, max(args.warmup, 3), dev)
+    t0 = time.perf_counter()
+    oracle.prnu_residual(wl.frames[0])
+    t1 = time.perf_counter()
+    oracle.prnu_residual_wavelet(wl.frames[0], 3.0)
+    t2 = time.perf_counter()
+    peak, kind = hbm_peak()
+    print(json.dumps({
+        "workload": "denoisers-1080p (Sec. 2.2 residual: 3x3 Wiener and Mihcak wavelet)", "metric": "frames/s",
+        "frames": F, "steps": args.steps, "dtype": "f32",
+        "wiener": {"value": round(F / (ms_w / 1e3), 1), "ms_per_step": round(ms_w, 3),
+                   "hbm_frac": round(5 * H * W * F / (ms_w / 1e3) / 1e9 / peak, 4)},
+        "wavelet": {"value": round(F / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 3)},
+        "cpu_baseline": {"unit": "frames/s", "cores": 1, "kind": "oracle", "sample": "frame 0, one each",
+                         "wiener": round(1 / (t1 - t0), 3), "wavelet": round(1 / (t2 - t1), 3)},
+        "peak": f"{peak} GB/s {kind}",
+    }), flush=True)
+    ctx.close()
+
+
 def run_precision(args):
     """Config 4: 32 frames of 3840x2160, full 41x41 grid, half of the frames
     from an independent fingerprint; FP16 and BF16 residual storage with an
@@ -769,6 +808,8 @@ def main():
         run_correction(args)
     elif args.workload == "literal":
         run_literal(args)
+    elif args.workload == "denoisers":
+        run_denoisers(args)
     else:
         run_ours(args)
 

@@ -176,6 +176,27 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
                           const prnu_grid* grid, const prnu_window* windows,
                           prnu_result* out, double* d_all_pce, prnu_stream stream);
 
+/* Noise residual by Mihcak's wavelet denoiser (the paper's denoiser, Sec.
+ * 2.2), the alternative to prnu_residual's 3x3 Wiener filter, with the same
+ * arguments plus the noise level sigma0 (grey levels; 3 is a common choice):
+ *   - the frame mirrored at its bottom and right edges (half-sample) up to
+ *     multiples of 16;
+ *   - a 4-level orthonormal separable transform with Daubechies' 8-tap filter
+ *     (4 vanishing moments), periodic;
+ *   - every detail coefficient c replaced by its noise part
+ *     c sigma0^2 / (s2 + sigma0^2), s2 = the smallest over W in {3, 5, 7, 9}
+ *     of max(0, mean of c^2 over the W x W window of its band - sigma0^2)
+ *     (zeros outside the band; 0 where s2 + sigma0^2 = 0); the coarsest
+ *     approximation band replaced by 0;
+ *   - the inverse transform cropped to H x W: W(I) = I - F(I);
+ *     R = I W(I) with PRNU_WEIGHT_BY_INTENSITY, else W(I); PRNU_NORMALISE as
+ *     prnu_residual.
+ * FP32 arithmetic.  H, W >= 16.  Scratch: two (H, W rounded up to 16) float
+ * images per frame, 16 frames at a time.  Asynchronous.  PRNU_EINVAL for a
+ * negative or non-finite sigma0, frames below 16 x 16, unknown flags. */
+int prnu_residual_wavelet(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags,
+                          int out_dtype, double sigma0, void* d_out, float* d_scale, prnu_stream stream);
+
 /* The reference fingerprint brought to a video's geometry: down-scaled (or
  * up-scaled) by `scale` and cropped (Sec. 3: the fingerprint estimated from
  * images must be down-scaled and cropped before it tests video frames; the

@@ -81,6 +81,8 @@ _SIGNATURES = {
                                   C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
     "eis_grid_search_naive": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint64),
                                         C.c_int, C.POINTER(prnu_grid), C.POINTER(prnu_window), _P, _P, _P]),
+    "prnu_residual_wavelet": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int, C.c_int,
+                                        C.c_double, _P, _P, _P]),
     "prnu_fingerprint_resize": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.c_double, C.c_int, C.c_int, _P,
                                           C.c_int, C.c_int, _P]),
     "eis_grid_search_frames": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_size_t, C.c_int,
@@ -265,6 +267,17 @@ class Context:
                                     out.ctypes.data_as(_P), its.ctypes.data_as(_P), _stream(stream)),
                "eis_correction")
         return out, its
+
+    def prnu_residual_wavelet(self, frames, out, sigma0=3.0, flags=PRNU_WEIGHT_BY_INTENSITY, scale=None, pitch=0,
+                              stream=None):
+        """Residual by Mihcak's wavelet denoiser (Sec. 2.2).  frames: CUDA
+        uint8 [F, H, W]; out: CUDA [F, H, W] float32/float16/bfloat16."""
+        import torch
+        F, H, W = frames.shape
+        dt = {torch.float32: PRNU_F32, torch.float16: PRNU_F16, torch.bfloat16: PRNU_BF16}[out.dtype]
+        _check(lib().prnu_residual_wavelet(self.h, _ptr(frames), F, H, W, pitch, flags, dt, float(sigma0), _ptr(out),
+                                           _ptr(scale), _stream(stream)), "prnu_residual_wavelet")
+        return out
 
     def prnu_fingerprint_resize(self, K, scale, y0, x0, H, W, out=None, stream=None):
         """The fingerprint K (CUDA float tensor [Hin, Win], rows may be

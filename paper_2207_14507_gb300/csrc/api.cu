@@ -751,7 +751,8 @@ int prnu_destroy(prnu_ctx* ctx) {
     ctx->fps.clear();
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
                          &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest,
-                         &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders, &ctx->ws_resize})
+                         &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders, &ctx->ws_resize,
+                         &ctx->ws_wav})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     ctx_free(ctx, ctx->d_err, sizeof(int));
@@ -790,6 +791,40 @@ int prnu_residual(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, s
       scale = reinterpret_cast<float*>(reinterpret_cast<char*>(partials) + ((sizeof(double) * np + 255) & ~(size_t)255));
     launch_residual(d_frames, F, H, W, pitch, flags, out_dtype, d_out, scale, acc, partials, (int)np, s,
                     ctx->launches);
+    PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
+  });
+}
+
+int prnu_residual_wavelet(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags,
+                          int out_dtype, double sigma0, void* d_out, float* d_scale, prnu_stream stream) {
+  return guarded([&] {
+    PRNU_CHECK_ARG(ctx, "NULL context");
+    PRNU_CHECK_ARG(F >= 0, "F must be >= 0");
+    if (F == 0) return;
+    PRNU_CHECK_ARG(d_frames && d_out, "NULL argument");
+    PRNU_CHECK_ARG(H >= 16 && W >= 16 && (long long)H * W <= (1LL << 26), "frames must be at least 16 x 16");
+    if (pitch == 0) pitch = (size_t)W;
+    PRNU_CHECK_ARG(pitch >= (size_t)W, "pitch < W");
+    PRNU_CHECK_ARG(out_dtype == kF32 || out_dtype == kF16 || out_dtype == kBF16, "unknown output dtype");
+    PRNU_CHECK_ARG((flags & ~(PRNU_WEIGHT_BY_INTENSITY | PRNU_NORMALISE)) == 0, "unknown flags");
+    PRNU_CHECK_ARG(std::isfinite(sigma0) && sigma0 >= 0.0, "sigma0 must be finite and >= 0");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
+    const size_t Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16;
+    const int chunk = std::min(F, 16);
+    const size_t buf = Hp * Wp * chunk * sizeof(float);
+    const size_t np = (flags & PRNU_NORMALISE) ? wavelet_partials_needed(F, H, W) : 0;
+    const size_t sc = (flags & PRNU_NORMALISE) && !d_scale ? sizeof(float) * F : 0;
+    ensure_buf(ctx, ctx->ws_wav, 2 * buf + sizeof(double) * np + sc + 1024);
+    char* base = reinterpret_cast<char*>(ctx->ws_wav.p);
+    float* bufA = reinterpret_cast<float*>(base);
+    float* bufT = reinterpret_cast<float*>(base + buf);
+    double* partials = reinterpret_cast<double*>(base + 2 * buf);
+    float* scale = d_scale ? d_scale : (sc ? reinterpret_cast<float*>(base + 2 * buf + sizeof(double) * np) : nullptr);
+    launch_wavelet_residual(d_frames, F, H, W, pitch, flags, out_dtype, (float)sigma0, d_out, scale, bufA, bufT, chunk,
+                            partials, s, ctx->launches);
     PRNU_CUDA_TRY(cudaEventRecord(ctx->last_done, s));
   });
 }

@@ -146,6 +146,18 @@ void launch_literal_residuals(const uint8_t* frames, size_t pitch, int H, int W,
                               int weight, float* out, const ResidLayout& lay, float* X, double* partials, float* nu2,
                               cudaStream_t s, LaunchCounter& lc);
 size_t literal_partials_needed(int nr, int H, int W);
+// s[f] = 1 / RMS from per-block sums of R^2 (nblk per frame); fill p[0..n) with v
+void launch_resid_scale(const double* partials, int nblk, int F, int H, int W, float* scale, cudaStream_t s,
+                        LaunchCounter& lc);
+void launch_fill(float* p, int n, float v, cudaStream_t s, LaunchCounter& lc);
+// residual by Mihcak's wavelet denoiser, `chunk` frames at a time through the
+// scratch buffers bufA, bufT (chunk * Hp * Wp floats each, Hp, Wp = H, W
+// rounded up to multiples of 16); partials: wavelet_partials_needed(F, H, W)
+// doubles (PRNU_NORMALISE only); H, W >= 16
+void launch_wavelet_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, int flags, int dtype,
+                             float sigma0, void* out, float* scale, float* bufA, float* bufT, int chunk,
+                             double* partials, cudaStream_t s, LaunchCounter& lc);
+size_t wavelet_partials_needed(int F, int H, int W);
 // fingerprint resampling with T taps per axis: weights and (clamped) indices per output row and column
 void launch_fp_resize(const float* K, size_t pitch, const float* wy, const int* iy, const float* wx, const int* ix,
                       int T, int H, int W, float* out, cudaStream_t s, LaunchCounter& lc);
@@ -212,7 +224,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders, ws_resize;
+      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders, ws_resize, ws_wav;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up

@@ -480,3 +480,17 @@ void launch_fp_resize(const float* K, size_t pitch, const float* wy, const int* 
   lc.n++;
 }
 }  // namespace prnu
+
+namespace prnu {
+void launch_resid_scale(const double* partials, int nblk, int F, int H, int W, float* scale, cudaStream_t s,
+                        LaunchCounter& lc) {
+  k_resid_scale<<<F, 256, 0, s>>>(partials, nblk, H, W, scale);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
+void launch_fill(float* p, int n, float v, cudaStream_t s, LaunchCounter& lc) {
+  k_fill<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n++;
+}
+}  // namespace prnu
