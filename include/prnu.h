@@ -400,6 +400,10 @@ typedef struct {
     int persistent;       /* 1: sizes with compile-time-planned kernels run a whole call
                              as one persistent launch that schedules every phase of every
                              candidate as tasks (spectra stay in L2); 0: waves */
+    int streams;          /* 1 or 2: waves of compile-time-planned sizes alternate between
+                             the call's stream and a second stream of the context, each
+                             with its own half of the workspace, so that one wave's
+                             kernels overlap the next wave's (set_tuning: 0 keeps 1) */
 } prnu_tuning;
 
 /* Read / override the configuration used for frames of H x W. */

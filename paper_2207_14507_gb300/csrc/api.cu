@@ -164,6 +164,9 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
   t.ppb = find_fixed(H, W) ? 1 : 2;
   const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
   t.wave = (int)std::max<size_t>(1, std::min<size_t>(512, ((size_t)4 << 30) / per_item));
+  // one stream: two-stream waves gain under 1% at 1080p and make the
+  // per-launch event times overlap (prnu_set_tuning selects them)
+  t.streams = 1;
   return t;
 }
 
@@ -282,7 +285,10 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
     const long long nrf = (H / 2) / fs->persist.ppb, ncol = (Wh + fs->persist.nc - 1) / fs->persist.nc;
     persistent = (long long)(n + 3) * (2 * nrf + ncol + 1) < (long long)INT_MAX;
   }
-  const int slots = persistent ? kPersistSlots : wave;
+  // two-stream waves: alternate waves on s and the context's second stream,
+  // each on its own half of the workspace
+  const bool two = fs && !persistent && !naive && tn.streams == 2 && n > wave;
+  const int slots = persistent ? kPersistSlots : (two ? 2 * wave : wave);
 
   if (*c->h_err)   // a bounded wait of an earlier asynchronous call gave up
     report_device_abort(c, s, "a bounded device-side wait of an earlier call timed out; its results are invalid");
@@ -344,6 +350,25 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
     a.nitems = n;
     launch_persistent(a, p, *fs, c->sm_count, s, c->launches);
     PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, p.error, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else if (two) {
+    if (!c->aux) {
+      PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+      PRNU_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      PRNU_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    PRNU_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    for (int i0 = 0, k = 0; i0 < n; i0 += wave, ++k) {
+      PassArgs ak = a;
+      ak.item0 = i0;
+      ak.nitems = std::min(wave, n - i0);
+      ak.spec = a.spec + (size_t)(k & 1) * wave * H * Wh;
+      ak.stats = a.stats + (size_t)(k & 1) * wave * H;
+      launch_fixed_wave(ak, *fs, tn.variant, (k & 1) ? c->aux : s, c->launches);
+    }
+    PRNU_CUDA_TRY(cudaEventRecord(c->ev_join, c->aux));
+    PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+    PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   } else if (!naive) {
     for (int i0 = 0; i0 < n; i0 += wave) {
       a.item0 = i0;
@@ -758,6 +783,9 @@ int prnu_destroy(prnu_ctx* ctx) {
     ctx_free(ctx, ctx->d_err, sizeof(int));
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     cudaEventDestroy(ctx->last_done);
     cudaEventDestroy(ctx->stage_free);
     delete ctx;
@@ -1291,6 +1319,7 @@ int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
     out->wave = t.wave;
     out->variant = t.variant;
     out->persistent = t.persistent;
+    out->streams = t.streams;
   });
 }
 
@@ -1325,7 +1354,9 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
     PRNU_CHECK_ARG(cfg->variant >= -1 && cfg->variant < (fs ? (int)fs->cols.size() : 0),
                    "variant out of range for this frame size (-1 = generic kernels)");
     PRNU_CHECK_ARG(cfg->persistent == 0 || cfg->persistent == 1, "persistent must be 0 or 1");
-    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant, cfg->persistent};
+    PRNU_CHECK_ARG(cfg->streams >= 0 && cfg->streams <= 2, "streams must be 0, 1 or 2");
+    ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant, cfg->persistent,
+                                 cfg->streams == 2 ? 2 : 1};
   });
 }
 

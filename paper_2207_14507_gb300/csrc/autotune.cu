@@ -152,6 +152,7 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
       best->wave = winner.wave;
       best->variant = winner.variant;
       best->persistent = winner.persistent;
+      best->streams = winner.streams;
     }
   } catch (const Error& e) {
     set_error(e.msg);

@@ -206,6 +206,7 @@ struct Tuning {
   int wave = 64;      // candidates in flight
   int variant = 0;    // compile-time-planned column variant; -1 = generic kernels only
   int persistent = 0; // compile-time-planned shapes: one persistent launch per call instead of waves
+  int streams = 1;    // compile-time-planned shapes: waves alternate over 1 or 2 streams
 };
 
 }  // namespace prnu
@@ -232,6 +233,8 @@ struct prnu_ctx {
   std::vector<char> h_stage;      // staging for host->device descriptors
   char* h_pinned = nullptr;
   size_t h_pinned_bytes = 0;
+  cudaStream_t aux = nullptr;                    // the second stream of two-stream waves
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t stage_free = nullptr;
   std::map<std::pair<int, int>, prnu::Tuning> tuning;
   std::unique_ptr<prnu::Server> server;

@@ -15,49 +15,82 @@ namespace prnu {
 
 namespace {
 
-constexpr int kBX = 32, kBY = 8;
+// A block covers a 32 x 32 tile with 32 x 8 threads (4 rows each); the tile
+// and its one-pixel halo (borders replicated) are staged once in shared memory.
+constexpr int kBX = 32, kBY = 32, kBR = 4, kTW = kBX + 2, kTH = kBY + 2;
+static_assert(kBY == 8 * kBR, "a thread covers kBR rows of the tile");
 
-__device__ __forceinline__ void moments3x3(const uint8_t* __restrict__ f, size_t pitch, int H, int W, int y, int x,
-                                           int* s1, int* s2, int* xc) {
+__device__ __forceinline__ void load_tile_u8(const uint8_t* __restrict__ f, size_t pitch, int H, int W, int* tile) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  const int x0 = blockIdx.x * kBX - 1, y0 = blockIdx.y * kBY - 1;
+  for (int k = tid; k < kTW * kTH; k += kBX * 8) {
+    const int sy = k / kTW, sx = k - sy * kTW;
+    const int y = min(max(y0 + sy, 0), H - 1), x = min(max(x0 + sx, 0), W - 1);
+    tile[k] = __ldg(f + (size_t)y * pitch + x);
+  }
+  __syncthreads();
+}
+
+// 3x3 sums of x and x^2 and the centre of tile pixel (tx, ty)
+__device__ __forceinline__ void moments3x3(const int* tile, int tx, int ty, int* s1, int* s2, int* xc) {
   int a = 0, b = 0;
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    int yy = min(max(y + dy, 0), H - 1);
-    const uint8_t* row = f + (size_t)yy * pitch;
+  for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      int xx = min(max(x + dx, 0), W - 1);
-      int v = __ldg(row + xx);
+    for (int dx = 0; dx < 3; ++dx) {
+      const int v = tile[(ty + dy) * kTW + tx + dx];
       a += v;
       b += v * v;
     }
-  }
   *s1 = a;
   *s2 = b;
-  *xc = __ldg(f + (size_t)y * pitch + x);
+  *xc = tile[(ty + 1) * kTW + tx + 1];
 }
 
-__global__ void k_resid_moments(const uint8_t* __restrict__ frames, size_t pitch, int H, int W,
-                                unsigned long long* __restrict__ acc) {
-  __shared__ unsigned long long part[kBX * kBY / 32];
+// per block: the integer sum of 81 * (local variance) of its pixels, one slot per block
+__global__ void __launch_bounds__(kBX * 8) k_resid_moments(const uint8_t* __restrict__ frames, size_t pitch, int H,
+                                                           int W, unsigned long long* __restrict__ part_out) {
+  __shared__ int tile[kTW * kTH];
+  __shared__ unsigned long long part[8];
   const int f = blockIdx.z;
-  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-  const uint8_t* fr = frames + (size_t)f * H * pitch;
+  load_tile_u8(frames + (size_t)f * H * pitch, pitch, H, W, tile);
+  const int tx = threadIdx.x, x = blockIdx.x * kBX + tx;
   unsigned long long v = 0;
-  if (x < W && y < H) {
-    int s1, s2, xc;
-    moments3x3(fr, pitch, H, W, y, x, &s1, &s2, &xc);
-    v = (unsigned long long)(9 * s2 - s1 * s1);
+#pragma unroll
+  for (int k = 0; k < kBR; ++k) {
+    const int ty = threadIdx.y + 8 * k, y = blockIdx.y * kBY + ty;
+    if (x < W && y < H) {
+      int s1, s2, xc;
+      moments3x3(tile, tx, ty, &s1, &s2, &xc);
+      v += (unsigned long long)(9 * s2 - s1 * s1);
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int tid = threadIdx.y * kBX + threadIdx.x;
-  if ((tid & 31) == 0) part[tid >> 5] = v;
+  if (tx == 0) part[threadIdx.y] = v;
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.y == 0 && tx == 0) {
     unsigned long long s = 0;
-    for (int k = 0; k < kBX * kBY / 32; ++k) s += part[k];
-    if (s) atomicAdd(acc + f, s);
+    for (int k = 0; k < 8; ++k) s += part[k];
+    part_out[(size_t)f * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// one block per frame: acc[f] = sum of the frame's block slots (integers: exact in any order)
+__global__ void k_resid_noise(const unsigned long long* __restrict__ part, int nblk,
+                              unsigned long long* __restrict__ acc) {
+  __shared__ unsigned long long red[32];
+  const int f = blockIdx.x;
+  unsigned long long v = 0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v += part[(size_t)f * nblk + k];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    acc[f] = t;
   }
 }
 
@@ -73,42 +106,48 @@ __device__ __forceinline__ float residual_value(int s1, int s2, int xc, float nu
 // MODE 0: store R; MODE 1: per-block sum of R^2 (double) to partials; MODE 2: store R * scale[f].
 // R(y, x) of frame f goes to out[f * lay.fpitch + lay.roff + y * lay.rpitch + x].
 template <int DT, int MODE>
-__global__ void k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, int H, int W,
-                              const unsigned long long* __restrict__ acc, int weight, void* __restrict__ out,
-                              double* __restrict__ partials, const float* __restrict__ scale, ResidLayout lay) {
-  __shared__ double part[kBX * kBY / 32];
-  const int f = blockIdx.z;
-  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-  const uint8_t* fr = frames + (size_t)f * H * pitch;
+__global__ void __launch_bounds__(kBX * 8) k_resid_apply(const uint8_t* __restrict__ frames, size_t pitch, int H,
+                                                         int W, const unsigned long long* __restrict__ acc,
+                                                         int weight, void* __restrict__ out,
+                                                         double* __restrict__ partials,
+                                                         const float* __restrict__ scale, ResidLayout lay) {
+  __shared__ int tile[kTW * kTH];
+  __shared__ double part[8];
   __shared__ float s_nu2[2];
+  const int f = blockIdx.z;
   if (threadIdx.x == 0 && threadIdx.y == 0) {   // once per block: the FP64 pipe is narrow
     const double nu2d = (double)acc[f] / (81.0 * (double)H * (double)W);
     s_nu2[0] = (float)nu2d;
     s_nu2[1] = (float)(81.0 * nu2d);
   }
-  __syncthreads();
+  load_tile_u8(frames + (size_t)f * H * pitch, pitch, H, W, tile);   // (synchronises)
   const float nu2 = s_nu2[0];
   const float nu2x81 = s_nu2[1];
-  float r = 0.f;
-  if (x < W && y < H) {
-    int s1, s2, xc;
-    moments3x3(fr, pitch, H, W, y, x, &s1, &s2, &xc);
-    r = residual_value(s1, s2, xc, nu2, nu2x81, weight);
-    const size_t o = (size_t)f * lay.fpitch + lay.roff + (size_t)y * lay.rpitch + x;
-    if (MODE == 0) store_store_type<DT>(out, o, r);
-    if (MODE == 2) store_store_type<DT>(out, o, r * scale[f]);
+  const int tx = threadIdx.x, x = blockIdx.x * kBX + tx;
+  float sq = 0.f;
+#pragma unroll
+  for (int k = 0; k < kBR; ++k) {
+    const int ty = threadIdx.y + 8 * k, y = blockIdx.y * kBY + ty;
+    if (x < W && y < H) {
+      int s1, s2, xc;
+      moments3x3(tile, tx, ty, &s1, &s2, &xc);
+      const float r = residual_value(s1, s2, xc, nu2, nu2x81, weight);
+      const size_t o = (size_t)f * lay.fpitch + lay.roff + (size_t)y * lay.rpitch + x;
+      if (MODE == 0) store_store_type<DT>(out, o, r);
+      if (MODE == 2) store_store_type<DT>(out, o, r * scale[f]);
+      sq = fmaf(r, r, sq);
+    }
   }
   if (MODE == 1) {   // float within a warp, double across warps and blocks
-    float v = r * r;
+    float v = sq;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int tid = threadIdx.y * kBX + threadIdx.x;
-    if ((tid & 31) == 0) part[tid >> 5] = (double)v;
+    if (tx == 0) part[threadIdx.y] = (double)v;
     __syncthreads();
-    if (tid == 0) {
-      double s = 0;
-      for (int k = 0; k < kBX * kBY / 32; ++k) s += part[k];
-      partials[(size_t)f * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.y == 0 && tx == 0) {
+      double t = 0;
+      for (int k = 0; k < 8; ++k) t += part[k];
+      partials[(size_t)f * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
   }
 }
@@ -441,14 +480,17 @@ void launch_residual(const uint8_t* frames, int F, int H, int W, size_t pitch, i
                      float* scale, unsigned long long* acc, double* partials, int /*max_partials*/, cudaStream_t s,
                      LaunchCounter& lc, const ResidLayout* lay) {
   const ResidLayout l = lay ? *lay : ResidLayout{W, (size_t)H * W, 0};
-  const dim3 b(kBX, kBY);
+  const dim3 b(kBX, 8);
   const dim3 g((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, F);
   const int weight = (flags & PRNU_WEIGHT_BY_INTENSITY) ? 1 : 0;
   ProfScope ps(lc, kKindResidual, s);
-  PRNU_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * F, s));
-  k_resid_moments<<<g, b, 0, s>>>(frames, pitch, H, W, acc);
+  // the block slots go to `partials` (8-byte slots, reused below by PRNU_NORMALISE)
+  auto* slots = reinterpret_cast<unsigned long long*>(partials);
+  k_resid_moments<<<g, b, 0, s>>>(frames, pitch, H, W, slots);
   PRNU_CUDA_TRY(cudaGetLastError());
-  lc.n++;
+  k_resid_noise<<<F, 256, 0, s>>>(slots, (int)(g.x * g.y), acc);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  lc.n += 2;
   if (flags & PRNU_NORMALISE) {
     apply_dispatch<1>(dtype, g, b, s, frames, pitch, H, W, acc, weight, out, partials, scale, l);
     PRNU_CUDA_TRY(cudaGetLastError());
