@@ -702,8 +702,8 @@ def run_precision(args):
         pce = res["r"]["pce"][:, 0]
         legs[name] = {"value": round(value, 1), "ms_per_step": round(ms, 1),
                       "path_roofline_frac": round(path_bytes(H, W, s_in, s_k) * value / 1e9 / peak, 4),
-                      "matched_min_pce": float(pce[wl.frame_fp == 0].min()),
-                      "unmatched_max_pce": float(pce[wl.frame_fp == 1].max()),
+                      "matched_min_pce": float(pce[wl.frame_fp == 0].min()) if (wl.frame_fp == 0).any() else None,
+                      "unmatched_max_pce": float(pce[wl.frame_fp == 1].max()) if (wl.frame_fp == 1).any() else None,
                       "decisions_at_60": [bool(p >= 60) for p in pce], "tuning": tuning,
                       "kernels": {k: round(v["total_ms"] / args.steps, 1) for k, v in prof.items()}}
     print(json.dumps({"workload": "precision-4k (config 4)", "metric": "candidates/s", "frames": F,
