@@ -64,6 +64,46 @@ def dist_env():
     return ws, rank, local
 
 
+class Replicas:
+    """One process per GPU, each running its own replica of the workload (the
+    search shards by frame and query with no exchange step: weak scaling, no
+    collective on the data path).  The only collectives are the timing ones:
+    a barrier around the timed region and the maximum of the per-rank times.
+    backend "nccl" on GPUs (reductions on `device`), "gloo" on CPU."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.ws, self.rank, self.local = dist_env()
+        self.backend = backend
+        self.device = device
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x: float) -> float:
+        """The largest x over all ranks (every rank gets it)."""
+        if self.ws == 1:
+            return float(x)
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device if self.backend == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def whole_job(self, units_per_rank: int, seconds_per_rank: float) -> float:
+        """Units all ranks processed / the slowest rank's time."""
+        return units_per_rank * self.ws / self.max(seconds_per_rank)
+
+    def close(self):
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------- algorithmic bytes
 
 def kernel_bytes(H, W, s_in, s_k):
@@ -246,11 +286,9 @@ def workload_config(args, H, W, F):
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    reps = Replicas("nccl", dev)
 
     import synth
     import paper_2207_14507_gb300 as prnu
@@ -287,9 +325,7 @@ def run_ours(args):
         ctx.prnu_fingerprint_release(h)
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize(dev)
 
     for _ in range(args.warmup):
@@ -306,13 +342,8 @@ def run_ours(args):
         barrier()
         prof = ctx.prnu_profile_end()
     launches = ctx.prnu_launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ncand * ws / (ms / 1e3)
+    ms = reps.max(e0.elapsed_time(e1) / args.steps)
+    value = reps.whole_job(ncand, ms / 1e3)
 
     # ---- e2e: the same step through the C ABI from pinned host memory
     frames_h = torch.from_numpy(wl.frames).pin_memory()
@@ -335,13 +366,8 @@ def run_ours(args):
     for _ in range(args.steps):
         res = step_e2e()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ncand * ws / e2e_s, "unit": UNIT,
+    e2e_s = reps.max((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": reps.whole_job(ncand, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(wl.frames.nbytes + wl.fingerprints[0].nbytes),
            "d2h_bytes_per_step": int(res.nbytes)}
 
@@ -408,9 +434,7 @@ def run_ours(args):
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    reps.close()
 
 
 # --------------------------------------------------------------------------- other workloads
