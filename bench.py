@@ -288,7 +288,7 @@ def run_ours(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    reps = Replicas("nccl", dev)
+    job = Replicas("nccl", dev)
 
     import synth
     import paper_2207_14507_gb300 as prnu
@@ -325,7 +325,7 @@ def run_ours(args):
         ctx.prnu_fingerprint_release(h)
 
     def barrier():
-        reps.barrier()
+        job.barrier()
         torch.cuda.synchronize(dev)
 
     for _ in range(args.warmup):
@@ -342,8 +342,8 @@ def run_ours(args):
         barrier()
         prof = ctx.prnu_profile_end()
     launches = ctx.prnu_launch_count() - launches0
-    ms = reps.max(e0.elapsed_time(e1) / args.steps)
-    value = reps.whole_job(ncand, ms / 1e3)
+    ms = job.max(e0.elapsed_time(e1) / args.steps)
+    value = job.whole_job(ncand, ms / 1e3)
 
     # ---- e2e: the same step through the C ABI from pinned host memory
     frames_h = torch.from_numpy(wl.frames).pin_memory()
@@ -366,8 +366,8 @@ def run_ours(args):
     for _ in range(args.steps):
         res = step_e2e()
     barrier()
-    e2e_s = reps.max((time.perf_counter() - t0) / args.steps)
-    e2e = {"value": reps.whole_job(ncand, e2e_s), "unit": UNIT,
+    e2e_s = job.max((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": job.whole_job(ncand, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(wl.frames.nbytes + wl.fingerprints[0].nbytes),
            "d2h_bytes_per_step": int(res.nbytes)}
 
@@ -434,7 +434,7 @@ def run_ours(args):
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    reps.close()
+    job.close()
 
 
 # --------------------------------------------------------------------------- other workloads
