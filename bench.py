@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--queries", type=int, default=16, help="serving: queries per run")
     ap.add_argument("--wave", type=int, default=0,
                     help="plain workload: candidates per wave after tuning (0 = the tuned value); for small profiles")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="column-pass variant of the compile-time-planned kernels; -1 = the generic "
+                         "runtime-plan kernels (default: the tuned or default variant)")
     ap.add_argument("--autotune-ms", type=float, default=5000.0,
                     help="time budget of the library autotuner run before the warm-up (0 = defaults)")
     return ap.parse_args()
@@ -313,8 +316,9 @@ def run_ours(args):
 
     tuning = ctx.prnu_autotune(H, W, fpd, budget_ms=args.autotune_ms) if args.autotune_ms > 0 \
         else ctx.prnu_get_tuning(H, W)
-    if args.wave > 0:
-        tuning = dict(tuning, wave=args.wave)
+    if args.wave > 0 or args.variant is not None:
+        tuning = dict(tuning, wave=args.wave if args.wave > 0 else tuning["wave"],
+                      variant=args.variant if args.variant is not None else tuning["variant"])
         ctx.prnu_set_tuning(H, W, tuning["col_width"], tuning["pairs_per_block"], tuning["wave"], tuning["variant"],
                             tuning["persistent"])
 
