@@ -431,3 +431,45 @@ def test_fingerprint_estimate_matches_oracle(ctx, prnu):
     assert np.corrcoef(got.ravel(), K.ravel())[0, 1] > 0.85
     same = ctx.prnu_fingerprint_estimate(torch.from_numpy(frames).to(DEV))     # dense frames, binding
     np.testing.assert_array_equal(same.cpu().numpy(), Kd.cpu().numpy())
+
+
+# ------------------------------------------------------------------ extreme sizes
+
+class _Grid:
+    """Two nodes: the identity (planted) and a 0.7 degree rotation."""
+    lam0, dlam, nlam, th0_deg, dth_deg, nth = 1.0, 0.0, 1, 0.0, 0.7, 2
+
+    @property
+    def size(self):
+        return 2
+
+
+@pytest.mark.parametrize("H,W", [(16, 16), (16, 4096), (4096, 16), (4096, 4096)])
+def test_extreme_sizes_search_matches_oracle(ctx, prnu, H, W):
+    """The smallest and largest sides the search accepts (16 and 4096, the
+    4096 plan's three radix-16 stages), on an unstabilised frame carrying the
+    fingerprint: both nodes' PCE within 1e-3 of the oracle and the oracle's
+    arg-max and shift (the identity at zero shift once the frame is large
+    enough for a 0.7 degree turn to lose the fingerprint)."""
+    rng = np.random.default_rng(H * 7 + W)
+    K = rng.normal(0.0, 0.02, (H, W))
+    content = 100.0 + 40.0 * np.sin(np.arange(W)[None, :] / 37.0) * np.cos(np.arange(H)[:, None] / 23.0)
+    frame = np.clip(np.rint(content * (1.0 + K) + rng.normal(0.0, 2.0, (H, W))), 0, 255).astype(np.uint8)
+    g = _Grid()
+    R = torch.empty((1, H, W), device=DEV)
+    ctx.prnu_residual(_t(frame[None]), R)
+    h = ctx.prnu_fingerprint_term(_t(K.astype(np.float32)))
+    allp = torch.empty((1, 1, 2), dtype=torch.float64, device=DEV)
+    got = ctx.eis_grid_search(R, [h], g, all_pce=allp)[0, 0]
+    ctx.prnu_fingerprint_release(h)
+    Rh = oracle.prnu_residual(frame)[0]
+    K0 = oracle.fingerprint_term(K.astype(np.float32).astype(np.float64))
+    ref = [oracle.score(Rh, K0, 1.0, th) for th in (0.0, oracle.grid_theta(0.0, 0.7, 1))]
+    gp = allp.cpu().numpy()[0, 0]
+    for k in range(2):
+        assert gp[k] == pytest.approx(ref[k]["pce"], rel=FP32_TOL)
+    best = int(np.argmax([r["pce"] for r in ref]))
+    assert abs(ref[0]["pce"] - ref[1]["pce"]) > 2 * FP32_TOL * max(r["pce"] for r in ref)   # no near-tie
+    assert int(got["cand_idx"]) == best and (int(got["dy"]), int(got["dx"])) == (ref[best]["dy"], ref[best]["dx"])
+    if H * W >= 16 * 4096:   # large enough for 0.7 degrees to lose the fingerprint: the identity wins
+        assert best == 0 and (ref[0]["dy"], ref[0]["dx"]) == (0, 0)
