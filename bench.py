@@ -465,8 +465,10 @@ def _timed_steps(step, steps, warmup, dev, ctx=None):
 
 def run_batched(args):
     """Config 3: 256 full-HD frames in one call, +-k warm-start windows
-    (k uniform in 2..10), FP32; plain per-candidate path on a sample of the
-    same inputs for the speedup."""
+    (k uniform in 2..10); FP32 (the configuration), or with --dtype f16/bf16
+    the FP16-storage variant (residuals with per-frame 1/RMS scale, FP16
+    fingerprint spectrum, FP32 arithmetic).  The plain per-candidate FP32
+    path runs on a sample of the same inputs for the speedup."""
     import torch
     import synth
     import paper_2207_14507_gb300 as prnu
@@ -476,47 +478,59 @@ def run_batched(args):
     F, H, W = wl.frames.shape
     win = wl.windows
     ncand = int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in win))
+    half = args.dtype != "f32"
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    fpd = prnu.PRNU_F16 if half else prnu.PRNU_F32
+    flags = prnu.PRNU_WEIGHT_BY_INTENSITY | (prnu.PRNU_NORMALISE if half else 0)
+    s_in, s_k = (2, 4) if half else (4, 8)
     ctx = prnu.Context(0)
-    tuning = ctx.prnu_autotune(H, W, prnu.PRNU_F32, budget_ms=args.autotune_ms) if args.autotune_ms > 0 else None
+    tuning = ctx.prnu_autotune(H, W, fpd, budget_ms=args.autotune_ms) if args.autotune_ms > 0 else None
     frames_d = torch.from_numpy(wl.frames).to(dev)
     K_d = torch.from_numpy(wl.fingerprints[0]).to(dev)
-    R = torch.empty((F, H, W), device=dev)
+    R = torch.empty((F, H, W), dtype=tdt, device=dev)
+    scale = torch.empty(F, device=dev)
     out_d = torch.empty((F, 32), dtype=torch.uint8, device=dev)
 
     def step():
-        ctx.prnu_residual(frames_d, R)
-        h = ctx.prnu_fingerprint_term(K_d)
-        ctx.eis_grid_search(R, [h], wl.grid, windows=win, out=out_d)
+        ctx.prnu_residual(frames_d, R, scale=scale, flags=flags)
+        h = ctx.prnu_fingerprint_term(K_d, fpd)
+        ctx.eis_grid_search(R, [h], wl.grid, windows=win, scale=scale, out=out_d)
         ctx.prnu_fingerprint_release(h)
 
     ms, prof = _timed_steps(step, args.steps, args.warmup, dev, ctx)
     value = ncand / (ms / 1e3)
-    # the plain per-candidate path on the first 4 frames' windows (same inputs)
+    res = out_d.cpu().numpy().view(prnu.RESULT_DTYPE).reshape(F)
+    hits = int(sum(abs(float(res[f]["lam"]) - wl.planted[f, 0]) <= wl.grid.dlam / 2 + 1e-6 and
+                   abs(float(res[f]["th_deg"]) - wl.planted[f, 1]) <= wl.grid.dth_deg / 2 + 1e-6 for f in range(F)))
+    # the plain per-candidate FP32 path on the first 4 frames' windows (same inputs)
+    R32 = torch.empty((4, H, W), device=dev)
+    ctx.prnu_residual(frames_d[:4], R32)
     h = ctx.prnu_fingerprint_term(K_d)
     sub = slice(0, 4)
     nsub = int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in win[sub]))
-    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub], naive=True)
+    ctx.eis_grid_search(R32, [h], wl.grid, windows=win[sub], naive=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub], naive=True)
+    ctx.eis_grid_search(R32, [h], wl.grid, windows=win[sub], naive=True)
     torch.cuda.synchronize(dev)
     naive = nsub / (time.perf_counter() - t0)
     t0 = time.perf_counter()
-    ctx.eis_grid_search(R[sub], [h], wl.grid, windows=win[sub])
+    ctx.eis_grid_search(R32, [h], wl.grid, windows=win[sub])
     torch.cuda.synchronize(dev)
     fused_sub = nsub / (time.perf_counter() - t0)
     ctx.prnu_fingerprint_release(h)
     peak, kind = hbm_peak()
-    pb = path_bytes(H, W, 4, 8)
+    pb = path_bytes(H, W, s_in, s_k)
     print(json.dumps({
         "workload": "batched-1080p (config 3)", "metric": "candidates/s", "value": round(value, 1),
         "frames": F, "candidates_per_step": ncand, "window_candidates": [int(((win[1:, 1] - win[1:, 0] + 1) * (win[1:, 3] - win[1:, 2] + 1)).min()),
                               int(((win[1:, 1] - win[1:, 0] + 1) * (win[1:, 3] - win[1:, 2] + 1)).max())],
-        "ms_per_step": round(ms, 2), "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "ms_per_step": round(ms, 2), "steps": args.steps, "warmup": args.warmup, "dtype": args.dtype,
         "path_roofline_frac": round(pb * value / 1e9 / peak, 4), "peak": f"{peak} GB/s {kind}",
+        "frames_within_half_a_grid_step_of_planted": hits,
         "naive_baseline": {"value": round(naive, 1), "speedup": round(value / naive, 2),
-                           "sample": f"first 4 frames' windows ({nsub} candidates), one call each way",
-                           "fused_same_sample": round(fused_sub, 1)},
+                           "sample": f"first 4 frames' windows ({nsub} candidates), FP32, one call each way",
+                           "fused_same_sample_f32": round(fused_sub, 1)},
         "tuning": tuning, "kernels": {k: round(v["total_ms"] / args.steps, 2) for k, v in prof.items()},
     }), flush=True)
     ctx.close()
