@@ -306,7 +306,9 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   PRNU_CHECK_ARG(!call.prepadded || (call.rdtype == kF32 && !naive), "prepadded residuals are FP32, planned or generic");
   const ResidLayout lay = (fs || call.prepadded) ? padded_layout(H, W) : dense_layout(H, W);
   const bool pad = fs && !call.prepadded;
-  if (pad) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 ? 4 : 2));
+  // half storage for the wave kernels: the pair layout (one load per row and sample)
+  const bool pairs = pad && !persistent && call.rdtype != kF32;
+  if (pad) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 || pairs ? 4 : 2));
   std::vector<FpDesc> fd = fp_descs(call);
   Stager st(c);
   st.add(c->ws_items.p, call.items.data(), call.items.size());
@@ -317,10 +319,10 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   PassArgs a{};
   a.resid = call.resid;
   if (pad) {
-    launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches);
+    launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches, pairs);
     a.resid = c->ws_pad.p;
   }
-  a.rdtype = call.rdtype;
+  a.rdtype = pairs ? (call.rdtype == kF16 ? kF16P : kBF16P) : call.rdtype;
   a.rpitch = lay.rpitch;
   a.fpitch = lay.fpitch;
   a.roff = lay.roff;

@@ -10,6 +10,10 @@
 namespace prnu {
 
 enum StoreType { kF32 = 0, kF16 = 1, kBF16 = 2 };
+// Zero-bordered residual layouts of the compile-time-planned row kernels for
+// half storage: element x holds the pair (R[x], R[x + 1]) as one 4-byte
+// word, so a bilinear sample takes one aligned load per row.
+enum PairStoreType { kF16P = 3, kBF16P = 4 };
 
 // One candidate of the search: which frame, which fingerprint, which grid
 // node, where its result goes, and the inverse-warp matrix

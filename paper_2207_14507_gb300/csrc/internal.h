@@ -168,7 +168,8 @@ void launch_fp_estimate_divide(const double* num, const double* den, float* K, s
                                LaunchCounter& lc);
 // dense [F][H][W] residuals -> the zero-bordered layout the compile-time-planned
 // kernels read (row pitch W + 3, pixel (0, 0) at W + 4, (H + 3)(W + 3) per frame)
-void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc);
+void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc,
+                       bool pairs = false);
 inline ResidLayout dense_layout(int H, int W) { return ResidLayout{W, (size_t)H * W, 0}; }
 inline ResidLayout padded_layout(int H, int W) {
   return ResidLayout{W + 3, (size_t)(H + 3) * (W + 3), (size_t)(W + 3) + 1};

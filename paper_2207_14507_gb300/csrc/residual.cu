@@ -189,6 +189,24 @@ __global__ void k_pad_frames(const T* __restrict__ in, int H, int W, T* __restri
   out[(size_t)f * (H + 3) * P + (size_t)yp * P + xp] = v;
 }
 
+// The same layout for half storage as pairs: element (yp, xp) holds the
+// 16-bit values of padded pixels (yp, xp) and (yp, xp + 1) (0 beyond the
+// padded row), the first in the low half (the .x of a __half2).
+__global__ void k_pad_pairs(const uint16_t* __restrict__ in, int H, int W, uint32_t* __restrict__ out) {
+  const int P = W + 3;
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x, yp = blockIdx.y;
+  const int f = blockIdx.z;
+  if (xp >= P) return;
+  const int x = xp - 1, y = yp - 1;
+  uint32_t lo = 0, hi = 0;
+  if ((unsigned)y < (unsigned)H) {
+    const uint16_t* row = in + ((size_t)f * H + y) * W;
+    if ((unsigned)x < (unsigned)W) lo = row[x];
+    if ((unsigned)(x + 1) < (unsigned)W) hi = row[x + 1];
+  }
+  out[(size_t)f * (H + 3) * P + (size_t)yp * P + xp] = lo | (hi << 16);
+}
+
 template <int MODE>
 void apply_dispatch(int dtype, dim3 g, dim3 b, cudaStream_t s, const uint8_t* frames, size_t pitch, int H, int W,
                     const unsigned long long* acc, int weight, void* out, double* partials, const float* scale,
@@ -438,11 +456,14 @@ void launch_fp_estimate_divide(const double* num, const double* den, float* K, s
   lc.n++;
 }
 
-void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc) {
+void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc,
+                       bool pairs) {
   if (F == 0) return;
   ProfScope ps(lc, kKindResidual, s);
   const dim3 b(256), g((W + 3 + 255) / 256, H + 3, F);
-  if (dtype == kF32)
+  if (pairs && dtype != kF32)
+    k_pad_pairs<<<g, b, 0, s>>>(reinterpret_cast<const uint16_t*>(in), H, W, reinterpret_cast<uint32_t*>(out));
+  else if (dtype == kF32)
     k_pad_frames<float><<<g, b, 0, s>>>(reinterpret_cast<const float*>(in), H, W, reinterpret_cast<float*>(out));
   else
     k_pad_frames<uint16_t><<<g, b, 0, s>>>(reinterpret_cast<const uint16_t*>(in), H, W,

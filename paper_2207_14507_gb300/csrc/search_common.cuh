@@ -165,6 +165,19 @@ struct StoreT<kBF16> {
   using type = __nv_bfloat16;
   __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 };
+// pair layouts: one load gives two horizontally adjacent taps
+template <>
+struct StoreT<kF16P> {
+  using type = __half2;
+  __device__ __forceinline__ static float2 ld2(const __half2* p) { return __half22float2(__ldg(p)); }
+};
+template <>
+struct StoreT<kBF16P> {
+  using type = __nv_bfloat162;
+  __device__ __forceinline__ static float2 ld2(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
+};
+template <int DT>
+constexpr bool kPairStore = DT == kF16P || DT == kBF16P;
 
 // Zero-bordered frame layout read by the compile-time-planned kernels: one
 // zero row/column before the frame and two after it, row pitch W + 3, so
@@ -194,7 +207,19 @@ __device__ __forceinline__ float bilinear_pad(const typename StoreT<DT>::type* _
   const float fx0 = floorf(qx), fy0 = floorf(qy);
   const float fx = qx - fx0, fy = qy - fy0;
   const auto* p = fr + __float2int_rn(fmaf(fy0, (float)P, fx0));
-  const float v00 = S::ld(p), v01 = S::ld(p + 1), v10 = S::ld(p + P), v11 = S::ld(p + P + 1);
+  float v00, v01, v10, v11;
+  if constexpr (kPairStore<DT>) {
+    const float2 a = S::ld2(p), b = S::ld2(p + P);
+    v00 = a.x;
+    v01 = a.y;
+    v10 = b.x;
+    v11 = b.y;
+  } else {
+    v00 = S::ld(p);
+    v01 = S::ld(p + 1);
+    v10 = S::ld(p + P);
+    v11 = S::ld(p + P + 1);
+  }
   const float top = fmaf(fx, v01 - v00, v00), bot = fmaf(fx, v11 - v10, v10);
   return fmaf(fy, bot - top, top);
 }

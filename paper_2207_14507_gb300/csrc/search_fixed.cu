@@ -875,6 +875,8 @@ struct ShapeDef {
     r.fwd[kF32] = (void*)k_row_forward_fx<kF32, RS, RT, PPB>;
     r.fwd[kF16] = (void*)k_row_forward_fx<kF16, RS, RT, PPB>;
     r.fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
+    r.fwd[kF16P] = (void*)k_row_forward_fx<kF16P, RS, RT, PPB>;
+    r.fwd[kBF16P] = (void*)k_row_forward_fx<kBF16P, RS, RT, PPB>;
     r.inv = (void*)k_row_inverse_fx<RS, RTI, PPB>;
     r.fin = (void*)k_finalize_fx<RS, RTI, kFinPairs>;
     r.fin_threads = RTI * kFinPairs;
@@ -883,6 +885,8 @@ struct ShapeDef {
     allow(k_row_forward_fx<kF32, RS, RT, PPB>);
     allow(k_row_forward_fx<kF16, RS, RT, PPB>);
     allow(k_row_forward_fx<kBF16, RS, RT, PPB>);
+    allow(k_row_forward_fx<kF16P, RS, RT, PPB>);
+    allow(k_row_forward_fx<kBF16P, RS, RT, PPB>);
     allow(k_row_inverse_fx<RS, RTI, PPB>);
     return r;
   }

@@ -25,7 +25,7 @@ struct FixedRow {
   int threads;               // per row pair, forward kernel
   int threads_inv;           // per row pair, inverse kernel
   size_t smem;
-  void* fwd[3];              // by residual storage type
+  void* fwd[5];              // by residual storage type (kF32, kF16, kBF16, kF16P, kBF16P)
   void* inv;
   void* fin;                 // per-candidate PCE (one block per candidate)
   int fin_threads;
