@@ -1,5 +1,10 @@
 """Plant plausible mistakes in the oracle (on the CPU) and check that a pin fails.
 
+Covered: the correlation sign, the warp matrix, the moments' border, the PCE
+window, the mean removal, the correction steps, Eq. 2's weighting, the wavelet
+filter, the shrinkage window choice, the fingerprint resampling, the
+frame-literal warp and the homography's angle.
+
 Each mutation replaces one oracle function for the duration of the test; the
 pin is then expected to raise AssertionError."""
 import numpy as np
@@ -38,6 +43,67 @@ def _no_mean_removal(K):
 
 
 _orig_pce = po.pce
+_orig_prnu_residual = po.prnu_residual
+
+
+def _widening_steps(n):
+    """Eq. 8's steps read literally (0.01^-n, 0.1^-n grow): the narrowing lost."""
+    return po._f32(0.01 * 10.0 ** (n - 1)), po._f32(0.1 * 10.0 ** (n - 1))
+
+
+def _estimate_without_intensity(frames):
+    """Eq. 2 with sum W(I) in the numerator instead of sum I W(I)."""
+    num = den = 0.0
+    for f in frames:
+        I = np.asarray(f, np.float64)
+        num = num + po.wiener_residual(I)[0]
+        den = den + I * I
+    out = np.zeros_like(num)
+    np.divide(num, den, out=out, where=den > 0)
+    return out
+
+
+_DB8_TYPO = po.DB8.copy()
+_DB8_TYPO[3] = -_DB8_TYPO[3]
+
+
+def _shrink_with_the_largest_window(c, sigma0):
+    """The largest of the four window variances instead of the smallest."""
+    c = np.asarray(c, np.float64)
+    c2 = c * c
+    s2 = None
+    for Wn in (3, 5, 7, 9):
+        r = Wn // 2
+        P = np.pad(c2, r)
+        acc = sum(P[dy:dy + c.shape[0], dx:dx + c.shape[1]] for dy in range(Wn) for dx in range(Wn))
+        v = np.maximum(acc / (Wn * Wn) - sigma0 ** 2, 0.0)
+        s2 = v if s2 is None else np.maximum(s2, v)
+    den = s2 + sigma0 ** 2
+    return np.where(den > 0, c * sigma0 ** 2 / np.where(den > 0, den, 1.0), 0.0)
+
+
+def _unwidened_tent(n_in, scale, first, n_out):
+    """Resampling with the tent never widened: shrinking aliases."""
+    Wm = np.zeros((n_out, n_in))
+    for r in range(n_out):
+        u = (first + r + 0.5) / scale - 0.5
+        j0 = int(np.floor(u))
+        for j, t in ((j0, 1.0 - (u - j0)), (j0 + 1, u - j0)):
+            Wm[r, min(max(j, 0), n_in - 1)] += t
+    return Wm
+
+
+def _literal_without_warp(frame, lam, theta_deg, weight_by_intensity=True):
+    """The frame's own residual whatever the candidate."""
+    return _orig_prnu_residual(frame, weight_by_intensity=weight_by_intensity)[0]
+
+
+def _similarity_angle_flipped(Hm):
+    lam, th = _orig_similarity(Hm)
+    return lam, -th
+
+
+_orig_similarity = po.similarity_from_homography
 
 MUTATIONS = [
     ("xcorr", _wrong_sign_xcorr, pins.test_shift_sign_convention),
@@ -45,12 +111,20 @@ MUTATIONS = [
     ("local_moments_3x3", _zero_padded_moments, pins.test_local_moments_match_scipy_nearest),
     ("pce", _pce_window9, pins.test_pce_golden_closed_forms),
     ("fingerprint_term", _no_mean_removal, pins.test_fingerprint_term_makes_correlation_blind_to_offsets),
+    ("_corr_step", _widening_steps, pins.test_correction_nodes_are_centred_and_spaced_by_the_iteration_step),
+    ("fingerprint_estimate", _estimate_without_intensity, pins.test_fingerprint_estimate_is_a_ratio_of_sums),
+    ("DB8", _DB8_TYPO, pins.test_dwt2_reconstructs_and_keeps_energy),
+    ("mihcak_shrink", _shrink_with_the_largest_window, pins.test_mihcak_shrink_of_an_isolated_coefficient),
+    ("resize_weights", _unwidened_tent, pins.test_resize_half_is_the_1331_filter),
+    ("literal_residual", _literal_without_warp, lambda: pins.test_literal_residual_commutes_with_a_quarter_turn(33)),
+    ("similarity_from_homography", _similarity_angle_flipped,
+     pins.test_similarity_from_homography_inverts_the_warp),
 ]
 
 
 @pytest.mark.parametrize("name,mutant,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pin_catches_mutation(monkeypatch, name, mutant, pin):
     monkeypatch.setattr(po, name, mutant)
-    monkeypatch.setattr(oracle, name, mutant)
+    monkeypatch.setattr(oracle, name, mutant, raising=False)
     with pytest.raises(AssertionError):
         pin()
