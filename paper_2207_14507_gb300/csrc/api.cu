@@ -843,7 +843,9 @@ int prnu_residual_wavelet(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     PRNU_CUDA_TRY(cudaStreamWaitEvent(s, ctx->last_done, 0));
     const size_t Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16;
-    const int chunk = std::min(F, 16);
+    // up to 16 frames at a time, within a quarter of what the budget leaves
+    const size_t used = ctx->used.load(), avail = ctx->budget > used ? ctx->budget - used : 0;
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>({(size_t)F, 16, avail / 4 / (2 * Hp * Wp * 4)}));
     const size_t buf = Hp * Wp * chunk * sizeof(float);
     const size_t np = (flags & PRNU_NORMALISE) ? wavelet_partials_needed(F, H, W) : 0;
     const size_t sc = (flags & PRNU_NORMALISE) && !d_scale ? sizeof(float) * F : 0;

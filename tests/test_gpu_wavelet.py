@@ -96,3 +96,21 @@ def test_wavelet_residual_rejects_bad_arguments(prnu):
         assert e.value.code == prnu.PRNU_EINVAL
         ctx.prnu_residual_wavelet(fr, out, 3.0)
         assert float(out.abs().max()) == 0.0     # a constant frame has no residual
+
+
+def test_wavelet_residual_in_chunks_equals_one_chunk(prnu):
+    """An 8 MB budget leaves room for about three 256x256 frames of scratch,
+    so four frames run in two chunks (and PRNU_NORMALISE recomputes each chunk
+    after the scales are known): the output equals the one-chunk run bit for
+    bit."""
+    wl = synth.make_workload(1, on_grid=True)
+    F = len(wl.frames)
+    outs = []
+    for budget in (0, 8 << 20):
+        with prnu.Context(0, hbm_budget_bytes=budget) as ctx:
+            out = torch.empty((F, 256, 256), dtype=torch.float16, device=DEV)
+            sc = torch.empty(F, device=DEV)
+            ctx.prnu_residual_wavelet(torch.from_numpy(wl.frames).to(DEV), out, 3.0,
+                                      prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE, scale=sc)
+            outs.append((out.cpu().numpy(), sc.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
