@@ -192,8 +192,9 @@ int eis_grid_search_naive(prnu_ctx* ctx, const void* d_resid, int dtype, const f
  *     R = I W(I) with PRNU_WEIGHT_BY_INTENSITY, else W(I); PRNU_NORMALISE as
  *     prnu_residual.
  * FP32 arithmetic.  H, W >= 16.  Scratch: two (H, W rounded up to 16) float
- * images per frame, 16 frames at a time.  Asynchronous.  PRNU_EINVAL for a
- * negative or non-finite sigma0, frames below 16 x 16, unknown flags. */
+ * images per frame, up to 16 frames at a time within a quarter of what the
+ * HBM budget leaves.  Asynchronous.  PRNU_EINVAL for a negative or
+ * non-finite sigma0, frames below 16 x 16, unknown flags. */
 int prnu_residual_wavelet(prnu_ctx* ctx, const uint8_t* d_frames, int F, int H, int W, size_t pitch, int flags,
                           int out_dtype, double sigma0, void* d_out, float* d_scale, prnu_stream stream);
 
