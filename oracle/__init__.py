@@ -5,3 +5,4 @@ may import this package.  It shares no code with the CUDA path and is never a
 fallback for it.
 """
 from .prnu_oracle import *  # noqa: F401,F403
+from . import parallel  # noqa: F401,E402

@@ -461,7 +461,7 @@ def correction_nodes(lam_c: float, th_c: float, n: int, th_half1: int = CORR_HAL
 
 
 def correction(R: np.ndarray, K0: np.ndarray, lam0: float = 1.0, th0: float = 0.0, max_iter: int = 3,
-               th_half1: int = CORR_HALF_TH1, K0_spectrum=None):
+               th_half1: int = CORR_HALF_TH1, K0_spectrum=None, score_nodes=None):
     """The correction operator of Sec. 3.2 for one frame residual R and one
     fingerprint term K0: at each iteration an exhaustive search over the
     iteration's nodes (ties to the lowest index, scale-major); stop when the
@@ -469,7 +469,9 @@ def correction(R: np.ndarray, K0: np.ndarray, lam0: float = 1.0, th0: float = 0.
     iterations.  Returns (best, iters, path): best = dict of the highest PCE
     seen over all iterations (earliest on ties) with lam, th_deg, cand (index in
     its iteration's node grid), iter (1-based); path = the estimate after each
-    iteration."""
+    iteration.  ``score_nodes`` (optional) scores a list of (lam, th) nodes of R
+    and K0 in order, e.g. a ``parallel.ScorePool`` of the same R and K0; by
+    default each node is scored here, one after the other."""
     if K0_spectrum is None:
         K0_spectrum = np.fft.rfft2(K0)
     lam_c, th_c = _f32(lam0), _f32(th0)
@@ -478,12 +480,15 @@ def correction(R: np.ndarray, K0: np.ndarray, lam0: float = 1.0, th0: float = 0.
     for n in range(1, max_iter + 1):
         lams, ths = correction_nodes(lam_c, th_c, n, th_half1)
         nb = len(ths)
+        nodes = [(lam, th) for lam in lams for th in ths]
+        if score_nodes is None:
+            scores = [score(R, K0, lam, th, K0_spectrum) for lam, th in nodes]
+        else:
+            scores = list(score_nodes(nodes))
         it_best = None
-        for a, lam in enumerate(lams):
-            for b, th in enumerate(ths):
-                r = score(R, K0, lam, th, K0_spectrum)
-                if it_best is None or r["pce"] > it_best["pce"]:
-                    it_best = dict(r, lam=lam, th_deg=th, cand=a * nb + b, iter=n)
+        for c, ((lam, th), r) in enumerate(zip(nodes, scores)):
+            if it_best is None or r["pce"] > it_best["pce"]:
+                it_best = dict(r, lam=lam, th_deg=th, cand=c, iter=n)
         if best is None or it_best["pce"] > best["pce"]:
             best = it_best
         path.append((it_best["lam"], it_best["th_deg"]))

@@ -2,8 +2,10 @@
 
 Covered: the correlation sign, the warp matrix, the moments' border, the PCE
 window, the mean removal, the correction steps, Eq. 2's weighting, the wavelet
-filter, the shrinkage window choice, the fingerprint resampling, the
-frame-literal warp and the homography's angle.
+filter (a sign typo, and the filter reversed), the wavelet analysis phase, the
+shrinkage window choice, the fingerprint resampling, the frame-literal warp,
+the homography's angle and the Wiener noise power (a median, zero-padded
+moments, the variance of the whole frame).
 
 Each mutation replaces one oracle function for the duration of the test; the
 pin is then expected to raise AssertionError."""
@@ -104,6 +106,42 @@ def _similarity_angle_flipped(Hm):
 
 
 _orig_similarity = po.similarity_from_homography
+_orig_moments = po.local_moments_3x3
+
+
+def _wiener_with(nu2_of):
+    """wiener_residual with the noise power taken by nu2_of(I, var) instead of
+    the mean of the replicated-border local variances."""
+    def wiener(I):
+        I = np.asarray(I, np.float64)
+        mu, var = _orig_moments(I)
+        nu2 = float(nu2_of(I, var))
+        den = np.maximum(var, nu2)
+        safe = np.where(den > 0, den, 1.0)
+        gain = np.where(den > 0, np.maximum(var - nu2, 0.0) / safe, 1.0)
+        return I - (mu + (I - mu) * gain), nu2
+    return wiener
+
+
+def _nu2_zero_padded(I, var):
+    return _zero_padded_moments(I)[1].mean()
+
+
+_DB8_REVERSED = po.DB8[::-1].copy()
+
+
+def _analysis_shifted(x, axis):
+    """The periodic analysis read one sample late: x[2n + k + 1]."""
+    return _orig_analysis(np.roll(x, -1, axis=axis), axis)
+
+
+def _synthesis_shifted(a, d, axis):
+    """Its transpose (so that the shifted pair still reconstructs)."""
+    return np.roll(_orig_synthesis(a, d, axis), 1, axis=axis)
+
+
+_orig_analysis = po._analysis_1d
+_orig_synthesis = po._synthesis_1d
 
 MUTATIONS = [
     ("xcorr", _wrong_sign_xcorr, pins.test_shift_sign_convention),
@@ -119,12 +157,34 @@ MUTATIONS = [
     ("literal_residual", _literal_without_warp, lambda: pins.test_literal_residual_commutes_with_a_quarter_turn(33)),
     ("similarity_from_homography", _similarity_angle_flipped,
      pins.test_similarity_from_homography_inverts_the_warp),
+    ("wiener_residual", _wiener_with(lambda I, var: np.median(var)), pins.test_wiener_impulse_closed_form),
+    ("wiener_residual", _wiener_with(_nu2_zero_padded), pins.test_wiener_impulse_closed_form),
+    ("wiener_residual", _wiener_with(lambda I, var: np.var(I)), pins.test_wiener_impulse_closed_form),
+    ("DB8", _DB8_REVERSED, pins.test_wavelet_analysis_of_an_impulse_closed_form),
+    (("_analysis_1d", "_synthesis_1d"), (_analysis_shifted, _synthesis_shifted),
+     pins.test_wavelet_analysis_of_an_impulse_closed_form),
 ]
+MUTATION_IDS = ["xcorr", "warp_matrix", "local_moments_3x3", "pce", "fingerprint_term", "_corr_step",
+                "fingerprint_estimate", "DB8", "mihcak_shrink", "resize_weights", "literal_residual",
+                "similarity_from_homography", "nu2_median", "nu2_zero_padded", "nu2_frame_variance",
+                "DB8_reversed", "wavelet_phase_shift"]
 
 
-@pytest.mark.parametrize("name,mutant,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutants_still_reconstruct():
+    """The wavelet mutants are the ones the older pins let through: the
+    reversed filter and the one-sample phase shift keep the transform
+    orthonormal, so reconstruction and energy hold."""
+    X = np.random.default_rng(3).standard_normal((32, 48))
+    for a, s in ((_analysis_shifted, _synthesis_shifted),):
+        lo, hi = a(X, 1)
+        np.testing.assert_allclose(s(lo, hi, 1), X, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,mutant,pin", MUTATIONS, ids=MUTATION_IDS)
 def test_pin_catches_mutation(monkeypatch, name, mutant, pin):
-    monkeypatch.setattr(po, name, mutant)
-    monkeypatch.setattr(oracle, name, mutant, raising=False)
+    names, mutants = (name, mutant) if isinstance(name, tuple) else ((name,), (mutant,))
+    for n, m in zip(names, mutants):
+        monkeypatch.setattr(po, n, m)
+        monkeypatch.setattr(oracle, n, m, raising=False)
     with pytest.raises(AssertionError):
         pin()

@@ -254,6 +254,46 @@ def test_wiener_constant_and_flat_frames():
     assert s == 1.0 and np.all(R == 0)
 
 
+def test_wiener_impulse_closed_form():
+    """A flat frame c with one interior impulse c + d.  Hand derivation: the 9
+    pixels whose 3x3 window holds the impulse have local variance
+    d^2/9 - (d/9)^2 = 8 d^2 / 81, every other pixel 0 (borders replicate a
+    constant), so the noise power -- the mean of the local variances over the
+    H W pixels -- is nu^2 = 8 d^2 / (9 H W).  Those 9 pixels keep the gain
+    1 - nu^2 / sigma^2 = 1 - 9 / (H W), so W = (I - mu) 9 / (H W): 8 d / (H W) at
+    the impulse, -d / (H W) at its 8 neighbours; elsewhere sigma^2 = 0 < nu^2,
+    the gain is 0 and W = I - mu = 0."""
+    H, W, c, d, y0, x0 = 24, 40, 50.0, 90.0, 9, 17
+    I = np.full((H, W), c)
+    I[y0, x0] += d
+    Wr, nu2 = oracle.wiener_residual(I)
+    assert nu2 == pytest.approx(8 * d * d / (9 * H * W), rel=1e-13)
+    ref = np.zeros((H, W))
+    ref[y0 - 1:y0 + 2, x0 - 1:x0 + 2] = -d / (H * W)
+    ref[y0, x0] = 8 * d / (H * W)
+    np.testing.assert_allclose(Wr, ref, rtol=0, atol=1e-12)
+
+
+def test_wiener_impulse_at_the_border_closed_form():
+    """The impulse in the corner (0, 0): with replicated borders the corner
+    value fills 4 cells of its own window, 2 of each edge neighbour's and 1 of
+    the diagonal's (window sums 4d, 2d, 2d, d over 9 cells); the local
+    variances are s(k) = k d^2/9 - (k d/9)^2 for k = 4, 2, 2, 1, and nu^2 is
+    their sum over H W."""
+    H, W, c, d = 20, 30, 40.0, 60.0
+    I = np.full((H, W), c)
+    I[0, 0] += d
+    Wr, nu2 = oracle.wiener_residual(I)
+    sv = {k: k * d * d / 9 - (k * d / 9) ** 2 for k in (4, 2, 1)}
+    assert nu2 == pytest.approx((sv[4] + 2 * sv[2] + sv[1]) / (H * W), rel=1e-13)
+    for (y, x), k in (((0, 0), 4), ((0, 1), 2), ((1, 0), 2), ((1, 1), 1)):
+        mu = c + k * d / 9
+        gain = max(sv[k] - nu2, 0.0) / max(sv[k], nu2)
+        assert Wr[y, x] == pytest.approx((I[y, x] - mu) * (1 - gain), rel=1e-12)
+    Wr[:2, :2] = 0.0
+    assert np.abs(Wr).max() < 1e-12
+
+
 def test_residual_normalised_rms_is_one():
     R, s = oracle.prnu_residual(_frame(13), normalise=True)
     assert np.sqrt(np.mean(R * R)) == pytest.approx(1.0, rel=1e-12)
@@ -616,6 +656,64 @@ def test_db8_filter_is_orthonormal_with_four_vanishing_moments():
     k = np.arange(8.0)
     for p in range(4):
         assert np.sum(k ** p * g) == pytest.approx(0.0, abs=1e-12)
+
+
+def _golden_db8():
+    with open(os.path.join(GOLDEN, "daubechies8.json")) as f:
+        return np.array(json.load(f)["h"])
+
+
+def test_db8_table_is_the_published_filter():
+    np.testing.assert_array_equal(oracle.DB8, _golden_db8())
+
+
+def test_wavelet_analysis_of_an_impulse_closed_form():
+    """Level-1 periodic analysis a[n] = sum_k h[k] x[(2n + k) mod N],
+    d[n] = sum_k g[k] x[(2n + k) mod N], g[k] = (-1)^k h[7 - k], of the impulse
+    x = e_m: a[n] = h[(m - 2n) mod N] and d[n] = g[(m - 2n) mod N] where that
+    index is below 8, else 0.  For m = 5, N = 16: a = (h5, h3, h1, 0, 0, 0, 0, h7)."""
+    h = _golden_db8()
+    g = np.array([(-1) ** k * h[7 - k] for k in range(8)])
+    N, m = 16, 5
+    x = np.zeros((1, N))
+    x[0, m] = 1.0
+    import oracle.prnu_oracle as po
+    a, d = po._analysis_1d(x, axis=1)
+    np.testing.assert_allclose(a[0], [h[5], h[3], h[1], 0, 0, 0, 0, h[7]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(d[0], [g[5], g[3], g[1], 0, 0, 0, 0, g[7]], rtol=0, atol=1e-15)
+    # the 2-D level: rows first, then columns; the impulse at (y0, x0) gives
+    # LL[n, q] = h[(y0 - 2n) mod N] h[(x0 - 2q) mod N]
+    X = np.zeros((N, N))
+    X[6, 5] = 1.0
+    LL, (LH, HL, HH) = oracle.dwt2_level(X)
+    hy = np.array([h[(6 - 2 * n) % N] if (6 - 2 * n) % N < 8 else 0.0 for n in range(N // 2)])
+    gy = np.array([g[(6 - 2 * n) % N] if (6 - 2 * n) % N < 8 else 0.0 for n in range(N // 2)])
+    hx = np.array([h[(5 - 2 * q) % N] if (5 - 2 * q) % N < 8 else 0.0 for q in range(N // 2)])
+    gx = np.array([g[(5 - 2 * q) % N] if (5 - 2 * q) % N < 8 else 0.0 for q in range(N // 2)])
+    np.testing.assert_allclose(LL, np.outer(hy, hx), atol=1e-15)
+    np.testing.assert_allclose(LH, np.outer(gy, hx), atol=1e-15)
+    np.testing.assert_allclose(HL, np.outer(hy, gx), atol=1e-15)
+    np.testing.assert_allclose(HH, np.outer(gy, gx), atol=1e-15)
+
+
+def test_wavelet_analysis_of_a_ramp_closed_form():
+    """x[n] = n on a period of N.  A window that does not wrap sees the ramp:
+    d[n] = sum_k g[k] (2n + k) = 0 (two vanishing moments suffice) and
+    a[n] = 2n sum_k h[k] + sum_k k h[k] = 2 sqrt(2) n + M1.  A window that
+    wraps sees the ramp minus N on its taps k >= N - 2n:
+    a[n] -= N sum_{k >= N - 2n} h[k], d[n] = -N sum_{k >= N - 2n} g[k]."""
+    h = _golden_db8()
+    g = np.array([(-1) ** k * h[7 - k] for k in range(8)])
+    N = 20
+    M1 = float(np.dot(np.arange(8.0), h))
+    import oracle.prnu_oracle as po
+    a, d = po._analysis_1d(np.arange(N, dtype=np.float64)[None, :], axis=1)
+    for n in range(N // 2):
+        tail = slice(max(N - 2 * n, 0), 8)
+        ea = 2 * np.sqrt(2) * n + M1 - N * h[tail].sum()
+        ed = -N * g[tail].sum()
+        assert a[0, n] == pytest.approx(ea, abs=1e-12)
+        assert d[0, n] == pytest.approx(ed, abs=1e-12)
 
 
 def test_dwt2_reconstructs_and_keeps_energy():
