@@ -337,6 +337,9 @@ int pce_score(prnu_ctx* ctx, const float* d_X, uint64_t fp_handle, int H, int W,
  *    calls whose GPU work overlaps race on it, so order them (one stream).
  *  - The first call on a device looks up the array's address and sets kernel
  *    attributes; make it before any stream capture on that device.
+ *  - d_X and d_K must both be device memory of the current device (checked
+ *    with cudaPointerGetAttributes: PRNU_EINVAL otherwise); the caller keeps
+ *    them H*W floats long and dense.
  * Host outputs, any of them may be NULL.  Synchronous (waits for `stream`). */
 int pce_score_noalloc(const float* d_X, const float* d_K, int H, int W,
                       double* pce, int* dy, int* dx, float* peak, prnu_stream stream);

@@ -5,8 +5,9 @@ FFTs).  Candidates are independent (Sec. 3.2: every node of the grid is
 scored on its own), so a pool of worker processes scores a list of nodes in
 parallel, one core each, with exactly the arithmetic of ``prnu_oracle.score``.
 The pool starts its workers with the ``spawn`` method: a process that has
-already touched a GPU must not fork.  Each worker holds one residual and one
-fingerprint term (set once, by the pool initializer).
+already touched a GPU must not fork.  The residuals and the fingerprint term
+reach the workers through .npy files in a private temporary directory (read
+memory-mapped), so large frames are not pickled once per worker.
 
 Only the tests and ``bench.py``'s CPU-baseline legs use it.
 """
@@ -14,6 +15,8 @@ from __future__ import annotations
 
 import multiprocessing as mp
 import os
+import shutil
+import tempfile
 from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
@@ -33,30 +36,40 @@ def available_cores() -> int:
         return os.cpu_count() or 1
 
 
-def _init(R, K0):
-    _STATE["R"] = np.asarray(R, dtype=np.float64)
-    _STATE["K0"] = np.asarray(K0, dtype=np.float64)
+def _init(d):
+    _STATE["R"] = np.load(os.path.join(d, "R.npy"), mmap_mode="r")
+    _STATE["K0"] = np.load(os.path.join(d, "K0.npy"))
     _STATE["FK"] = np.fft.rfft2(_STATE["K0"])
 
 
 def _score_node(node):
-    lam, th = node
-    return score(_STATE["R"], _STATE["K0"], lam, th, _STATE["FK"])
+    f, lam, th = node
+    return score(np.asarray(_STATE["R"][f]), _STATE["K0"], lam, th, _STATE["FK"])
 
 
 class ScorePool:
-    """``pool(nodes)`` -> [score(R, K0, lam, th) for (lam, th) in nodes], in order.
+    """Score candidates of the residual(s) R against K0 in worker processes.
 
-    A worker that cannot start or dies raises BrokenProcessPool in the caller
-    (rather than being replaced and waited for)."""
+    R is one residual [H, W] or a stack [F, H, W].  ``pool(nodes)`` takes
+    (lam, th) pairs (frame 0) or (f, lam, th) triples and returns
+    [score(R[f], K0, lam, th) ...] in order.  A worker that cannot start or
+    dies raises BrokenProcessPool in the caller (it is not replaced and waited
+    for)."""
 
     def __init__(self, R, K0, processes: int | None = None):
+        R = np.asarray(R, dtype=np.float64)
+        if R.ndim == 2:
+            R = R[None]
         self.processes = max(1, processes or available_cores())
+        self._dir = tempfile.mkdtemp(prefix="oracle-pool-")
+        np.save(os.path.join(self._dir, "R.npy"), R)
+        np.save(os.path.join(self._dir, "K0.npy"), np.asarray(K0, dtype=np.float64))
         self._pool = ProcessPoolExecutor(self.processes, mp_context=mp.get_context("spawn"), initializer=_init,
-                                         initargs=(R, K0))
+                                         initargs=(self._dir,))
 
     def __call__(self, nodes):
-        nodes = [(float(l), float(t)) for l, t in nodes]
+        nodes = [(0, float(n[0]), float(n[1])) if len(n) == 2 else (int(n[0]), float(n[1]), float(n[2]))
+                 for n in nodes]
         if not nodes:
             return []
         chunk = max(1, len(nodes) // (4 * self.processes))
@@ -66,6 +79,9 @@ class ScorePool:
         if self._pool is not None:
             self._pool.shutdown(wait=True, cancel_futures=True)
             self._pool = None
+        if self._dir is not None:
+            shutil.rmtree(self._dir, ignore_errors=True)
+            self._dir = None
 
     def __enter__(self):
         return self

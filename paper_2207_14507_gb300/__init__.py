@@ -176,12 +176,25 @@ def similarity_from_homography(Hm):
 
 def pce_score_noalloc(X, K, stream=None) -> dict:
     """PCE of the aligned pair (X, K) without any device allocation, for callers
-    that cannot allocate (see include/prnu.h).  X, K: float32 CUDA tensors [H, W]
-    with H*W <= 2^20."""
+    that cannot allocate (see include/prnu.h).  X, K: dense float32 CUDA tensors
+    [H, W] on one device, H*W <= 2^20.  The call runs with X's device current,
+    on `stream` or that device's current stream."""
+    import torch
+    if X.dim() != 2 or tuple(K.shape) != tuple(X.shape):
+        raise PrnuError(PRNU_EINVAL, "pce_score_noalloc", f"X {tuple(X.shape)} and K {tuple(K.shape)} "
+                                                          "must be [H, W] of one size")
+    if X.dtype != torch.float32 or K.dtype != torch.float32:
+        raise PrnuError(PRNU_EINVAL, "pce_score_noalloc", "X and K must be float32")
+    if not (X.is_cuda and K.is_cuda) or X.device != K.device:
+        raise PrnuError(PRNU_EINVAL, "pce_score_noalloc", "X and K must be CUDA tensors on one device")
+    if not (X.is_contiguous() and K.is_contiguous()):
+        raise PrnuError(PRNU_EINVAL, "pce_score_noalloc", "X and K must be contiguous")
     H, W = X.shape
     pce, dy, dx, peak = C.c_double(), C.c_int(), C.c_int(), C.c_float()
-    _check(lib().pce_score_noalloc(_ptr(X), _ptr(K), H, W, C.byref(pce), C.byref(dy), C.byref(dx),
-                                   C.byref(peak), _stream(stream)), "pce_score_noalloc")
+    with torch.cuda.device(X.device):
+        st = _stream(stream if stream is not None else torch.cuda.current_stream(X.device))
+        _check(lib().pce_score_noalloc(_ptr(X), _ptr(K), H, W, C.byref(pce), C.byref(dy), C.byref(dx),
+                                       C.byref(peak), st), "pce_score_noalloc")
     return dict(pce=pce.value, dy=dy.value, dx=dx.value, peak=peak.value)
 
 

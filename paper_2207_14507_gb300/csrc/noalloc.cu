@@ -82,6 +82,18 @@ unsigned char* scratch_for_device(int dev) {
   return g_addr[dev];
 }
 
+// PRNU_EINVAL unless p is device memory of device `dev`
+void check_device_pointer(const void* p, int dev, const char* what) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{PRNU_EINVAL, std::string(what) + " is not a CUDA pointer"};
+  }
+  if (at.type != cudaMemoryTypeDevice || at.device != dev)
+    throw Error{PRNU_EINVAL, std::string(what) + " must be device memory of the current device (" +
+                                 std::to_string(dev) + ")"};
+}
+
 }  // namespace
 
 }  // namespace prnu
@@ -98,6 +110,10 @@ extern "C" int pce_score_noalloc(const float* d_X, const float* d_K, int H, int 
                        " given); use pce_score for larger frames");
     int dev = 0;
     PRNU_CUDA_TRY(cudaGetDevice(&dev));
+    // both images must be device memory of the current device: the kernels
+    // below read H*W floats through each pointer on this device
+    check_device_pointer(d_X, dev, "X");
+    check_device_pointer(d_K, dev, "K");
     unsigned char* base = scratch_for_device(dev);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     LaunchCounter lc;
@@ -112,13 +128,11 @@ extern "C" int pce_score_noalloc(const float* d_X, const float* d_K, int H, int 
     float* scal = reinterpret_cast<float*>(base + kOffScal);   // mean, scale, inv_scale
     double* partials = reinterpret_cast<double*>(base + kOffPartials);
 
-    // twiddle tables: length W at tw[0], length H at tw[kMaxSide]
-    std::vector<int> off(kMaxFft + 1, 0);
-    off[W] = 0;
-    off[H] = kMaxSide;
-    FftPlan prow = make_plan(W, off);
-    off[W] = 0;
-    FftPlan pcol = make_plan(H, off);
+    // twiddle tables: length W at tw[0], length H at tw[kMaxSide] (the
+    // offsets are set here, not looked up, so H == W needs no special case)
+    const std::vector<int> zero_off(kMaxFft + 1, 0);
+    FftPlan prow = make_plan(W, zero_off);
+    FftPlan pcol = make_plan(H, zero_off);
     prow.tw_off = 0;
     pcol.tw_off = kMaxSide;
     k_noalloc_twiddles<<<8, 256, 0, s>>>(tw, W);
@@ -158,10 +172,12 @@ extern "C" int pce_score_noalloc(const float* d_X, const float* d_K, int H, int 
     a.col_log2 = lg;
     a.row_threads = rowT;
 
-    // fingerprint term: spectrum of K - mean(K), FP32
+    // fingerprint term: spectrum of K - mean(K), FP32.  Its row spectrum goes
+    // to specX (free until X's row pass) so that the column pass reads one
+    // buffer and writes another.
     launch_fp_stats(d_K, H, W, partials, kNblk, scal, scal + 1, scal + 2, false, s, lc);
     a.resid = d_K;
-    a.spec = specK;
+    a.spec = specX;
     launch_row_forward(a, false, scal, nullptr, s, lc);
     launch_col(a, 1, specK, nullptr, scal + 1, s, lc);
     // the pair: row FFT of X, correlation with the fingerprint, PCE

@@ -50,6 +50,38 @@ def test_two_calls_in_a_row_match_pce_score(prnu):
             assert got["peak"] == pytest.approx(ref["peak"], rel=FP32_TOL)
 
 
+def test_square_frame_and_fingerprint_offset(prnu):
+    """H == W (both FFT lengths share one size, so the two twiddle tables have
+    the same length), and a fingerprint with a DC offset: the mean is removed
+    inside, so K + 0.5 scores as K does."""
+    X, K, s = _pair(1024, 1024, 7)
+    ref = _reference(prnu, X, K)
+    assert (ref["dy"], ref["dx"]) == s
+    for _call in range(2):
+        got = prnu.pce_score_noalloc(X, K)
+        assert (got["dy"], got["dx"]) == s
+        assert got["pce"] == pytest.approx(ref["pce"], rel=FP32_TOL)
+        off = prnu.pce_score_noalloc(X, K + 0.5)
+        assert (off["dy"], off["dx"]) == s
+        assert off["pce"] == pytest.approx(ref["pce"], rel=FP32_TOL)
+
+
+def test_rejects_mismatched_inputs(prnu):
+    X, K, _ = _pair(128, 160, 9)
+    with pytest.raises(prnu.PrnuError):
+        prnu.pce_score_noalloc(X, K[:, :80].contiguous())
+    with pytest.raises(prnu.PrnuError):
+        prnu.pce_score_noalloc(X, K.half())
+    with pytest.raises(prnu.PrnuError):
+        prnu.pce_score_noalloc(X, K.t().contiguous().t())
+    # through the C ABI: a host pointer is refused before any kernel runs
+    import ctypes
+    host = np.zeros((128, 160), np.float32)
+    code = prnu.lib().pce_score_noalloc(ctypes.c_void_p(X.data_ptr()), host.ctypes.data_as(ctypes.c_void_p),
+                                        128, 160, None, None, None, None, None)
+    assert code == prnu.PRNU_EINVAL
+
+
 def test_rejects_frames_beyond_the_limit(prnu):
     X = torch.zeros((1080, 1920), device=DEV)
     with pytest.raises(prnu.PrnuError) as e:
