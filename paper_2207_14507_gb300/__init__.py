@@ -154,10 +154,14 @@ def make_grid(g) -> prnu_grid:
     return prnu_grid(g.lam0, g.dlam, g.nlam, g.th0_deg, g.dth_deg, g.nth)
 
 
-def make_windows(windows):
+def make_windows(windows, F=None):
+    """ctypes array of prnu_window from an int array [F, 4] (or None); with F
+    given, a count other than F raises PRNU_EINVAL (the library reads F)."""
     if windows is None:
         return None
     w = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 4)
+    if F is not None and len(w) != F:
+        raise PrnuError(PRNU_EINVAL, "windows", f"{len(w)} windows for {F} frames")
     arr = (prnu_window * len(w))()
     for i, (a, b, c, d) in enumerate(w):
         arr[i] = prnu_window(int(a), int(b), int(c), int(d))
@@ -314,7 +318,7 @@ class Context:
         P = len(fp_handles)
         hs = (C.c_uint64 * max(P, 1))(*fp_handles)
         g = make_grid(grid)
-        win = make_windows(windows)
+        win = make_windows(windows, F)
         host = out is None
         if host:
             out = np.zeros((F, P), dtype=RESULT_DTYPE)
@@ -358,7 +362,7 @@ class Context:
         P = len(fp_handles)
         hs = (C.c_uint64 * max(P, 1))(*fp_handles)
         g = make_grid(grid)
-        w = make_windows(windows)
+        w = make_windows(windows, F)
         host = out is None
         if host:
             res = np.zeros((F, P), dtype=RESULT_DTYPE)
@@ -386,7 +390,7 @@ class Context:
         F, H, W = frames.shape
         P = len(fp_handles)
         hs = (C.c_uint64 * max(P, 1))(*fp_handles)
-        w = make_windows(windows)
+        w = make_windows(windows, F)
         q = prnu_query(C.c_void_p(frames.data_ptr()), F, H, W, frames.stride(1), hs, P, make_grid(grid),
                        w, dtype, flags)
         qid = C.c_uint64()
