@@ -49,7 +49,10 @@ def parse():
                                                  "denoisers"],
                     default="plain",
                     help="plain = the 1080p metric line; the others print their own JSON record")
-    ap.add_argument("--queries", type=int, default=16, help="serving: queries per run")
+    ap.add_argument("--queries", type=int, default=16, help="serving: queries of the capacity run")
+    ap.add_argument("--steady-queries", type=int, default=100, help="serving: queries at 70%% of capacity")
+    ap.add_argument("--overload-queries", type=int, default=200, help="serving: queries at 20 queries/s")
+    ap.add_argument("--oracle-queries", type=int, default=20, help="serving: served queries checked by the oracle")
     ap.add_argument("--wave", type=int, default=0,
                     help="plain workload: candidates per wave after tuning (0 = the tuned value); for small profiles")
     ap.add_argument("--variant", type=int, default=None,
@@ -898,42 +901,53 @@ def run_precision(args):
 def run_serving(args):
     """Config 5: Poisson query stream (720p/1080p/4K, 8-64 frames, 1-16
     fingerprints, one matching with probability 0.5, +-k windows, FP16
-    storage, 120 GB admission budget).  Three runs: all queries at once
-    (capacity), a Poisson stream at 70% of the measured capacity, and the
-    nominal 20 queries/s (overloaded)."""
+    storage, 120 GB admission budget).  Three runs through query_submit /
+    query_poll: --queries queries submitted at once (capacity), then
+    --steady-queries at 70% of that capacity and --overload-queries at the
+    nominal 20 queries/s (overloaded when capacity is below it: latencies then
+    include queueing).  The FP64 oracle checks sampled served results: for
+    --oracle-queries queries of the steady run, one (frame, fingerprint) pair
+    each, the PCE at the served node and at its grid neighbours inside the
+    window."""
     import threading
     import torch
+    import oracle
     import synth
+    from oracle.parallel import ScorePool, available_cores
     import paper_2207_14507_gb300 as prnu
     prnu.build()
     dev = torch.device("cuda", 0)
-    n = args.queries
-    queries, banks = synth.make_query_stream(3 * n, rate_hz=20.0, pool_frames=8, match_sources=1)
+    n_cap, n_st, n_ov = args.queries, args.steady_queries, args.overload_queries
+    queries, banks, pools = synth.make_query_stream(n_cap + n_st + n_ov, rate_hz=20.0, pool_frames=8,
+                                                    match_sources=1, materialise=False)
     ctx = prnu.Context(0, hbm_budget_bytes=120 << 30)
     tunings = {}
     for (H, W) in banks:
         tunings[f"{H}x{W}"] = ctx.prnu_autotune(H, W, prnu.PRNU_F16, budget_ms=args.autotune_ms) \
-            if args.autotune_ms > 0 else None
+            if args.autotune_ms > 0 else ctx.prnu_get_tuning(H, W)
     handles = {k: [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(dev), prnu.PRNU_F16) for K in bank]
                for k, bank in banks.items()}
-    frames = [torch.from_numpy(q.frames).to(dev) for q in queries]
+    dpools = {k: torch.from_numpy(v).to(dev) for k, v in pools.items()}
     torch.cuda.synchronize(dev)
     ncand = [len(q.fp_ids) * int(sum((w[1] - w[0] + 1) * (w[3] - w[2] + 1) for w in q.windows)) for q in queries]
-
-    def submit(q, fr):
-        hs = [handles[(q.H, q.W)][i] for i in q.fp_ids]
-        return ctx.query_submit(fr, hs, synth.GRID_FULL, windows=q.windows, dtype=prnu.PRNU_F16,
-                                flags=prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE)
+    flags = prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE
+    results = {}
 
     def run(idx, arrivals):
-        ids = {}
-        done = []
+        ids, frames, done = {}, {}, []
+        lock = threading.Lock()
 
         def poller():
             for i in idx:
-                while i not in ids:
+                while True:
+                    with lock:
+                        if i in ids:
+                            break
                     time.sleep(0.0005)
-                ctx.query_poll(ids[i], queries[i].frames.shape[0], len(queries[i].fp_ids), timeout_us=-1)
+                q = queries[i]
+                results[i] = ctx.query_poll(ids[i], len(q.pool_index), len(q.fp_ids), timeout_us=-1)
+                with lock:
+                    frames.pop(i, None)       # the query's device frames are no longer needed
                 done.append(i)
 
         th = threading.Thread(target=poller)
@@ -943,37 +957,79 @@ def run_serving(args):
             now = time.perf_counter() - t0
             if t > now:
                 time.sleep(t - now)
-            ids[i] = submit(queries[i], frames[i])
+            q = queries[i]
+            fr = dpools[q.pool][torch.from_numpy(q.pool_index).to(dev)]     # this query's frames, on the device
+            torch.cuda.current_stream(dev).synchronize()
+            hs = [handles[(q.H, q.W)][b] for b in q.fp_ids]
+            qid = ctx.query_submit(fr, hs, synth.GRID_FULL, windows=q.windows, dtype=prnu.PRNU_F16, flags=flags)
+            with lock:
+                frames[i] = fr
+                ids[i] = qid
         th.join()
         wall = time.perf_counter() - t0
         lat = np.array([ctx.query_latency(ids[i])["total_ms"] for i in idx])
         return wall, lat
 
+    def summary(name, rate, idx, wall, lat, cap_q=None):
+        return {"rate_qps": None if rate is None else round(rate, 3), "queries": len(idx), "wall_s": round(wall, 2),
+                "throughput_qps": round(len(idx) / wall, 3),
+                "candidates_per_s": round(sum(ncand[i] for i in idx) / wall, 1),
+                "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                "overloaded": None if rate is None else bool(rate > cap_q)}
+
     # capacity: everything at once
-    idx0 = list(range(0, n))
-    wall, lat = run(idx0, [0.0] * n)
-    cap_q = n / wall
-    cap_c = sum(ncand[i] for i in idx0) / wall
-    # Poisson at 70% of capacity, and at the nominal 20 queries/s
+    idx0 = list(range(0, n_cap))
+    wall, lat = run(idx0, [0.0] * n_cap)
+    cap_q = n_cap / wall
+    out = {"capacity": summary("capacity", None, idx0, wall, lat)}
     rng = np.random.default_rng(5)
-    out = {}
-    for name, rate, idx in (("70pct_capacity", 0.7 * cap_q, list(range(n, 2 * n))),
-                            ("20qps_overloaded", 20.0, list(range(2 * n, 3 * n)))):
+    for name, rate, idx in (("70pct_capacity", 0.7 * cap_q, list(range(n_cap, n_cap + n_st))),
+                            ("20qps_overloaded", 20.0, list(range(n_cap + n_st, n_cap + n_st + n_ov)))):
         arr = np.cumsum(rng.exponential(1.0 / rate, size=len(idx)))
         w2, l2 = run(idx, list(arr))
-        out[name] = {"rate_qps": round(rate, 3), "queries": len(idx), "wall_s": round(w2, 2),
-                     "throughput_qps": round(len(idx) / w2, 3),
-                     "candidates_per_s": round(sum(ncand[i] for i in idx) / w2, 1),
-                     "p50_ms": round(float(np.percentile(l2, 50)), 1), "p99_ms": round(float(np.percentile(l2, 99)), 1),
-                     "overloaded": bool(rate > cap_q)}
+        out[name] = summary(name, rate, idx, w2, l2, cap_q)
     st = ctx.prnu_server_stats_get()
+    # the oracle on sampled served results of the steady run
+    t0 = time.perf_counter()
+    g = synth.GRID_FULL
+    checks, max_err, local_ok = [], 0.0, 0
+    sample = list(range(n_cap, n_cap + n_st))[:args.oracle_queries]
+    for i in sample:
+        q = queries[i]
+        f = int(rng.integers(0, len(q.pool_index)))
+        b = q.fp_ids.index(q.match) if q.match >= 0 else int(rng.integers(0, len(q.fp_ids)))
+        r = results[i][f, b]
+        c = int(r["cand_idx"])
+        ci, cj = divmod(c, g.nth)
+        lo_l, hi_l, lo_t, hi_t = (int(v) for v in q.windows[f])
+        nodes = [(ci + di, cj + dj) for di in (-1, 0, 1) for dj in (-1, 0, 1)
+                 if lo_l <= ci + di <= hi_l and lo_t <= cj + dj <= hi_t]
+        Rf = oracle.prnu_residual(pools[q.pool][q.pool_index[f]], normalise=True)[0]
+        K0 = oracle.fingerprint_term(banks[(q.H, q.W)][q.fp_ids[b]])
+        with ScorePool(Rf, K0, processes=min(len(nodes), available_cores())) as pool:
+            sc = pool([(g.lam_node(a), g.th_node(bb)) for a, bb in nodes])
+        ref = {n: s_["pce"] for n, s_ in zip(nodes, sc)}
+        err = abs(float(r["pce"]) - ref[(ci, cj)]) / abs(ref[(ci, cj)])
+        best = max(ref.values())
+        ok = ref[(ci, cj)] >= best * (1 - 2e-2) and (int(r["dy"]), int(r["dx"])) == (
+            sc[nodes.index((ci, cj))]["dy"], sc[nodes.index((ci, cj))]["dx"])
+        max_err = max(max_err, err)
+        local_ok += bool(ok)
+        checks.append({"query": i, "res": f"{q.W}x{q.H}", "frame": f, "fingerprint": q.fp_ids[b],
+                       "matched": bool(q.match >= 0), "served_pce": round(float(r["pce"]), 3),
+                       "oracle_pce": round(ref[(ci, cj)], 3), "rel_err": err, "local_argmax_ok": bool(ok)})
+    oracle_check = {"queries": len(sample), "max_pce_rel_err": max_err, "local_argmax_ok": local_ok,
+                    "seconds": round(time.perf_counter() - t0, 1),
+                    "what": "per sampled query one (frame, fingerprint) pair: the FP64 oracle's PCE at the served "
+                            "node (rel. error) and at its grid neighbours inside the window (the served node must "
+                            "score highest within 2e-2, with the oracle's shift)",
+                    "checks": checks}
+    mean_fp = float(np.mean([len(q.fp_ids) for q in queries]))
     print(json.dumps({"workload": "serving (config 5)", "metric": "served p50/p99 query latency",
-                      "capacity": {"queries_per_s": round(cap_q, 3), "candidates_per_s": round(cap_c, 1),
-                                   "queries": n, "p50_ms": round(float(np.percentile(lat, 50)), 1),
-                                   "p99_ms": round(float(np.percentile(lat, 99)), 1)},
                       "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
-                      "budget_gb": 120, "admitted_bytes_peak": st["admitted_bytes_peak"],
-                      "server_launches": st["server_launches"], "dtype": "f16", "tuning": tunings}), flush=True)
+                      "mean_fingerprints_per_query": round(mean_fp, 2), "budget_gb": 120,
+                      "admitted_bytes_peak": st["admitted_bytes_peak"], "server_launches": st["server_launches"],
+                      "dtype": "f16", "oracle_check": oracle_check, "tuning": tunings}), flush=True)
     ctx.close()
 
 

@@ -408,6 +408,12 @@ typedef struct {
                              the call's stream and a second stream of the context, each
                              with its own half of the workspace, so that one wave's
                              kernels overlap the next wave's (set_tuning: 0 keeps 1) */
+    int share_forward;    /* 1 (default): with P > 1 fingerprints, the candidates of one
+                             frame and grid node (Eq. 3 against each fingerprint) share
+                             one warp, row FFT and forward column FFT; the product and the
+                             inverse FFT run per fingerprint (compile-time-planned sizes,
+                             waves; the results equal those of 0 bit for bit).  0: every
+                             candidate runs its own forward pass. */
 } prnu_tuning;
 
 /* Read / override the configuration used for frames of H x W. */

@@ -56,7 +56,7 @@ class prnu_server_stats(C.Structure):
 
 class prnu_tuning(C.Structure):
     _fields_ = [("col_width", C.c_int), ("pairs_per_block", C.c_int), ("wave", C.c_int), ("variant", C.c_int),
-                ("persistent", C.c_int), ("streams", C.c_int)]
+                ("persistent", C.c_int), ("streams", C.c_int), ("share_forward", C.c_int)]
 
 
 class prnu_kernel_stat(C.Structure):
@@ -432,17 +432,18 @@ class Context:
         t = prnu_tuning()
         _check(lib().prnu_get_tuning(self.h, H, W, C.byref(t)), "prnu_get_tuning")
         return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant,
-                    persistent=t.persistent, streams=t.streams)
+                    persistent=t.persistent, streams=t.streams, share_forward=t.share_forward)
 
     def prnu_debug_set(self, key, value):
         _check(lib().prnu_debug_set(self.h, key, value), "prnu_debug_set")
 
-    def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave, variant=0, persistent=0, streams=1):
-        t = prnu_tuning(col_width, pairs_per_block, wave, variant, persistent, streams)
+    def prnu_set_tuning(self, H, W, col_width, pairs_per_block, wave, variant=0, persistent=0, streams=1,
+                        share_forward=1):
+        t = prnu_tuning(col_width, pairs_per_block, wave, variant, persistent, streams, share_forward)
         _check(lib().prnu_set_tuning(self.h, H, W, C.byref(t)), "prnu_set_tuning")
 
     def prnu_autotune(self, H, W, dtype=PRNU_F32, budget_ms=2000.0, stream=None) -> dict:
         t = prnu_tuning()
         _check(lib().prnu_autotune(self.h, H, W, dtype, budget_ms, C.byref(t), _stream(stream)), "prnu_autotune")
         return dict(col_width=t.col_width, pairs_per_block=t.pairs_per_block, wave=t.wave, variant=t.variant,
-                    persistent=t.persistent, streams=t.streams)
+                    persistent=t.persistent, streams=t.streams, share_forward=t.share_forward)

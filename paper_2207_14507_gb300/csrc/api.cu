@@ -170,6 +170,14 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
   return t;
 }
 
+bool share_forward(prnu_ctx* c, int H, int W, int P, bool naive) {
+  if (naive || P < 2) return false;
+  const Tuning t = tuning_for(c, H, W);
+  if (!t.share || t.persistent || t.variant < 0 || P > t.wave) return false;
+  const FixedShape* fs = find_fixed(H, W);
+  return fs && fixed_supports(*fs, H, t.ppb);
+}
+
 // Host-side staging of small descriptor arrays through pinned memory.
 struct Stager {
   prnu_ctx* c;
@@ -208,11 +216,12 @@ struct Stager {
   }
 };
 
-void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call) {
+void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call, bool unit_major) {
   PRNU_CHECK_ARG(g.nlam >= 1 && g.nth >= 1, "grid must have nlam >= 1 and nth >= 1");
   PRNU_CHECK_ARG((long long)g.nlam * g.nth <= (1 << 24), "grid too large");
   call.items.clear();
-  call.group_start.assign((size_t)F * P + 1, 0);
+  call.share = unit_major ? P : 1;
+  call.group_start.assign((size_t)F * (unit_major ? 1 : P) + 1, 0);
   call.cmax = g.nlam * g.nth;
   std::vector<float> lam(g.nlam), th(g.nth);
   for (int i = 0; i < g.nlam; ++i) lam[i] = (float)((double)g.lam0 + (double)i * (double)g.dlam);
@@ -226,31 +235,38 @@ void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, S
                      "window " + std::to_string(f) + " lies outside the grid");
       il = w.lam_lo; ih = w.lam_hi; jl = w.th_lo; jh = w.th_hi;
     }
-    for (int p = 0; p < P; ++p) {
-      call.group_start[(size_t)f * P + p] = (int)call.items.size();
-      for (int i = il; i <= ih; ++i) {
-        const double L = (double)lam[i];
-        PRNU_CHECK_ARG(L > 0 && std::isfinite(L), "grid scales must be positive");
-        for (int j = jl; j <= jh; ++j) {
-          const double t = (double)th[j] * 3.14159265358979323846 / 180.0;
-          const double cs = cos(t), sn = sin(t);
-          WorkItem it;
-          it.frame = f;
-          it.fp = p;
-          it.cand = i * g.nth + j;
-          it.group = f * P + p;
-          it.a11 = (float)(cs / L);
-          it.a12 = (float)(sn / L);
-          it.a21 = (float)(-sn / L);
-          it.a22 = (float)(cs / L);
-          it.lam = lam[i];
-          it.th_deg = th[j];
-          call.items.push_back(it);
-        }
+    auto node = [&](int p, int i, int j) {
+      const double L = (double)lam[i];
+      PRNU_CHECK_ARG(L > 0 && std::isfinite(L), "grid scales must be positive");
+      const double t = (double)th[j] * 3.14159265358979323846 / 180.0;
+      const double cs = cos(t), sn = sin(t);
+      WorkItem it;
+      it.frame = f;
+      it.fp = p;
+      it.cand = i * g.nth + j;
+      it.group = f * P + p;
+      it.a11 = (float)(cs / L);
+      it.a12 = (float)(sn / L);
+      it.a21 = (float)(-sn / L);
+      it.a22 = (float)(cs / L);
+      it.lam = lam[i];
+      it.th_deg = th[j];
+      call.items.push_back(it);
+    };
+    if (unit_major) {
+      call.group_start[f] = (int)call.items.size();
+      for (int i = il; i <= ih; ++i)
+        for (int j = jl; j <= jh; ++j)
+          for (int p = 0; p < P; ++p) node(p, i, j);
+    } else {
+      for (int p = 0; p < P; ++p) {
+        call.group_start[(size_t)f * P + p] = (int)call.items.size();
+        for (int i = il; i <= ih; ++i)
+          for (int j = jl; j <= jh; ++j) node(p, i, j);
       }
     }
   }
-  call.group_start[(size_t)F * P] = (int)call.items.size();
+  call.group_start.back() = (int)call.items.size();
   PRNU_CHECK_ARG(call.items.size() < (size_t)INT_MAX, "too many candidates");
 }
 
@@ -272,14 +288,18 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
                     cudaStream_t s) {
   const int H = call.H, W = call.W, Wh = W / 2;
   const int n = (int)call.items.size();
-  const int ngroups = (int)call.group_start.size() - 1;
+  const int share = std::max(call.share, 1);
+  const int ngroups = ((int)call.group_start.size() - 1) * share;
   const FftPlan prow = make_plan(W, c->tw_off), pcol = make_plan(H, c->tw_off);
   Tuning tn = tuning_for(c, H, W);
   int rowT, rowMB;
   row_launch_shape(prow, &rowT, &rowMB);
-  const int wave = naive ? 1 : std::max(1, std::min(tn.wave, n));
+  // waves hold whole forward units (share items each)
+  const int wave = naive ? 1 : std::max(share, std::min(tn.wave, n) / share * share);
   const FixedShape* fs = (!naive && tn.variant >= 0) ? find_fixed(H, W) : nullptr;
   if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
+  PRNU_CHECK_ARG(share == 1 || (fs && !tn.persistent && n % share == 0),
+                 "shared forward units need the compile-time-planned wave kernels");
   bool persistent = fs && tn.persistent && (H / 2) % fs->persist.ppb == 0;
   if (persistent) {   // tickets of one launch: (n + 3) steps of 2 row phases, the column phase and a finalisation
     const long long nrf = (H / 2) / fs->persist.ppb, ncol = (Wh + fs->persist.nc - 1) / fs->persist.nc;
@@ -287,8 +307,9 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   }
   // two-stream waves: alternate waves on s and the context's second stream,
   // each on its own half of the workspace
-  const bool two = fs && !persistent && !naive && tn.streams == 2 && n > wave;
-  const int slots = persistent ? kPersistSlots : (two ? 2 * wave : wave);
+  const bool two = fs && !persistent && !naive && tn.streams == 2 && n > wave && share == 1;
+  // forward units compute in slots after the wave's candidates (one per unit)
+  const int slots = persistent ? kPersistSlots : (two ? 2 * wave : wave + (share > 1 ? wave / share : 0));
 
   if (*c->h_err)   // a bounded wait of an earlier asynchronous call gave up
     report_device_abort(c, s, "a bounded device-side wait of an earlier call timed out; its results are invalid");
@@ -307,6 +328,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   const ResidLayout lay = (fs || call.prepadded) ? padded_layout(H, W) : dense_layout(H, W);
   const bool pad = fs && !call.prepadded;
   // half storage for the wave kernels: the pair layout (one load per row and sample)
+  // half storage for the wave kernels: the pair layout (one load per row and sample)
   const bool pairs = pad && !persistent && call.rdtype != kF32;
   if (pad) ensure_buf(c, c->ws_pad, (size_t)call.F * lay.fpitch * (call.rdtype == kF32 || pairs ? 4 : 2));
   std::vector<FpDesc> fd = fp_descs(call);
@@ -319,7 +341,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   PassArgs a{};
   a.resid = call.resid;
   if (pad) {
-    launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches, pairs);
+    launch_pad_frames(call.resid, call.rdtype, call.F, H, W, c->ws_pad.p, s, c->launches, pairs ? 1 : 0);
     a.resid = c->ws_pad.p;
   }
   a.rdtype = pairs ? (call.rdtype == kF16 ? kF16P : kBF16P) : call.rdtype;
@@ -342,6 +364,9 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.pairs_per_block = naive ? 2 : tn.ppb;
   a.col_log2 = tn.col_log2;
   a.row_threads = rowT;
+  a.share = share;
+  a.units = nullptr;
+  a.unit_of = nullptr;
 
   if (persistent) {
     int* st0 = reinterpret_cast<int*>(c->ws_persist.p);
@@ -364,6 +389,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
       PassArgs ak = a;
       ak.item0 = i0;
       ak.nitems = std::min(wave, n - i0);
+      ak.nunits = ak.nitems / share;
       ak.spec = a.spec + (size_t)(k & 1) * wave * H * Wh;
       ak.stats = a.stats + (size_t)(k & 1) * wave * H;
       launch_fixed_wave(ak, *fs, tn.variant, (k & 1) ? c->aux : s, c->launches);
@@ -375,6 +401,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
     for (int i0 = 0; i0 < n; i0 += wave) {
       a.item0 = i0;
       a.nitems = std::min(wave, n - i0);
+      a.nunits = a.nitems / share;
       if (fs) {
         launch_fixed_wave(a, *fs, tn.variant, s, c->launches);
       } else {
@@ -415,8 +442,8 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
                        c->launches);
     }
   }
-  launch_argmax(a.results, a.items, reinterpret_cast<const int*>(c->ws_groups.p), ngroups, d_out, call.scale, H, W,
-                s, c->launches);
+  launch_argmax(a.results, a.items, reinterpret_cast<const int*>(c->ws_groups.p), ngroups, share, d_out, call.scale,
+                H, W, s, c->launches);
   if (d_all) {
     PRNU_CUDA_TRY(cudaMemsetAsync(d_all, 0xff, sizeof(double) * (size_t)ngroups * call.cmax, s));
     launch_scatter_all(a.results, n, call.cmax, d_all, s, c->launches);
@@ -464,7 +491,7 @@ static int search_common(prnu_ctx* ctx, const void* d_resid, int dtype, const fl
       PRNU_CHECK_ARG(f->H == H && f->W == W, "fingerprint size differs from the frames");
       call.fps.push_back(f);
     }
-    build_items(*grid, windows, F, P, call);
+    build_items(*grid, windows, F, P, call, share_forward(ctx, H, W, P, naive));
     const bool dev_out = is_device_pointer(out);
     prnu_result* d_out = out;
     if (!dev_out) {
@@ -1324,6 +1351,7 @@ int prnu_get_tuning(prnu_ctx* ctx, int H, int W, prnu_tuning* out) {
     out->variant = t.variant;
     out->persistent = t.persistent;
     out->streams = t.streams;
+    out->share_forward = t.share;
   });
 }
 
@@ -1359,8 +1387,9 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
                    "variant out of range for this frame size (-1 = generic kernels)");
     PRNU_CHECK_ARG(cfg->persistent == 0 || cfg->persistent == 1, "persistent must be 0 or 1");
     PRNU_CHECK_ARG(cfg->streams >= 0 && cfg->streams <= 2, "streams must be 0, 1 or 2");
+    PRNU_CHECK_ARG(cfg->share_forward == 0 || cfg->share_forward == 1, "share_forward must be 0 or 1");
     ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant, cfg->persistent,
-                                 cfg->streams == 2 ? 2 : 1};
+                                 cfg->streams == 2 ? 2 : 1, cfg->share_forward};
   });
 }
 

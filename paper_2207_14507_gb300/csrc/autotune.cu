@@ -153,6 +153,7 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
       best->variant = winner.variant;
       best->persistent = winner.persistent;
       best->streams = winner.streams;
+      best->share_forward = winner.share;
     }
   } catch (const Error& e) {
     set_error(e.msg);

@@ -14,6 +14,7 @@ enum StoreType { kF32 = 0, kF16 = 1, kBF16 = 2 };
 // half storage: element x holds the pair (R[x], R[x + 1]) as one 4-byte
 // word, so a bilinear sample takes one aligned load per row.
 enum PairStoreType { kF16P = 3, kBF16P = 4 };
+constexpr int kNumStoreLayouts = 5;
 
 // One candidate of the search: which frame, which fingerprint, which grid
 // node, where its result goes, and the inverse-warp matrix
@@ -82,7 +83,21 @@ struct PassArgs {
   const void* const* frame_ptrs;
   int* err;                   // device flag set when a bounded device-side wait gives up (may be nullptr)
   int stall;                  // test hook: 1 = every bounded wait expects one arrival too many
+  // Forward units: items that share a frame and a grid node and differ only in
+  // the fingerprint share one warp, row FFT and forward column FFT, computed
+  // in slot nitems + u of the workspace (after the items' slots).  Unit u of
+  // the wave holds slots units[u] .. units[u+1]-1 and slot s belongs to unit
+  // unit_of[s] (device arrays), or, with units == nullptr, slots u*share ..
+  // u*share+share-1.  share = 1 and no table: every item is its own unit and
+  // computes in its own slot (nunits == nitems).
+  const int* units;
+  const int* unit_of;
+  int nunits;
+  int share;
 };
+
+__device__ __forceinline__ int unit_first(const PassArgs& a, int u) { return a.units ? a.units[u] : u * a.share; }
+__device__ __forceinline__ int unit_of_slot(const PassArgs& a, int s) { return a.unit_of ? a.unit_of[s] : s / a.share; }
 
 __device__ __forceinline__ WorkItem item_of(const PassArgs& a, int slot) {
   return a.item_ptrs ? *a.item_ptrs[slot] : a.items[a.item0 + slot];

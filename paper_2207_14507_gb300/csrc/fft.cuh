@@ -72,6 +72,12 @@ __device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// conj(a) * b with its rounding fixed: each component is one product rounded
+// on its own plus one fused multiply-add, so every kernel that forms this
+// product gets the same bits (no contraction left to the compiler's choice).
+__device__ __forceinline__ float2 c_conj_mul(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
 // multiply by -i (forward quarter turn) / +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 c_quarter(float2 v) {

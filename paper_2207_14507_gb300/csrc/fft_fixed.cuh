@@ -132,10 +132,13 @@ constexpr TwTab<R, NS> make_twtab() {
 template <int R, int NS>
 __device__ constexpr TwTab<R, NS> kStageTw = make_twtab<R, NS>();
 
+// v * w (forward) or v * conj(w) (INV), w = (wx, wy), with the rounding fixed
+// (one product rounded on its own plus one fused multiply-add per component)
+// so that every kernel running a stage gets the same bits.
 template <bool INV>
 __device__ __forceinline__ float2 tw_mul(float2 v, float wx, float wy) {
-  return INV ? make_float2(v.x * wx + v.y * wy, v.y * wx - v.x * wy)
-             : make_float2(v.x * wx - v.y * wy, v.x * wy + v.y * wx);
+  return INV ? make_float2(__fmaf_rn(v.x, wx, __fmul_rn(v.y, wy)), __fmaf_rn(v.y, wx, -__fmul_rn(v.x, wy)))
+             : make_float2(__fmaf_rn(v.x, wx, -__fmul_rn(v.y, wy)), __fmaf_rn(v.x, wy, __fmul_rn(v.y, wx)));
 }
 
 // v[n][r] *= w_{Ns*R}^{r*k} (conjugate for INV) for the NV transforms of one

@@ -93,7 +93,8 @@ void launch_col(const PassArgs& a, int mode, float2* out_f32, void* out_f16, con
                 cudaStream_t s, LaunchCounter& lc);
 void launch_row_inverse(const PassArgs& a, float* c_out, cudaStream_t s, LaunchCounter& lc);
 void launch_finalize(const PassArgs& a, cudaStream_t s, LaunchCounter& lc);
-void launch_argmax(const CandResult* res, const WorkItem* items, const int* group_start, int ngroups,
+// groups as SearchCall describes them (share = 1: contiguous)
+void launch_argmax(const CandResult* res, const WorkItem* items, const int* group_start, int ngroups, int share,
                    prnu_result* out, const float* scale, int H, int W, cudaStream_t s, LaunchCounter& lc);
 void launch_scatter_all(const CandResult* res, int nitems, int cmax, double* all, cudaStream_t s,
                         LaunchCounter& lc);
@@ -168,8 +169,9 @@ void launch_fp_estimate_divide(const double* num, const double* den, float* K, s
                                LaunchCounter& lc);
 // dense [F][H][W] residuals -> the zero-bordered layout the compile-time-planned
 // kernels read (row pitch W + 3, pixel (0, 0) at W + 4, (H + 3)(W + 3) per frame)
+// layout (half storage only): 0 single elements, 1 pairs (kF16P/kBF16P)
 void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc,
-                       bool pairs = false);
+                       int layout = 0);
 inline ResidLayout dense_layout(int H, int W) { return ResidLayout{W, (size_t)H * W, 0}; }
 inline ResidLayout padded_layout(int H, int W) {
   return ResidLayout{W + 3, (size_t)(H + 3) * (W + 3), (size_t)(W + 3) + 1};
@@ -208,6 +210,7 @@ struct Tuning {
   int variant = 0;    // compile-time-planned column variant; -1 = generic kernels only
   int persistent = 0; // compile-time-planned shapes: one persistent launch per call instead of waves
   int streams = 1;    // compile-time-planned shapes: waves alternate over 1 or 2 streams
+  int share = 1;      // compile-time-planned shapes, waves: fingerprints of one (frame, node) share the forward pass
 };
 
 }  // namespace prnu
@@ -256,11 +259,23 @@ struct SearchCall {
   int F, H, W;
   std::vector<std::shared_ptr<Fingerprint>> fps;
   std::vector<WorkItem> items;
-  std::vector<int> group_start;   // [F*P + 1]
+  // items of group g (= frame * P + fingerprint) are first + k * share for
+  // k < count, with f = g / share, first = group_start[f] + g % share and
+  // count = (group_start[f + 1] - group_start[f]) / share: share = 1, the
+  // groups' items are contiguous ([F*P + 1] starts); share = P, the items
+  // are ordered (frame, node, fingerprint) ([F + 1] starts) and every P
+  // consecutive items form one forward unit
+  std::vector<int> group_start;
+  int share = 1;
   int cmax;
   bool prepadded = false;         // resid is FP32 in padded_layout already (zero border included)
 };
-void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call);
+// unit_major: order (frame, node, fingerprint) with call.share = P, else
+// (frame, fingerprint, node) with call.share = 1
+void build_items(const prnu_grid& g, const prnu_window* windows, int F, int P, SearchCall& call,
+                 bool unit_major = false);
+// whether eis_grid_search-style calls of P fingerprints on H x W share the forward pass
+bool share_forward(prnu_ctx* c, int H, int W, int P, bool naive);
 void validate_shape(int H, int W);
 // enqueue: results into d_out (device prnu_result [F*P]); optional d_all
 void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, double* d_all, bool naive,

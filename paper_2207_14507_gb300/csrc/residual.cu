@@ -457,11 +457,11 @@ void launch_fp_estimate_divide(const double* num, const double* den, float* K, s
 }
 
 void launch_pad_frames(const void* in, int dtype, int F, int H, int W, void* out, cudaStream_t s, LaunchCounter& lc,
-                       bool pairs) {
+                       int layout) {
   if (F == 0) return;
   ProfScope ps(lc, kKindResidual, s);
   const dim3 b(256), g((W + 3 + 255) / 256, H + 3, F);
-  if (pairs && dtype != kF32)
+  if (layout == 1 && dtype != kF32)
     k_pad_pairs<<<g, b, 0, s>>>(reinterpret_cast<const uint16_t*>(in), H, W, reinterpret_cast<uint32_t*>(out));
   else if (dtype == kF32)
     k_pad_frames<float><<<g, b, 0, s>>>(reinterpret_cast<const float*>(in), H, W, reinterpret_cast<float*>(out));

@@ -18,6 +18,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "search_common.cuh"
 
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(512) k_col(PassArgs a, int mode, float2* __res
       const int i = e >> lg, col = c0 + (e & (NC - 1));
       if (col == 0 || col >= Wh) continue;
       const float2 s = load_spec(fp.spec, fp.dtype, (size_t)i * Wh + col);
-      buf[e] = c_mul(c_conj(buf[e]), s);
+      buf[e] = c_conj_mul(buf[e], s);
     }
     if (c0 == 0) {
       // packed column 0 = DC column + i * Nyquist column of both spectra:
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(512) k_col(PassArgs a, int mode, float2* __res
         const float2 B = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
         const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
         const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
-        const float2 p1 = c_mul(c_conj(A), Ka), p2 = c_mul(c_conj(B), Kb);
+        const float2 p1 = c_conj_mul(A, Ka), p2 = c_conj_mul(B, Kb);
         const float2 q1 = c_mulc(A, Ka), q2 = c_mulc(B, Kb);
         buf[i << lg] = make_float2(p1.x - p2.y, p1.y + p2.x);
         buf[im << lg] = make_float2(q1.x - q2.y, q1.y + q2.x);
@@ -211,25 +213,28 @@ __global__ void __launch_bounds__(512) k_finalize(PassArgs a) {
   finalize_body(a, blockIdx.x, blockIdx.x, smem);
 }
 
-// Best candidate of each (frame, fingerprint) group; items of a group are
-// contiguous and in ascending candidate order.  One warp per group.
+// Best candidate of each (frame, fingerprint) group g: its items are
+// first + k*share (k < count) with first = gstart[g / share] + g % share and
+// count = (gstart[g / share + 1] - gstart[g / share]) / share, in ascending
+// candidate order (share = 1: contiguous groups).  One warp per group.
 __global__ void k_argmax(const CandResult* __restrict__ res, const WorkItem* __restrict__ items,
-                         const int* __restrict__ gstart, int ngroups, prnu_result* __restrict__ out,
+                         const int* __restrict__ gstart, int ngroups, int share, prnu_result* __restrict__ out,
                          int H, int W) {
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (g >= ngroups) return;
-  const int b = gstart[g], e = gstart[g + 1];
+  const int f = g / share;
+  const int b = gstart[f] + (g - f * share), n = (gstart[f + 1] - gstart[f]) / share;
   double bv = -INFINITY;
   int bi = INT_MAX;
-  for (int k = b + lane; k < e; k += 32) {
-    const double v = res[k].pce;
-    better_d(bv, bi, v, k);
+  for (int k = lane; k < n; k += 32) {
+    const int i = b + k * share;
+    better_d(bv, bi, res[i].pce, i);
   }
   warp_maxarg_d(bv, bi);
   if (lane == 0) {
     prnu_result r;
-    if (bi == INT_MAX || e == b) {
+    if (bi == INT_MAX || n == 0) {
       r.lam = 0.f; r.th_deg = 0.f; r.dy = 0; r.dx = 0; r.pce = 0.0; r.peak = 0.f; r.cand_idx = -1;
     } else {
       const CandResult c = res[bi];
@@ -436,12 +441,13 @@ void launch_finalize(const PassArgs& a, cudaStream_t s, LaunchCounter& lc) {
   lc.n++;
 }
 
-void launch_argmax(const CandResult* res, const WorkItem* items, const int* group_start, int ngroups,
+void launch_argmax(const CandResult* res, const WorkItem* items, const int* group_start, int ngroups, int share,
                    prnu_result* out, const float* /*scale*/, int H, int W, cudaStream_t s, LaunchCounter& lc) {
   if (ngroups <= 0) return;
   const int warps = 8;
   ProfScope ps(lc, kKindArgmax, s);
-  k_argmax<<<(ngroups + warps - 1) / warps, warps * 32, 0, s>>>(res, items, group_start, ngroups, out, H, W);
+  k_argmax<<<(ngroups + warps - 1) / warps, warps * 32, 0, s>>>(res, items, group_start, ngroups,
+                                                                std::max(share, 1), out, H, W);
   PRNU_LAUNCH_CHECK();
   lc.n++;
 }

@@ -235,10 +235,19 @@ constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait b
 // the last forward stage has taken its inputs (the packed column-0 scratch then
 // sits after the strip).  A TMA wait that runs out raises a.err and abandons
 // the candidate.
-template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0>
+// PART splits the pass for forward units (candidates that share a frame and
+// a grid node): PART 1 runs the forward column FFT only and stores its
+// output, in natural order, back to slot ws; PART 2 loads that output from
+// slot src_ws, where each thread finds the values the last forward stage
+// leaves in its registers, and runs the product and the inverse FFT into slot
+// ws.  PART 1 then PART 2 compute bit for bit what PART 0 (the whole pass)
+// computes.  PART 1 and 2 need TMA (MODE >= 1); PART 2 takes MODE 2.
+template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0, int PART = 0>
 __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
-                                         const CUtensorMap* map = nullptr) {
-  constexpr bool TMA = MODE >= 1, FPT = MODE == 2;
+                                         const CUtensorMap* map = nullptr, int src_ws = -1) {
+  constexpr bool TMA = MODE >= 1, FPT = MODE == 2 && PART != 1;
+  static_assert(PART == 0 || TMA, "the split column pass moves its strips by TMA");
+  if (src_ws < 0) src_ws = ws;
   constexpr int H = SP::N, Wh = W / 2;
   using IS = typename SP::Rev;
   using M = ColMap<NC, T>;
@@ -265,7 +274,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     if (t == 0) {
       mbar_expect_tx(&s_bar, H * NC * 8 + (a.stall ? 16 : 0));   // the test hook waits for bytes that never come
 #pragma unroll 1
-      for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, ws * H + b * BR, &s_bar);
+      for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, src_ws * H + b * BR, &s_bar);
     }
     const bool ok = mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);
     if (__syncthreads_or(!ok)) {
@@ -276,7 +285,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
       __syncthreads();
       return;
     }
-    ColStages<SP, 0, SP::S - 1, T, NC, false>::run(sm4, t);
+    if constexpr (PART != 2) ColStages<SP, 0, SP::S - 1, T, NC, false>::run(sm4, t);
   } else {  // forward stage 0 from global memory
     using G = Stg<SP, 0>;
     constexpr int IT = (G::NB + TJ - 1) / TJ;
@@ -328,13 +337,36 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
         tma_load_2d(reinterpret_cast<char*>(sm) + (size_t)b * fbr * NC * es, fm, 2 * c0, b * fbr, &s_bar);
     }
   }
+  if constexpr (PART != 2) {   // PART 2: the strip held the outputs of this stage
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int j = j0 + it * TJ;
-    if (FL::NB % TJ != 0 && j >= FL::NB) continue;
-    twiddle_tab<FL::R, FL::NS, false, 2>(v[it], j);
-    Dft<FL::R, false>::run(v[it][0]);
-    Dft<FL::R, false>::run(v[it][1]);
+    for (int it = 0; it < IT; ++it) {
+      const int j = j0 + it * TJ;
+      if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+      twiddle_tab<FL::R, FL::NS, false, 2>(v[it], j);
+      Dft<FL::R, false>::run(v[it][0]);
+      Dft<FL::R, false>::run(v[it][1]);
+    }
+  }
+  if constexpr (PART == 1) {
+    // outputs i = j + r*NS go back where the stage took its inputs (NB == NS),
+    // then the strip leaves for slot ws
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int j = j0 + it * TJ;
+      if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+      float4* dst = sm4 + j * NP + cp;
+#pragma unroll
+      for (int r = 0; r < FL::R; ++r) dst[r * FL::NS * NP] = join2(v[it][0][r], v[it][1][r]);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll 1
+      for (int b = 0; b < H / BR; ++b) tma_store_2d(map, 2 * c0, ws * H + b * BR, sm + b * BR * NC);
+      bulk_commit();
+      bulk_wait_read();
+    }
+    return;
   }
   if constexpr (FPT) {
     if (fp_tma) {
@@ -386,7 +418,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
           const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
           const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
           const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
-          const float2 p1 = c_mul(c_conj(Aa), Ka), p2 = c_mul(c_conj(Bb), Kb);
+          const float2 p1 = c_conj_mul(Aa, Ka), p2 = c_conj_mul(Bb, Kb);
           v[it][0][r] = make_float2(p1.x - p2.y, p1.y + p2.x);
         }
       }
@@ -411,16 +443,16 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
           s0 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
           s1 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         }
-        if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), s0);
-        v[it][1][r] = c_mul(c_conj(v[it][1][r]), s1);
+        if (!col0_done) v[it][0][r] = c_conj_mul(v[it][0][r], s0);
+        v[it][1][r] = c_conj_mul(v[it][1][r], s1);
       }
     } else {
       float2 sf[2][FL::R];
       load_fp_pair<FL::R, FL::NS, Wh>(fp, j, col0, sf);
 #pragma unroll
       for (int r = 0; r < FL::R; ++r) {
-        if (!col0_done) v[it][0][r] = c_mul(c_conj(v[it][0][r]), sf[0][r]);
-        v[it][1][r] = c_mul(c_conj(v[it][1][r]), sf[1][r]);
+        if (!col0_done) v[it][0][r] = c_conj_mul(v[it][0][r], sf[0][r]);
+        v[it][1][r] = c_conj_mul(v[it][1][r], sf[1][r]);
       }
     }
   }
@@ -547,19 +579,28 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
   const float2* pa = a.spec + ((size_t)ws * H + 2 * pair) * Wh;
   float2 v[GL::IT][GL::R];
   row_inverse_fft<SP, T, CG>(pa, pa + Wh, A, t, v);
-  // per thread: max, first arg-max and energy of each row over its outputs
+  // per thread: max, first arg-max and energy of each row over its outputs,
+  // visited in increasing x (x = t + it*T + r*NS with t + it*T < NS), so a
+  // strictly larger value is the only one that moves the arg-max: the first
+  // maximum is kept without comparing indices
   float ma = -INFINITY, mb = -INFINITY;
   int ia = INT_MAX, ib = INT_MAX;
   float sa = 0.f, sb = 0.f;
 #pragma unroll
-  for (int it = 0; it < GL::IT; ++it) {
-    if (!GL::valid(t, it)) break;
+  for (int r = 0; r < GL::R; ++r) {
 #pragma unroll
-    for (int r = 0; r < GL::R; ++r) {
+    for (int it = 0; it < GL::IT; ++it) {
+      if (!GL::valid(t, it)) continue;
       const int x = t + it * T + r * GL::NS;
       const float2 u = v[it][r];
-      better_f(ma, ia, u.x, x);
-      better_f(mb, ib, u.y, x);
+      if (u.x > ma) {
+        ma = u.x;
+        ia = x;
+      }
+      if (u.y > mb) {
+        mb = u.y;
+        ib = x;
+      }
       sa = fmaf(u.x, u.x, sa);
       sb = fmaf(u.y, u.y, sb);
     }
@@ -583,11 +624,15 @@ __device__ __forceinline__ void row_inverse_body(const PassArgs& a, int ws, int 
 
 // ---------------------------------------------------------------- wave kernels
 
+// blockIdx.y = candidate slot, or with forward units the unit u, whose row
+// spectrum goes to slot a.nitems + u
 template <int DT, class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
-  row_forward_body<DT, SP, T, PPB>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4),
-                                   threadIdx.x);
+  const bool units = a.units || a.share > 1;
+  const int u = blockIdx.y;
+  row_forward_body<DT, SP, T, PPB>(a, units ? unit_first(a, u) : u, units ? a.nitems + u : u, blockIdx.x,
+                                   reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
 
 template <class SP, int W, int NC, int T, int MINB>
@@ -601,6 +646,25 @@ __global__ void __launch_bounds__(T, MINB) k_col_tma_fx(PassArgs a, const __grid
   extern __shared__ __align__(1024) float4 smem4t[];
   col_body<SP, W, NC, T, false, MODE>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4t),
                                       &map);
+}
+
+// Forward units (see col_body PART): the forward column FFT of unit
+// blockIdx.y, in place in its slot a.nitems + u; then, per candidate slot
+// blockIdx.y, the product with its fingerprint and the inverse FFT from its
+// unit's slot into its own.
+template <class SP, int W, int NC, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_col_fwd_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
+  extern __shared__ __align__(1024) float4 smem4f[];
+  const int u = blockIdx.y;
+  col_body<SP, W, NC, T, false, 1, 1>(a, unit_first(a, u), a.nitems + u, blockIdx.x,
+                                      reinterpret_cast<float2*>(smem4f), &map);
+}
+template <class SP, int W, int NC, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_col_inv_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
+  extern __shared__ __align__(1024) float4 smem4i[];
+  const int s = blockIdx.y;
+  col_body<SP, W, NC, T, false, 2, 2>(a, s, s, blockIdx.x, reinterpret_cast<float2*>(smem4i), &map,
+                                      a.nitems + unit_of_slot(a, s));
 }
 
 template <class SP, int T, int PPB>
@@ -865,6 +929,19 @@ struct ShapeDef {
     return FixedCol{NC, CT, MODE == 2 ? col_fx_smem_fpt(H, NC) : col_fx_smem(H, NC), fn, MODE != 0,
                     tma_box_rows(H, NC)};
   }
+  // the split column pass of forward units (NC columns, CT threads, MINB blocks)
+  template <int NC, int CT, int MINB>
+  static FixedCol col_fwd() {
+    void* fn = (void*)k_col_fwd_fx<CS, W, NC, CT, MINB>;
+    allow_max_dynamic_smem(fn);
+    return FixedCol{NC, CT, col_fx_smem(H, NC), fn, true, tma_box_rows(H, NC)};
+  }
+  template <int NC, int CT, int MINB>
+  static FixedCol col_inv() {
+    void* fn = (void*)k_col_inv_fx<CS, W, NC, CT, MINB>;
+    allow_max_dynamic_smem(fn);
+    return FixedCol{NC, CT, col_fx_smem_fpt(H, NC), fn, true, tma_box_rows(H, NC)};
+  }
   template <int PPB>
   static FixedRow row() {
     FixedRow r{};
@@ -913,12 +990,15 @@ struct ShapeDef {
     }
     return f;
   }
-  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, FixedPersist ps) {
+  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, std::pair<FixedCol, FixedCol> split,
+                         FixedPersist ps) {
     FixedShape s{};
     s.W = W;
     s.H = H;
     s.rows = std::move(rows);
     s.cols = std::move(cols);
+    s.col_fwd = split.first;
+    s.col_inv = split.second;
     s.persist = ps;
     return s;
   }
@@ -931,25 +1011,25 @@ std::vector<FixedShape> build_registry() {
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(), D::col<4, 240, 3, 0>(),
                          D::col<8, 480, 1, 1>()},
-                        D::persist<192, 2, 4>()));
+                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>()}, D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(), D::col<8, 360, 2, 0>(),
                          D::col<4, 180, 4, 2>()},
-                        D::persist<160, 2, 4>()));
+                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>()}, D::persist<160, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(), D::col<4, 360, 2, 0>()},
-                        D::persist<256, 2, 4>()));
+                        {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>()}, D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
     v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>()},
-                        D::persist<32, 8, 16>()));
+                        {D::col_fwd<16, 128, 4>(), D::col_inv<16, 128, 4>()}, D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
   return v;
@@ -1033,18 +1113,31 @@ bool encode_fp_tmaps(const void* spec, int dtype, int H, int W, void* out) {
 }
 
 void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant, cudaStream_t s, LaunchCounter& lc) {
-  const FixedCol& fc = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
+  // forward units (several candidates of one frame and node): the row pass
+  // and the forward column FFT per unit, into slots a.nitems + u; the product
+  // and the inverse column FFT per candidate
+  const bool units = a.units != nullptr || a.share > 1;
+  const int nunits = units ? a.nunits : a.nitems;
+  const FixedCol& fc = units ? fs.col_inv : fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
   const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};
   alignas(64) CUtensorMap map;
-  if (fc.tma && !encode_spec_map(&map, a.spec, a.W, (long long)a.nitems * a.H, fc.nc, fc.br))
+  const long long rows = (long long)(a.nitems + (units ? nunits : 0)) * a.H;
+  if (fc.tma && !encode_spec_map(&map, a.spec, a.W, rows, fc.nc, fc.br))
     throw Error{PRNU_ECUDA, "cannot describe the workspace spectra for TMA (cuTensorMapEncodeTiled)"};
   void* targs[] = {const_cast<PassArgs*>(&a), &map};
   {
     ProfScope ps(lc, kKindRowForward, s);
-    dim3 g((a.H / 2) / fr.ppb, a.nitems), b(fr.threads * fr.ppb);
+    dim3 g((a.H / 2) / fr.ppb, nunits), b(fr.threads * fr.ppb);
     PRNU_CUDA_TRY(cudaLaunchKernel(fr.fwd[a.rdtype], g, b, args, fr.smem, s));
+  }
+  if (units) {   // the forward half, per unit (same strip shape as the inverse half: one tensor map)
+    ProfScope ps(lc, kKindColumn, s);
+    const FixedCol& ff = fs.col_fwd;
+    dim3 g((Wh + ff.nc - 1) / ff.nc, nunits), b(ff.threads);
+    PRNU_CUDA_TRY(cudaLaunchKernel(ff.fn, g, b, targs, ff.smem, s));
+    lc.n += 1;
   }
   {
     ProfScope ps(lc, kKindColumn, s);

@@ -25,7 +25,7 @@ struct FixedRow {
   int threads;               // per row pair, forward kernel
   int threads_inv;           // per row pair, inverse kernel
   size_t smem;
-  void* fwd[5];              // by residual storage type (kF32, kF16, kBF16, kF16P, kBF16P)
+  void* fwd[kNumStoreLayouts];   // by residual storage type (kF32, kF16, kBF16, kF16P, kBF16P)
   void* inv;
   void* fin;                 // per-candidate PCE (one block per candidate)
   int fin_threads;
@@ -59,6 +59,7 @@ struct FixedShape {
   int W, H;
   std::vector<FixedRow> rows;
   std::vector<FixedCol> cols;
+  FixedCol col_fwd, col_inv; // the column pass split for forward units (k_col_fwd_fx, k_col_inv_fx)
   FixedPersist persist;
   // the row kernels with `ppb` pairs per block, else the first variant
   const FixedRow& row_for(int ppb) const {

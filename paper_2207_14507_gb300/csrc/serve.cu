@@ -34,6 +34,9 @@ constexpr int kMaxFrameSlots = 8192;
 constexpr int kMaxFpSlots = 1024;
 constexpr int kWaveSlots = 8;
 constexpr int kMaxWave = 256;
+// per wave: item pointers [kMaxWave], result pointers [kMaxWave], then the
+// forward units' first slots [kMaxWave + 1] and each slot's unit [kMaxWave] (int)
+constexpr size_t kWaveTabBytes = sizeof(void*) * 2 * kMaxWave + sizeof(int) * (2 * kMaxWave + 1);
 constexpr size_t kMaxQueued = 4096;
 constexpr int kArenaBlocks = 256;
 constexpr size_t kArenaBlock = 64 * 1024;   // results of up to 2048 (frame, fingerprint) pairs
@@ -150,8 +153,8 @@ struct Server::Impl {
     d_fpdesc = reinterpret_cast<FpDesc*>(ctx_alloc(ctx, sizeof(FpDesc) * kMaxFpSlots));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&arena, kArenaBlock * kArenaBlocks, cudaHostAllocDefault));
     for (auto& w : waves) {
-      PRNU_CUDA_TRY(cudaHostAlloc((void**)&w.h_tab, sizeof(void*) * 2 * kMaxWave, cudaHostAllocDefault));
-      w.d_tab = reinterpret_cast<void**>(ctx_alloc(ctx, sizeof(void*) * 2 * kMaxWave));
+      PRNU_CUDA_TRY(cudaHostAlloc((void**)&w.h_tab, kWaveTabBytes, cudaHostAllocDefault));
+      w.d_tab = reinterpret_cast<void**>(ctx_alloc(ctx, kWaveTabBytes));
       PRNU_CUDA_TRY(cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming));
       PRNU_CUDA_TRY(cudaEventRecord(w.ev, s_comp));
     }
@@ -171,7 +174,7 @@ struct Server::Impl {
     cudaStreamSynchronize(s_comp);
     for (auto& w : waves) {
       cudaFreeHost(w.h_tab);
-      ctx_free(ctx, w.d_tab, sizeof(void*) * 2 * kMaxWave);
+      ctx_free(ctx, w.d_tab, kWaveTabBytes);
       cudaEventDestroy(w.ev);
     }
     ctx_free(ctx, d_frame_ptrs, sizeof(void*) * kMaxFrameSlots);
@@ -200,8 +203,10 @@ struct Server::Impl {
     return b;
   }
 
+  // spectra: the wave's candidates, then one slot per forward unit (at most
+  // one per candidate); row statistics: the candidates
   size_t workspace_bytes(int H, int W, int wave) const {
-    return (size_t)wave * H * (W / 2) * sizeof(float2) + (size_t)wave * H * sizeof(RowStat);
+    return 2 * (size_t)wave * H * (W / 2) * sizeof(float2) + (size_t)wave * H * sizeof(RowStat);
   }
 
   // ---------------------------------------------------------------- submit / poll (user threads)
@@ -232,6 +237,7 @@ struct Server::Impl {
       q->windows.assign(pq->windows, pq->windows + pq->F);
       q->has_windows = true;
     }
+    bool unit_major = false;
     {
       std::lock_guard<std::recursive_mutex> lk(ctx->mu);
       for (int p = 0; p < pq->P; ++p) {
@@ -242,8 +248,11 @@ struct Server::Impl {
         q->fps.push_back(it->second);
       }
       q->tn = tuning_for(ctx, q->H, q->W);
+      // the fingerprints of one (frame, node) share its forward pass; a unit
+      // (P items) never spans two waves
+      unit_major = share_forward(ctx, q->H, q->W, q->P, false) && q->P <= kMaxWave;
     }
-    build_items(q->grid, q->has_windows ? q->windows.data() : nullptr, q->F, q->P, q->call);
+    build_items(q->grid, q->has_windows ? q->windows.data() : nullptr, q->F, q->P, q->call, unit_major);
     q->call.F = q->F;
     q->call.H = q->H;
     q->call.W = q->W;
@@ -345,7 +354,7 @@ struct Server::Impl {
   }
 
   void ensure_workspace(int H, int W, int wave) {
-    const size_t sb = (size_t)wave * H * (W / 2) * sizeof(float2);
+    const size_t sb = 2 * (size_t)wave * H * (W / 2) * sizeof(float2);
     const size_t tb = (size_t)wave * H * sizeof(RowStat);
     if (sb <= ws_spec_bytes && tb <= ws_stats_bytes) return;
     PRNU_CUDA_TRY(cudaStreamSynchronize(s_comp));
@@ -486,28 +495,40 @@ struct Server::Impl {
     ensure_workspace(H, W, wave);
     void** hi = slot.h_tab;
     void** hr = slot.h_tab + kMaxWave;
-    int count = 0;
+    int* hu = reinterpret_cast<int*>(slot.h_tab + 2 * kMaxWave);   // forward units' first slots
+    int* hs = hu + kMaxWave + 1;                                      // unit of each slot
+    int count = 0, nunits = 0;
+    bool grouped = false;
     std::vector<Query*> finished;
     for (auto& qp : best->second) {
       if (count >= wave) break;
       Query& q = *qp;
       const int n = (int)q.call.items.size();
       if (q.failed || q.next >= n) continue;
+      // whole forward units only: a unit (the fingerprints of one frame and
+      // node, share items) never spans two waves
+      const int S = std::max(q.call.share, 1);
+      const int take = std::min(wave - count, n - q.next) / S * S;
+      if (take == 0) break;
       if (!q.ingest_waited) {
         PRNU_CUDA_TRY(cudaStreamWaitEvent(s_comp, q.ingest, 0));
         q.ingest_waited = true;
       }
-      const int take = std::min(wave - count, n - q.next);
       for (int k = 0; k < take; ++k) {
         hi[count + k] = q.d_items + q.next + k;
         hr[count + k] = q.d_results + q.next + k;
       }
+      for (int u = 0; u < take / S; ++u) {
+        for (int k = 0; k < S; ++k) hs[count + u * S + k] = nunits;
+        hu[nunits++] = count + u * S;
+      }
+      grouped = grouped || S > 1;
       count += take;
       q.next += take;
       if (q.next == n) finished.push_back(&q);
     }
-    PRNU_CUDA_TRY(cudaMemcpyAsync(slot.d_tab, slot.h_tab, sizeof(void*) * 2 * kMaxWave, cudaMemcpyHostToDevice,
-                                  s_comp));
+    hu[nunits] = count;
+    PRNU_CUDA_TRY(cudaMemcpyAsync(slot.d_tab, slot.h_tab, kWaveTabBytes, cudaMemcpyHostToDevice, s_comp));
     PassArgs a{};
     a.err = ctx->d_err;
     a.rdtype = key.dtype;
@@ -531,6 +552,11 @@ struct Server::Impl {
     a.item_ptrs = reinterpret_cast<const WorkItem* const*>(slot.d_tab);
     a.result_ptrs = reinterpret_cast<CandResult* const*>(slot.d_tab + kMaxWave);
     a.frame_ptrs = d_frame_ptrs;
+    // forward units of several items: the unit table; else one item per unit
+    a.units = grouped ? reinterpret_cast<const int*>(slot.d_tab + 2 * kMaxWave) : nullptr;
+    a.unit_of = grouped ? a.units + kMaxWave + 1 : nullptr;
+    a.nunits = grouped ? nunits : count;
+    a.share = 1;
     const FixedShape* fs = tn.variant >= 0 ? find_fixed(H, W) : nullptr;
     if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
     if (fs) {
@@ -545,8 +571,8 @@ struct Server::Impl {
     st.server_launches += 4;
     st.candidates_done += count;
     for (Query* q : finished) {
-      launch_argmax(q->d_results, q->d_items, q->d_groups, q->F * q->P, q->d_out, nullptr, q->H, q->W, s_comp,
-                    ctx->launches);
+      launch_argmax(q->d_results, q->d_items, q->d_groups, q->F * q->P, q->call.share, q->d_out, nullptr, q->H, q->W,
+                    s_comp, ctx->launches);
       PRNU_CUDA_TRY(cudaMemcpyAsync(q->h_out, q->d_out, sizeof(prnu_result) * (size_t)q->F * q->P,
                                     cudaMemcpyDeviceToHost, s_comp));
       PRNU_CUDA_TRY(cudaLaunchHostFunc(s_comp, on_done, q));

@@ -254,18 +254,20 @@ class ServingQuery:
     arrival_s: float
     H: int
     W: int
-    frames: np.ndarray        # uint8 [F, H, W]
+    frames: np.ndarray | None  # uint8 [F, H, W]; None when the stream was made with materialise=False
     fp_ids: list              # fingerprint-bank ids to test, per resolution
     match: int                # bank id that generated the frames, or -1
     windows: np.ndarray       # int32 [F, 4]
     planted: np.ndarray
+    pool: tuple = ()          # (H, W, source): the frame pool the frames come from
+    pool_index: np.ndarray | None = None   # int [F]: frame f is pools[pool][pool_index[f]]
 
 
 def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
                       resolutions=((720, 1280), (1080, 1920), (2160, 3840)),
                       frames_range=(8, 64), fps_range=(1, 16), bank_size: int = 16,
                       pool_frames: int = 64, grid: Grid = GRID_FULL, config: int = 5,
-                      match_sources: int | None = None):
+                      match_sources: int | None = None, materialise: bool = True):
     """Poisson query stream over per-resolution fingerprint banks and frame pools.
 
     To keep generation cheap, each resolution gets a pool of `pool_frames`
@@ -273,6 +275,9 @@ def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
     (with `match_sources` set, only bank fingerprints 0..match_sources-1 can be
     the match); a query takes a contiguous run of a pool (wrapping around).
     Returns (queries, banks) where banks[(H, W)] is a list of float32 fingerprints.
+    With materialise=False the queries carry no frame arrays, only their pool
+    key and frame indices, and the return value is (queries, banks, pools)
+    with pools[key] = uint8 [pool_frames, H, W].
     """
     ra = rng_for(config, STREAM_ARRIVALS)
     t = 0.0
@@ -317,6 +322,9 @@ def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
         ks = ra.integers(2, 11, size=F)
         centres = pp[(idx - 1) % pool_frames, :2]
         windows = snap_windows(grid, centres, ks)
-        queries.append(ServingQuery(qid=q, arrival_s=t, H=H, W=W, frames=pf[idx], fp_ids=fp_ids,
-                                    match=match, windows=windows, planted=pp[idx]))
+        queries.append(ServingQuery(qid=q, arrival_s=t, H=H, W=W, frames=pf[idx] if materialise else None,
+                                    fp_ids=fp_ids, match=match, windows=windows, planted=pp[idx], pool=key,
+                                    pool_index=idx))
+    if not materialise:
+        return queries, banks, {k: v[0] for k, v in pools.items()}
     return queries, banks
