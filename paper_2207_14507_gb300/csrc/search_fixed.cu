@@ -227,86 +227,33 @@ __host__ __device__ constexpr int fp_tmap_index(int NC) { return NC == 2 ? 0 : N
 __host__ __device__ constexpr size_t col_fx_smem_fpt(int H, int nc) { return (size_t)H * (nc + 1) * sizeof(float2); }
 constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait before giving up
 
-// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
-// MODE 0: every thread loads and stores its own elements.  MODE >= 1: the
-// strip comes into shared memory by TMA tile copies through `map` (the
-// workspace spectra as a [slots*H][W] float tensor) and leaves the same way.
-// MODE 2: the fingerprint strip too comes by TMA, into the strip buffer once
-// the last forward stage has taken its inputs (the packed column-0 scratch then
-// sits after the strip).  A TMA wait that runs out raises a.err and abandons
-// the candidate.
-// PART splits the pass for forward units (candidates that share a frame and
-// a grid node): PART 1 runs the forward column FFT only and stores its
-// output, in natural order, back to slot ws; PART 2 loads that output from
-// slot src_ws, where each thread finds the values the last forward stage
-// leaves in its registers, and runs the product and the inverse FFT into slot
-// ws.  PART 1 then PART 2 compute bit for bit what PART 0 (the whole pass)
-// computes.  PART 1 and 2 need TMA (MODE >= 1); PART 2 takes MODE 2.
-template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0, int PART = 0>
-__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
-                                         const CUtensorMap* map = nullptr, int src_ws = -1) {
+// The column pass from the last forward stage on, for the strip of NC
+// columns from c0 whose forward stages have run in the strip buffer sm (PART
+// 2: which holds the last forward stage's outputs): the last forward stage,
+// the product with the fingerprint fp, the inverse stages; the last inverse
+// stage leaves the strip in sm (MODE >= 1) or in Z (MODE 0).  PART 1 stops
+// after the last forward stage and leaves its outputs in sm, in natural
+// order.  With MODE 2 the fingerprint strip comes by TMA into sm once every
+// thread holds its inputs (fp_tma_ok: the caller allows it), completing the
+// mbarrier bar (its completions so far: bar_uses, advanced here when the copy
+// is made, the same on every thread); X0 is the packed column-0 scratch (H
+// float2 that the fingerprint strip does not cover).  hook() runs on every
+// thread right after the barrier that follows the loads of the last forward
+// stage (the strip buffer's old contents are then no longer needed).
+// t = threadIdx.x.  Returns false if the fingerprint copy did not land in
+// time (a.err raised).
+template <class SP, int W, int NC, int T, int MODE, int PART, class Hook>
+__device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, int c0, float2* sm, float2* Z,
+                                         uint64_t* bar, int& bar_uses, bool fp_tma_ok, float2* X0, Hook&& hook,
+                                         int t) {
   constexpr bool TMA = MODE >= 1, FPT = MODE == 2 && PART != 1;
-  static_assert(PART == 0 || TMA, "the split column pass moves its strips by TMA");
-  if (src_ws < 0) src_ws = ws;
   constexpr int H = SP::N, Wh = W / 2;
   using IS = typename SP::Rev;
   using M = ColMap<NC, T>;
   constexpr int NP = M::NP, TJ = M::TJ;
-  static_assert(Wh % NC == 0, "strips tile the half spectrum");
-  const int t = threadIdx.x;
-  const int c0 = bx * NC;
   const int cp = t % NP, j0 = t / NP;
   const int col0 = c0 + 2 * cp;
-  float2* Z = a.spec + (size_t)ws * H * Wh;
   float4* sm4 = reinterpret_cast<float4*>(sm);
-  const WorkItem wi = item_of(a, is);
-  const FpDesc fp = a.fps[wi.fp];
-
-  constexpr int BR = tma_box_rows(H, NC);
-  __shared__ uint64_t s_bar;
-  if constexpr (TMA) {
-    static_assert(BR > 0, "no TMA box for this strip");
-    if (t == 0) {
-      mbar_init(&s_bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (t == 0) {
-      mbar_expect_tx(&s_bar, H * NC * 8 + (a.stall ? 16 : 0));   // the test hook waits for bytes that never come
-#pragma unroll 1
-      for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, src_ws * H + b * BR, &s_bar);
-    }
-    const bool ok = mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);
-    if (__syncthreads_or(!ok)) {
-      if (t == 0) {
-        if (a.err) atomicExch(a.err, 1);
-        mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);   // let the copy land before the block leaves
-      }
-      __syncthreads();
-      return;
-    }
-    if constexpr (PART != 2) ColStages<SP, 0, SP::S - 1, T, NC, false>::run(sm4, t);
-  } else {  // forward stage 0 from global memory
-    using G = Stg<SP, 0>;
-    constexpr int IT = (G::NB + TJ - 1) / TJ;
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int j = j0 + it * TJ;
-      if (G::NB % TJ != 0 && j >= G::NB) continue;
-      float2 v[2][G::R];
-      const float4* src = reinterpret_cast<const float4*>(Z + (size_t)j * Wh + col0);
-#pragma unroll
-      for (int r = 0; r < G::R; ++r) split2(ld_spec4<CG>(src + (size_t)r * G::NB * (Wh / 2)), v[0][r], v[1][r]);
-      Dft<G::R, false>::run(v[0]);
-      Dft<G::R, false>::run(v[1]);
-      float4* dst = sm4 + j * G::R * NP + cp;
-#pragma unroll
-      for (int r = 0; r < G::R; ++r) dst[r * NP] = join2(v[0][r], v[1][r]);
-    }
-    __syncthreads();
-    ColStages<SP, 1, SP::S - 1, T, NC, false>::run(sm4, t);
-  }
-
   // last forward stage -> spectrum product -> first inverse stage, in registers
   using FL = Stg<SP, SP::S - 1>;
   using I0 = Stg<IS, 0>;
@@ -322,19 +269,20 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     for (int r = 0; r < FL::R; ++r) split2(src[r * FL::NB * NP], v[it][0][r], v[it][1][r]);
   }
   __syncthreads();
+  hook();
   // The fingerprint strip: by TMA into the strip buffer, which is free now
   // (every thread holds its inputs), else by per-thread loads.
-  const bool fp_tma = FPT && fp.tmaps != nullptr && NC * (fp.dtype == kF32 ? 8 : 4) >= 16;
+  const bool fp_tma = FPT && fp_tma_ok && fp.tmaps != nullptr && NC * (fp.dtype == kF32 ? 8 : 4) >= 16;
   if constexpr (FPT) {
     if (fp_tma && t == 0) {
       const CUtensorMap* fm = reinterpret_cast<const CUtensorMap*>(fp.tmaps) + fp_tmap_index(NC);
       const int es = fp.dtype == kF32 ? 8 : 4, fbr = tma_box_rows(H, NC, es);
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(fm))
                    : "memory");
-      mbar_expect_tx(&s_bar, H * NC * es);
+      mbar_expect_tx(bar, H * NC * es);
 #pragma unroll 1
       for (int b = 0; b < H / fbr; ++b)
-        tma_load_2d(reinterpret_cast<char*>(sm) + (size_t)b * fbr * NC * es, fm, 2 * c0, b * fbr, &s_bar);
+        tma_load_2d(reinterpret_cast<char*>(sm) + (size_t)b * fbr * NC * es, fm, 2 * c0, b * fbr, bar);
     }
   }
   if constexpr (PART != 2) {   // PART 2: the strip held the outputs of this stage
@@ -348,8 +296,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
     }
   }
   if constexpr (PART == 1) {
-    // outputs i = j + r*NS go back where the stage took its inputs (NB == NS),
-    // then the strip leaves for slot ws
+    // outputs i = j + r*NS go back where the stage took its inputs (NB == NS)
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
       const int j = j0 + it * TJ;
@@ -358,26 +305,20 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
 #pragma unroll
       for (int r = 0; r < FL::R; ++r) dst[r * FL::NS * NP] = join2(v[it][0][r], v[it][1][r]);
     }
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (t == 0) {
-#pragma unroll 1
-      for (int b = 0; b < H / BR; ++b) tma_store_2d(map, 2 * c0, ws * H + b * BR, sm + b * BR * NC);
-      bulk_commit();
-      bulk_wait_read();
-    }
-    return;
+    return true;
   }
   if constexpr (FPT) {
     if (fp_tma) {
-      const bool ok = mbar_wait_bounded(&s_bar, 1, kTmaWaitPolls);
+      const int ph = bar_uses & 1;
+      ++bar_uses;
+      const bool ok = mbar_wait_bounded(bar, ph, kTmaWaitPolls);
       if (__syncthreads_or(!ok)) {
         if (t == 0) {
           if (a.err) atomicExch(a.err, 1);
-          mbar_wait_bounded(&s_bar, 1, kTmaWaitPolls);
+          mbar_wait_bounded(bar, ph, kTmaWaitPolls);
         }
         __syncthreads();
-        return;
+        return false;
       }
     }
   }
@@ -392,7 +333,6 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   // thread holds bins i = j + r*NS of columns col0 and col0 + 1
   if (c0 == 0) {
     // packed column 0 (DC + i*Nyquist): the product needs bin H - i as well
-    float2* X0 = FPT ? sm + H * NC : sm;   // with MODE 2 the strip buffer holds the fingerprint
     if (cp == 0) {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
@@ -497,6 +437,94 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
       }
     }
   }
+  return true;
+}
+
+
+// Columns bx*NC .. bx*NC+NC-1 of candidate `is` in workspace slot `ws`.
+// MODE 0: every thread loads and stores its own elements.  MODE >= 1: the
+// strip comes into shared memory by TMA tile copies through `map` (the
+// workspace spectra as a [slots*H][W] float tensor) and leaves the same way.
+// MODE 2: the fingerprint strip too comes by TMA, into the strip buffer once
+// the last forward stage has taken its inputs (the packed column-0 scratch then
+// sits after the strip).  A TMA wait that runs out raises a.err and abandons
+// the candidate.
+// PART splits the pass for forward units (candidates that share a frame and
+// a grid node): PART 1 runs the forward column FFT only and stores its
+// output, in natural order, back to slot ws; PART 2 loads that output from
+// slot src_ws, where each thread finds the values the last forward stage
+// leaves in its registers, and runs the product and the inverse FFT into slot
+// ws.  PART 1 then PART 2 compute bit for bit what PART 0 (the whole pass)
+// computes.  PART 1 and 2 need TMA (MODE >= 1); PART 2 takes MODE 2.
+template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0, int PART = 0>
+__device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
+                                         const CUtensorMap* map = nullptr, int src_ws = -1) {
+  constexpr bool TMA = MODE >= 1, FPT = MODE == 2 && PART != 1;
+  static_assert(PART == 0 || TMA, "the split column pass moves its strips by TMA");
+  if (src_ws < 0) src_ws = ws;
+  constexpr int H = SP::N, Wh = W / 2;
+  using IS = typename SP::Rev;
+  using M = ColMap<NC, T>;
+  constexpr int NP = M::NP, TJ = M::TJ;
+  static_assert(Wh % NC == 0, "strips tile the half spectrum");
+  const int t = threadIdx.x;
+  const int c0 = bx * NC;
+  const int cp = t % NP, j0 = t / NP;
+  const int col0 = c0 + 2 * cp;
+  float2* Z = a.spec + (size_t)ws * H * Wh;
+  float4* sm4 = reinterpret_cast<float4*>(sm);
+  const WorkItem wi = item_of(a, is);
+  const FpDesc fp = a.fps[wi.fp];
+
+  constexpr int BR = tma_box_rows(H, NC);
+  __shared__ uint64_t s_bar;
+  if constexpr (TMA) {
+    static_assert(BR > 0, "no TMA box for this strip");
+    if (t == 0) {
+      mbar_init(&s_bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+      mbar_expect_tx(&s_bar, H * NC * 8 + (a.stall ? 16 : 0));   // the test hook waits for bytes that never come
+#pragma unroll 1
+      for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, src_ws * H + b * BR, &s_bar);
+    }
+    const bool ok = mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        if (a.err) atomicExch(a.err, 1);
+        mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);   // let the copy land before the block leaves
+      }
+      __syncthreads();
+      return;
+    }
+    if constexpr (PART != 2) ColStages<SP, 0, SP::S - 1, T, NC, false>::run(sm4, t);
+  } else {  // forward stage 0 from global memory
+    using G = Stg<SP, 0>;
+    constexpr int IT = (G::NB + TJ - 1) / TJ;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int j = j0 + it * TJ;
+      if (G::NB % TJ != 0 && j >= G::NB) continue;
+      float2 v[2][G::R];
+      const float4* src = reinterpret_cast<const float4*>(Z + (size_t)j * Wh + col0);
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) split2(ld_spec4<CG>(src + (size_t)r * G::NB * (Wh / 2)), v[0][r], v[1][r]);
+      Dft<G::R, false>::run(v[0]);
+      Dft<G::R, false>::run(v[1]);
+      float4* dst = sm4 + j * G::R * NP + cp;
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) dst[r * NP] = join2(v[0][r], v[1][r]);
+    }
+    __syncthreads();
+    ColStages<SP, 1, SP::S - 1, T, NC, false>::run(sm4, t);
+  }
+
+  // the rest of the pass (PART 1 leaves its outputs in the strip buffer)
+  float2* X0 = FPT ? sm + H * NC : sm;   // with MODE 2 the strip buffer holds the fingerprint
+  int bar_uses = 1;                       // s_bar completed once (the strip)
+  if (!col_tail<SP, W, NC, T, MODE, PART>(a, fp, c0, sm, Z, &s_bar, bar_uses, true, X0, [] {}, t)) return;
   if constexpr (TMA) {
     fence_proxy_async_smem();
     __syncthreads();
@@ -922,25 +950,24 @@ struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   // NC columns per block, CT threads, at least MINB resident blocks per SM
   // MODE: 0 plain loads and stores, 1 strip by TMA, 2 strip and fingerprint by TMA
+  static FixedCol col_entry(void* fn, int nc, int ct, size_t smem, bool tma) {
+    allow_max_dynamic_smem(fn);
+    FixedCol c{nc, ct, smem, fn, tma, tma_box_rows(H, nc)};
+    return c;
+  }
   template <int NC, int CT, int MINB, int MODE>
   static FixedCol col() {
     void* fn = MODE ? (void*)k_col_tma_fx<CS, W, NC, CT, MINB, MODE> : (void*)k_col_fx<CS, W, NC, CT, MINB>;
-    allow_max_dynamic_smem(fn);
-    return FixedCol{NC, CT, MODE == 2 ? col_fx_smem_fpt(H, NC) : col_fx_smem(H, NC), fn, MODE != 0,
-                    tma_box_rows(H, NC)};
+    return col_entry(fn, NC, CT, MODE == 2 ? col_fx_smem_fpt(H, NC) : col_fx_smem(H, NC), MODE != 0);
   }
   // the split column pass of forward units (NC columns, CT threads, MINB blocks)
   template <int NC, int CT, int MINB>
   static FixedCol col_fwd() {
-    void* fn = (void*)k_col_fwd_fx<CS, W, NC, CT, MINB>;
-    allow_max_dynamic_smem(fn);
-    return FixedCol{NC, CT, col_fx_smem(H, NC), fn, true, tma_box_rows(H, NC)};
+    return col_entry((void*)k_col_fwd_fx<CS, W, NC, CT, MINB>, NC, CT, col_fx_smem(H, NC), true);
   }
   template <int NC, int CT, int MINB>
   static FixedCol col_inv() {
-    void* fn = (void*)k_col_inv_fx<CS, W, NC, CT, MINB>;
-    allow_max_dynamic_smem(fn);
-    return FixedCol{NC, CT, col_fx_smem_fpt(H, NC), fn, true, tma_box_rows(H, NC)};
+    return col_entry((void*)k_col_inv_fx<CS, W, NC, CT, MINB>, NC, CT, col_fx_smem_fpt(H, NC), true);
   }
   template <int PPB>
   static FixedRow row() {
@@ -1011,25 +1038,30 @@ std::vector<FixedShape> build_registry() {
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(), D::col<4, 240, 3, 0>(),
                          D::col<8, 480, 1, 1>()},
-                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>()}, D::persist<192, 2, 4>()));
+                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>()},
+                        D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(), D::col<8, 360, 2, 0>(),
                          D::col<4, 180, 4, 2>()},
-                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>()}, D::persist<160, 2, 4>()));
+                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>()},
+                        D::persist<160, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(), D::col<4, 360, 2, 0>()},
-                        {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>()}, D::persist<256, 2, 4>()));
+                        {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>()},
+                        D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
-    v.push_back(D::make({D::row<4>(), D::row<2>()}, {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>()},
-                        {D::col_fwd<16, 128, 4>(), D::col_inv<16, 128, 4>()}, D::persist<32, 8, 16>()));
+    v.push_back(D::make({D::row<4>(), D::row<2>()},
+                        {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>()},
+                        {D::col_fwd<16, 128, 4>(), D::col_inv<16, 128, 4>()},
+                        D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
   return v;
@@ -1118,7 +1150,9 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   // and the inverse column FFT per candidate
   const bool units = a.units != nullptr || a.share > 1;
   const int nunits = units ? a.nunits : a.nitems;
-  const FixedCol& fc = units ? fs.col_inv : fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
+  const FixedCol& fv = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
+  // forward units take the split pass
+  const FixedCol& fc = units ? fs.col_inv : fv;
   const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};
@@ -1132,17 +1166,17 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
     dim3 g((a.H / 2) / fr.ppb, nunits), b(fr.threads * fr.ppb);
     PRNU_CUDA_TRY(cudaLaunchKernel(fr.fwd[a.rdtype], g, b, args, fr.smem, s));
   }
+  auto col_grid = [&](const FixedCol& c, int n) { return dim3((Wh + c.nc - 1) / c.nc, n); };
   if (units) {   // the forward half, per unit (same strip shape as the inverse half: one tensor map)
     ProfScope ps(lc, kKindColumn, s);
     const FixedCol& ff = fs.col_fwd;
-    dim3 g((Wh + ff.nc - 1) / ff.nc, nunits), b(ff.threads);
-    PRNU_CUDA_TRY(cudaLaunchKernel(ff.fn, g, b, targs, ff.smem, s));
+    PRNU_CUDA_TRY(cudaLaunchKernel(ff.fn, col_grid(ff, nunits), dim3(ff.threads), targs, ff.smem, s));
     lc.n += 1;
   }
   {
     ProfScope ps(lc, kKindColumn, s);
-    dim3 g((Wh + fc.nc - 1) / fc.nc, a.nitems), b(fc.threads);
-    PRNU_CUDA_TRY(cudaLaunchKernel(fc.fn, g, b, fc.tma ? targs : args, fc.smem, s));
+    PRNU_CUDA_TRY(cudaLaunchKernel(fc.fn, col_grid(fc, a.nitems), dim3(fc.threads), fc.tma ? targs : args, fc.smem,
+                                   s));
   }
   {
     ProfScope ps(lc, kKindRowInverse, s);
