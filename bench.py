@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the naive-path and CPU-oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", choices=["plain", "batched", "precision", "serving", "correction", "literal",
-                                                 "denoisers"],
+                                                 "denoisers", "shared"],
                     default="plain",
                     help="plain = the 1080p metric line; the others print their own JSON record")
     ap.add_argument("--queries", type=int, default=16, help="serving: queries of the capacity run")
@@ -882,6 +882,63 @@ def available_cores_str():
     return str(available_cores())
 
 
+def run_shared(args):
+    """Several fingerprints per frame (Eq. 3 against each candidate device):
+    frames of 1920x1080 (4) and 3840x2160 (2), 7x7-node windows around the
+    planted nodes, 8 fingerprints (the camera's own and 7 others), FP16
+    storage; the forward pass shared by each (frame, node) against every
+    candidate running its own (prnu_tuning.share_forward 1 and 0), with the
+    per-kernel split and the check that both give the same results bit for
+    bit."""
+    import torch
+    import synth
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    ctx = prnu.Context(0)
+    P = 8
+    peak, kind = hbm_peak()
+    out = {}
+    for (H, W, F) in ((1080, 1920, 4), (2160, 3840, 2)):
+        wl = synth.make_workload(2, H=H, W=W, F=F, on_grid=True, s_max=16)
+        fps = [wl.fingerprints[0]] + [synth.fingerprint_field(H, W, np.random.default_rng(50 + p)) for p in range(P - 1)]
+        win = synth.snap_windows(wl.grid, wl.planted[:, :2], np.full(F, 3))
+        frames = torch.from_numpy(wl.frames).to(dev)
+        R = torch.empty(frames.shape, dtype=torch.float16, device=dev)
+        sc = torch.empty(F, device=dev)
+        ctx.prnu_residual(frames, R, scale=sc, flags=prnu.PRNU_WEIGHT_BY_INTENSITY | prnu.PRNU_NORMALISE)
+        hs = [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(dev), prnu.PRNU_F16) for K in fps]
+        n = F * 49 * P
+        t0 = ctx.prnu_get_tuning(H, W)
+        leg, res = {}, {}
+        for share in (1, 0):
+            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"], 0, 1, share)
+            state = {}
+
+            def step():
+                state["r"] = ctx.eis_grid_search(R, hs, wl.grid, windows=win, scale=sc)
+
+            ms, prof = _timed_steps(step, args.steps, args.warmup, dev, ctx)
+            res[share] = state["r"].tobytes()
+            leg["shared" if share else "per_candidate"] = {
+                "value": round(n / (ms / 1e3), 1), "ms_per_step": round(ms, 3),
+                "kernels": {k: round(v["total_ms"] / args.steps, 3) for k, v in prof.items()}}
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"], t0["streams"], t0["share_forward"])
+        for h in hs:
+            ctx.prnu_fingerprint_release(h)
+        # byte model with P candidates per forward unit: (s_in + 12) HW / P + (12 + s_K / 2) HW
+        pb = (2 + 12) * H * W / P + (12 + 4 / 2) * H * W
+        leg["shared"]["path_roofline_frac"] = round(pb * leg["shared"]["value"] / 1e9 / peak, 4)
+        leg["speedup"] = round(leg["shared"]["value"] / leg["per_candidate"]["value"], 3)
+        leg["results_identical"] = res[1] == res[0]
+        out[f"{W}x{H}"] = dict(leg, frames=F, fingerprints=P, candidates_per_step=n)
+    print(json.dumps({"workload": "shared forward pass (several fingerprints per frame)", "metric": "candidates/s",
+                      "dtype": "f16", "steps": args.steps, "warmup": args.warmup, "peak": f"{peak} GB/s {kind}",
+                      "sizes": out}), flush=True)
+    ctx.close()
+
+
 def run_precision(args):
     """Config 4: 32 frames of 3840x2160, full 41x41 grid, half of the frames
     from an independent fingerprint; FP16 and BF16 residual storage with an
@@ -989,35 +1046,49 @@ def run_serving(args):
         w2, l2 = run(idx, list(arr))
         out[name] = summary(name, rate, idx, w2, l2, cap_q)
     st = ctx.prnu_server_stats_get()
-    # the oracle on sampled served results of the steady run
+    # the oracle on sampled served results of the steady run: per query one
+    # (frame, fingerprint) pair, its served node and the grid neighbours of
+    # that node inside the window; one process pool per resolution
     t0 = time.perf_counter()
     g = synth.GRID_FULL
-    checks, max_err, local_ok = [], 0.0, 0
     sample = list(range(n_cap, n_cap + n_st))[:args.oracle_queries]
+    picks = []
     for i in sample:
         q = queries[i]
         f = int(rng.integers(0, len(q.pool_index)))
         b = q.fp_ids.index(q.match) if q.match >= 0 else int(rng.integers(0, len(q.fp_ids)))
         r = results[i][f, b]
-        c = int(r["cand_idx"])
-        ci, cj = divmod(c, g.nth)
+        ci, cj = divmod(int(r["cand_idx"]), g.nth)
         lo_l, hi_l, lo_t, hi_t = (int(v) for v in q.windows[f])
         nodes = [(ci + di, cj + dj) for di in (-1, 0, 1) for dj in (-1, 0, 1)
                  if lo_l <= ci + di <= hi_l and lo_t <= cj + dj <= hi_t]
-        Rf = oracle.prnu_residual(pools[q.pool][q.pool_index[f]], normalise=True)[0]
-        K0 = oracle.fingerprint_term(banks[(q.H, q.W)][q.fp_ids[b]])
-        with ScorePool(Rf, K0, processes=min(len(nodes), available_cores())) as pool:
-            sc = pool([(g.lam_node(a), g.th_node(bb)) for a, bb in nodes])
+        picks.append((i, f, b, r, (ci, cj), nodes))
+    scored = {}
+    for res_key in sorted({(queries[i].H, queries[i].W) for i, *_ in picks}):
+        mine = [p_ for p_ in picks if (queries[p_[0]].H, queries[p_[0]].W) == res_key]
+        Rs = np.stack([oracle.prnu_residual(pools[queries[i].pool][queries[i].pool_index[f]], normalise=True)[0]
+                       for i, f, *_ in mine])
+        K0s = np.stack([oracle.fingerprint_term(banks[res_key][queries[i].fp_ids[b]]) for i, f, b, *_ in mine])
+        todo = [(k, g.lam_node(a_), g.th_node(b_)) for k, p_ in enumerate(mine) for a_, b_ in p_[5]]
+        with ScorePool(Rs, K0s, processes=min(len(todo), available_cores())) as pool:
+            out_ = pool(todo)
+        pos = 0
+        for k, p_ in enumerate(mine):
+            scored[p_[0]] = out_[pos:pos + len(p_[5])]
+            pos += len(p_[5])
+    checks, max_err, local_ok = [], 0.0, 0
+    for i, f, b, r, node, nodes in picks:
+        q = queries[i]
+        sc = scored[i]
         ref = {n: s_["pce"] for n, s_ in zip(nodes, sc)}
-        err = abs(float(r["pce"]) - ref[(ci, cj)]) / abs(ref[(ci, cj)])
-        best = max(ref.values())
-        ok = ref[(ci, cj)] >= best * (1 - 2e-2) and (int(r["dy"]), int(r["dx"])) == (
-            sc[nodes.index((ci, cj))]["dy"], sc[nodes.index((ci, cj))]["dx"])
+        at = sc[nodes.index(node)]
+        err = abs(float(r["pce"]) - at["pce"]) / abs(at["pce"])
+        ok = at["pce"] >= max(ref.values()) * (1 - 2e-2) and (int(r["dy"]), int(r["dx"])) == (at["dy"], at["dx"])
         max_err = max(max_err, err)
         local_ok += bool(ok)
         checks.append({"query": i, "res": f"{q.W}x{q.H}", "frame": f, "fingerprint": q.fp_ids[b],
                        "matched": bool(q.match >= 0), "served_pce": round(float(r["pce"]), 3),
-                       "oracle_pce": round(ref[(ci, cj)], 3), "rel_err": err, "local_argmax_ok": bool(ok)})
+                       "oracle_pce": round(at["pce"], 3), "rel_err": err, "local_argmax_ok": bool(ok)})
     oracle_check = {"queries": len(sample), "max_pce_rel_err": max_err, "local_argmax_ok": local_ok,
                     "seconds": round(time.perf_counter() - t0, 1),
                     "what": "per sampled query one (frame, fingerprint) pair: the FP64 oracle's PCE at the served "
@@ -1049,6 +1120,8 @@ def main():
         run_literal(args)
     elif args.workload == "denoisers":
         run_denoisers(args)
+    elif args.workload == "shared":
+        run_shared(args)
     else:
         run_ours(args)
 

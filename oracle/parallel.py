@@ -38,21 +38,27 @@ def available_cores() -> int:
 
 def _init(d):
     _STATE["R"] = np.load(os.path.join(d, "R.npy"), mmap_mode="r")
-    _STATE["K0"] = np.load(os.path.join(d, "K0.npy"))
-    _STATE["FK"] = np.fft.rfft2(_STATE["K0"])
+    _STATE["K0"] = np.load(os.path.join(d, "K0.npy"), mmap_mode="r")
+    _STATE["FK"] = {}
 
 
 def _score_node(node):
     f, lam, th = node
-    return score(np.asarray(_STATE["R"][f]), _STATE["K0"], lam, th, _STATE["FK"])
+    K0 = _STATE["K0"]
+    kf = f if K0.ndim == 3 else 0          # one fingerprint term per frame, or one for all
+    if kf not in _STATE["FK"]:
+        _STATE["FK"][kf] = np.fft.rfft2(np.asarray(K0[kf] if K0.ndim == 3 else K0))
+    K = np.asarray(K0[kf] if K0.ndim == 3 else K0)
+    return score(np.asarray(_STATE["R"][f]), K, lam, th, _STATE["FK"][kf])
 
 
 class ScorePool:
     """Score candidates of the residual(s) R against K0 in worker processes.
 
-    R is one residual [H, W] or a stack [F, H, W].  ``pool(nodes)`` takes
-    (lam, th) pairs (frame 0) or (f, lam, th) triples and returns
-    [score(R[f], K0, lam, th) ...] in order.  A worker that cannot start or
+    R is one residual [H, W] or a stack [F, H, W]; K0 one fingerprint term
+    [H, W] or one per frame [F, H, W].  ``pool(nodes)`` takes (lam, th) pairs
+    (frame 0) or (f, lam, th) triples and returns [score(R[f], K0 (or K0[f]),
+    lam, th) ...] in order.  A worker that cannot start or
     dies raises BrokenProcessPool in the caller (it is not replaced and waited
     for)."""
 

@@ -306,7 +306,9 @@ def make_query_stream(n_queries: int, *, rate_hz: float = 20.0,
             if src < bank_size:
                 Kp = banks[(H, W)][src]
             else:
-                Kp = fingerprint_field(H, W, rng_for(config, STREAM_K, variant=2 + 1000 * H))
+                # a camera outside the bank: its variant is disjoint from the
+                # bank's 1 + 1000 H + b (b < bank_size <= 999)
+                Kp = fingerprint_field(H, W, rng_for(config, STREAM_K, variant=5_000_000 + H))
             rt = rng_for(config, STREAM_TRANSFORM, variant=1 + 1000 * H + src)
             planted = np.empty((pool_frames, 4))
             lam, th = rt.uniform(0.95, 1.05), rt.uniform(-2.5, 2.5)
