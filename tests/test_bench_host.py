@@ -74,3 +74,20 @@ def test_single_process_replica_needs_no_collective():
     assert r.max(3.5) == 3.5 and r.whole_job(10, 2.0) == 5.0
     r.barrier()
     r.close()
+
+
+def test_affinity_ranges_are_compact():
+    assert bench._ranges([0, 1, 2, 5, 7, 8]) == "0-2,5,7-8"
+    assert bench._ranges([3]) == "3"
+    assert bench._ranges([]) == ""
+
+
+def test_shared_byte_model_reduces_to_the_path_model():
+    """With one fingerprint per forward unit the shared byte model charges
+    the row pass (s_in HW + 4HW), the forward half in place (8HW) and the
+    per-candidate half (read 4HW, fingerprint s_K HW/2, write 4HW) plus the
+    row inverse's read (4HW): the path model plus the forward half's extra
+    round trip of the spectrum (8HW)."""
+    H, W, s_in, s_k = 1080, 1920, 2, 4
+    shared = (s_in + 12) * H * W / 1 + (12 + s_k / 2) * H * W
+    assert shared == bench.path_bytes(H, W, s_in, s_k) + 8 * H * W

@@ -59,3 +59,22 @@ def test_precision_workload_half_unmatched():
     wl = synth.make_workload(4, H=64, W=96, F=8)
     assert list(wl.frame_fp) == [0] * 4 + [1] * 4 and len(wl.fingerprints) == 1
     assert wl.meta["generated_by"] == [0, 1]
+
+
+def test_query_stream_without_frame_arrays_is_the_same_stream():
+    q1, b1 = synth.make_query_stream(6, rate_hz=20.0, pool_frames=4, match_sources=1)
+    q2, b2, pools = synth.make_query_stream(6, rate_hz=20.0, pool_frames=4, match_sources=1, materialise=False)
+    for a, c in zip(q1, q2):
+        assert c.frames is None
+        assert np.array_equal(a.frames, pools[c.pool][c.pool_index])
+        assert a.fp_ids == c.fp_ids and a.match == c.match and np.array_equal(a.windows, c.windows)
+
+
+def test_out_of_bank_camera_differs_from_every_bank_fingerprint():
+    qs, banks, pools = synth.make_query_stream(12, rate_hz=20.0, pool_frames=2, match_sources=1, materialise=False)
+    for (H, W, src), frames in pools.items():
+        if src < len(banks[(H, W)]):
+            continue
+        K = synth.fingerprint_field(H, W, synth.rng_for(5, gen.STREAM_K, variant=5_000_000 + H))
+        for Kb in banks[(H, W)]:
+            assert abs(np.corrcoef(K.ravel()[:100000], Kb.ravel()[:100000])[0, 1]) < 0.05
