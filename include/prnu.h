@@ -160,6 +160,10 @@ int prnu_fingerprint_release(prnu_ctx* ctx, uint64_t handle);
  *            device pointer it is asynchronous.
  *  d_all_pce: device double [F*P*nlam*nth] or NULL; receives every evaluated
  *            candidate's PCE at (f*P + p)*nlam*nth + cand_idx, NaN elsewhere.
+ * With P > 1 the candidates of one frame and node share the warp, the row FFT
+ * and the forward column FFT (they do not depend on the fingerprint), on the
+ * sizes with compile-time-planned kernels, unless prnu_tuning.share_forward
+ * is 0; the results are the same bit for bit either way.
  * F == 0 or P == 0 is a no-op.  Errors: PRNU_EINVAL, PRNU_ENOTFOUND, PRNU_ENOMEM. */
 int eis_grid_search(prnu_ctx* ctx, const void* d_resid, int dtype, const float* d_scale,
                     int F, int H, int W, const uint64_t* fp_handles, int P,
