@@ -774,3 +774,28 @@ def test_wavelet_residual_recovers_planted_on_grid():
         b = best[f][0]
         assert (b["lam"], b["th_deg"]) == (pytest.approx(lam, abs=0), pytest.approx(th, abs=0))
         assert (b["dy"], b["dx"]) == (sy, sx) and b["pce"] > 1000
+
+
+# ------------------------------------------------------------------ NCC (Eq. 1)
+
+def test_ncc_of_a_signal_with_itself_is_one():
+    """rho(X, K) at the shift that aligns them: for K0 = X - mean(X) the
+    correlation at zero shift is sum (X - mean)^2 = ||X - mean||^2, so rho = 1;
+    for K0 = -(X - mean), rho = -1; scaling either side leaves rho unchanged."""
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((24, 30)) * 3 + 5
+    K0 = X - X.mean()
+    C = oracle.xcorr(X, K0)
+    assert oracle.ncc_peak(X, K0, C[0, 0]) == pytest.approx(1.0, rel=1e-13)
+    assert oracle.ncc_peak(X, -K0, -C[0, 0]) == pytest.approx(-1.0, rel=1e-13)
+    assert oracle.ncc_peak(4 * X, K0, oracle.xcorr(4 * X, K0)[0, 0]) == pytest.approx(1.0, rel=1e-13)
+
+
+def test_ncc_is_bounded_by_one_at_every_shift():
+    """Cauchy-Schwarz: |rho| <= 1 for the correlation at any cyclic shift."""
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((20, 28))
+    K0 = oracle.fingerprint_term(rng.standard_normal((20, 28)))
+    C = oracle.xcorr(X, K0)
+    r = np.array([oracle.ncc_peak(X, K0, c) for c in C.ravel()])
+    assert np.all(np.abs(r) <= 1 + 1e-12)
