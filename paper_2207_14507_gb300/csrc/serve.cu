@@ -203,10 +203,11 @@ struct Server::Impl {
     return b;
   }
 
-  // spectra: the wave's candidates, then one slot per forward unit (at most
-  // one per candidate); row statistics: the candidates
-  size_t workspace_bytes(int H, int W, int wave) const {
-    return 2 * (size_t)wave * H * (W / 2) * sizeof(float2) + (size_t)wave * H * sizeof(RowStat);
+  // spectra: the wave's candidates, then, for a query whose fingerprints share
+  // forward units, one slot per unit (at most one per candidate of the wave);
+  // row statistics: the candidates
+  size_t workspace_bytes(int H, int W, int wave, bool units) const {
+    return (units ? 2 : 1) * (size_t)wave * H * (W / 2) * sizeof(float2) + (size_t)wave * H * sizeof(RowStat);
   }
 
   // ---------------------------------------------------------------- submit / poll (user threads)
@@ -257,7 +258,7 @@ struct Server::Impl {
     q->call.H = q->H;
     q->call.W = q->W;
     q->bytes = query_bytes(*q);
-    if (q->bytes + workspace_bytes(q->H, q->W, std::max(1, std::min(q->tn.wave, kMaxWave))) > ctx->budget)
+    if (q->bytes + workspace_bytes(q->H, q->W, std::max(1, std::min(q->tn.wave, kMaxWave)), unit_major) > ctx->budget)
       throw Error{PRNU_ENOMEM, "the query alone exceeds the HBM budget"};
     std::lock_guard<std::mutex> lk(mu);
     if (queued.size() >= kMaxQueued) throw Error{PRNU_EAGAIN, "query queue full"};
@@ -353,9 +354,10 @@ struct Server::Impl {
     q.h_out = nullptr;
   }
 
-  void ensure_workspace(int H, int W, int wave) {
-    const size_t sb = 2 * (size_t)wave * H * (W / 2) * sizeof(float2);
-    const size_t tb = (size_t)wave * H * sizeof(RowStat);
+  // spectrum slots and row-statistics slots (candidates) for frames of H x W
+  void ensure_workspace(int H, int W, int spec_slots, int stat_slots) {
+    const size_t sb = (size_t)spec_slots * H * (W / 2) * sizeof(float2);
+    const size_t tb = (size_t)stat_slots * H * sizeof(RowStat);
     if (sb <= ws_spec_bytes && tb <= ws_stats_bytes) return;
     PRNU_CUDA_TRY(cudaStreamSynchronize(s_comp));
     if (ws_spec) ctx_free(ctx, ws_spec, ws_spec_bytes);
@@ -372,7 +374,7 @@ struct Server::Impl {
   bool admit(const std::shared_ptr<Query>& qp) {
     Query& q = *qp;
     const int wave = std::max(1, std::min(q.tn.wave, kMaxWave));
-    ensure_workspace(q.H, q.W, wave);
+    ensure_workspace(q.H, q.W, (q.call.share > 1 ? 2 : 1) * wave, wave);
     if (ctx->used.load() + q.bytes > ctx->budget) return false;
     const int slot0 = alloc_frames(q.F);
     if (slot0 < 0) return false;
@@ -492,7 +494,6 @@ struct Server::Impl {
     int rowT, rowMB;
     row_launch_shape(prow, &rowT, &rowMB);
     const int wave = std::max(1, std::min(tn.wave, kMaxWave));
-    ensure_workspace(H, W, wave);
     void** hi = slot.h_tab;
     void** hr = slot.h_tab + kMaxWave;
     int* hu = reinterpret_cast<int*>(slot.h_tab + 2 * kMaxWave);   // forward units' first slots
@@ -528,6 +529,8 @@ struct Server::Impl {
       if (q.next == n) finished.push_back(&q);
     }
     hu[nunits] = count;
+    // the candidates' slots, then (grouped wave) one per forward unit
+    ensure_workspace(H, W, count + (grouped ? nunits : 0), count);
     PRNU_CUDA_TRY(cudaMemcpyAsync(slot.d_tab, slot.h_tab, kWaveTabBytes, cudaMemcpyHostToDevice, s_comp));
     PassArgs a{};
     a.err = ctx->d_err;
