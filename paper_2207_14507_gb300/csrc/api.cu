@@ -162,6 +162,9 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
   // the planned kernels run one row pair per block best; waves of a few
   // hundred candidates (a few GB of spectra) amortise the per-wave finalisation
   t.ppb = find_fixed(H, W) ? 1 : 2;
+  // sizes without compile-time-planned kernels run the generic ones (-1), so
+  // that what prnu_get_tuning reports is accepted by prnu_set_tuning
+  t.variant = find_fixed(H, W) ? 0 : -1;
   const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
   t.wave = (int)std::max<size_t>(1, std::min<size_t>(512, ((size_t)4 << 30) / per_item));
   // one stream: two-stream waves gain under 1% at 1080p and make the

@@ -120,3 +120,44 @@ def test_served_queries_share_and_match(ctx, prnu):
     assert res1.tobytes() == res0.tobytes()
     for s in served:
         assert s.tobytes() == res1.tobytes()
+
+
+def test_sharing_steps_aside_where_it_cannot_apply(ctx, prnu):
+    """Sizes without compile-time-planned kernels, the persistent launch, and
+    waves smaller than one unit run every candidate alone: the results equal
+    the default path's (waves of shared units where it applies)."""
+    # a size with no planned kernels: 240 x 320, three fingerprints
+    wl = synth.make_workload(2, H=240, W=320, F=2, on_grid=True, s_max=8)
+    fps = _fingerprints(wl, 3)
+    win = synth.snap_windows(wl.grid, wl.planted[:, :2], np.array([1, 1]))
+    r1, a1 = _search(ctx, prnu, wl, fps, win, torch.float32, 1, 8)
+    r0, a0 = _search(ctx, prnu, wl, fps, win, torch.float32, 0, 8)
+    assert r1.tobytes() == r0.tobytes()
+    np.testing.assert_array_equal(a1, a0)
+    # a planned size: waves of 2 candidates (smaller than a unit of 3), and the persistent launch
+    wl = synth.make_workload(1, F=2, on_grid=True)
+    fps = _fingerprints(wl, 3)
+    win = synth.snap_windows(wl.grid, wl.planted[:, :2], np.array([1, 2]))
+    ref, aref = _search(ctx, prnu, wl, fps, win, torch.float32, 1, 64)
+    small, asmall = _search(ctx, prnu, wl, fps, win, torch.float32, 1, 2)
+    assert small.tobytes() == ref.tobytes()
+    np.testing.assert_array_equal(asmall, aref)
+    t0 = ctx.prnu_get_tuning(256, 256)
+    try:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], 64, 0, 1, 1, 1)
+        frames = torch.from_numpy(wl.frames).to(DEV)
+        R = torch.empty(frames.shape, device=DEV)
+        sc = torch.empty(2, device=DEV)
+        ctx.prnu_residual(frames, R, scale=sc)
+        hs = [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(DEV)) for K in fps]
+        ap = torch.empty((2, 3, wl.grid.size), dtype=torch.float64, device=DEV)
+        pers = ctx.eis_grid_search(R, hs, wl.grid, windows=win, scale=sc, all_pce=ap)
+        torch.cuda.synchronize()
+        for h in hs:
+            ctx.prnu_fingerprint_release(h)
+    finally:
+        ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"], t0["streams"], t0["share_forward"])
+    np.testing.assert_allclose(ap.cpu().numpy(), aref, rtol=1e-5)
+    assert np.array_equal(pers["cand_idx"], ref["cand_idx"])
+    assert np.array_equal(pers["dy"], ref["dy"]) and np.array_equal(pers["dx"], ref["dx"])
