@@ -370,6 +370,7 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.share = share;
   a.units = nullptr;
   a.unit_of = nullptr;
+  a.fp_f32 = std::any_of(fd.begin(), fd.end(), [](const FpDesc& d) { return d.dtype == kF32; }) ? 1 : 0;
 
   if (persistent) {
     int* st0 = reinterpret_cast<int*>(c->ws_persist.p);

@@ -94,6 +94,8 @@ struct PassArgs {
   const int* unit_of;
   int nunits;
   int share;
+  // host-side: some fingerprint of the pass is stored FP32 (launch choices only)
+  int fp_f32;
 };
 
 __device__ __forceinline__ int unit_first(const PassArgs& a, int u) { return a.units ? a.units[u] : u * a.share; }

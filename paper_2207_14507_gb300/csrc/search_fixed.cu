@@ -215,6 +215,19 @@ __device__ __forceinline__ void load_fp_pair(const FpDesc& fp, int j, int col0, 
   }
 }
 
+// The product for the packed column 0 (DC + i*Nyquist columns of two real
+// spectra in one complex column): F, Fm the frame bins i and H - i, S, Sm the
+// fingerprint bins; unpack both, conj-multiply each real column's spectrum,
+// repack.
+__device__ __forceinline__ float2 packed_col0_product(float2 F, float2 Fm, float2 S, float2 Sm) {
+  const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
+  const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
+  const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
+  const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
+  const float2 p1 = c_conj_mul(Aa, Ka), p2 = c_conj_mul(Bb, Kb);
+  return make_float2(p1.x - p2.y, p1.y + p2.x);
+}
+
 // Rows per TMA box of an H-row strip of NC columns (float2): a divisor of H of
 // at most 256 rows whose box size is a multiple of 128 bytes, so that every
 // box lands 128-byte aligned in shared memory.
@@ -225,6 +238,12 @@ __host__ __device__ constexpr int tma_box_rows(int H, int NC, int esize = 8) {
 }
 __host__ __device__ constexpr int fp_tmap_index(int NC) { return NC == 2 ? 0 : NC == 4 ? 1 : NC == 8 ? 2 : 3; }
 __host__ __device__ constexpr size_t col_fx_smem_fpt(int H, int nc) { return (size_t)H * (nc + 1) * sizeof(float2); }
+// bytes per fingerprint bin of the separate fingerprint region (MODE 3: FP32
+// or FP16 bins; MODE 4: FP16 bins only)
+__host__ __device__ constexpr int fp_region_bin(int mode) { return mode == 3 ? 8 : mode == 4 ? 4 : 0; }
+__host__ __device__ constexpr size_t col_fx_smem_sep(int H, int nc, int mode) {
+  return (size_t)H * nc * (sizeof(float2) + fp_region_bin(mode));
+}
 constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait before giving up
 
 // The column pass from the last forward stage on, for the strip of NC
@@ -237,16 +256,20 @@ constexpr long long kTmaWaitPolls = 1ll << 20;   // polls of mbarrier.try_wait b
 // thread holds its inputs (fp_tma_ok: the caller allows it), completing the
 // mbarrier bar (its completions so far: bar_uses, advanced here when the copy
 // is made, the same on every thread); X0 is the packed column-0 scratch (H
-// float2 that the fingerprint strip does not cover).  hook() runs on every
-// thread right after the barrier that follows the loads of the last forward
-// stage (the strip buffer's old contents are then no longer needed).
+// float2 that the fingerprint strip does not cover).  With MODE 3 and 4 the
+// caller has already issued the fingerprint strip's copy into its own region
+// after the strip (fp_tma_ok: it did), completing fbar once; X0 is then the
+// strip buffer itself, free once every thread holds its inputs (PART 2 needs
+// no X0: it multiplies as it loads).  hook() runs on every thread right after
+// the barrier that follows the loads of the last forward stage (the strip
+// buffer's old contents are then no longer needed).
 // t = threadIdx.x.  Returns false if the fingerprint copy did not land in
 // time (a.err raised).
 template <class SP, int W, int NC, int T, int MODE, int PART, class Hook>
 __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, int c0, float2* sm, float2* Z,
                                          uint64_t* bar, int& bar_uses, bool fp_tma_ok, float2* X0, Hook&& hook,
-                                         int t) {
-  constexpr bool TMA = MODE >= 1, FPT = MODE == 2 && PART != 1;
+                                         int t, uint64_t* fbar = nullptr) {
+  constexpr bool TMA = MODE >= 1, FPT = MODE >= 2 && PART != 1, FPSEP = MODE >= 3;
   constexpr int H = SP::N, Wh = W / 2;
   using IS = typename SP::Rev;
   using M = ColMap<NC, T>;
@@ -260,6 +283,71 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
   static_assert(I0::R == FL::R && I0::NB == FL::NB && FL::NB == FL::NS, "register hand-off needs the reversed plan");
   constexpr int IT = (FL::NB + TJ - 1) / TJ;
   float2 v[IT][2][FL::R];
+  // The fingerprint strip comes by TMA (into the strip buffer with MODE 2,
+  // into its own region with MODE 3/4), else by per-thread loads.
+  const bool fp_tma = FPT && fp_tma_ok && fp.tmaps != nullptr && NC * (fp.dtype == kF32 ? 8 : 4) >= 16;
+  char* const fpsm = reinterpret_cast<char*>(sm) + (FPSEP ? (size_t)H * NC * sizeof(float2) : 0);
+  // fingerprint bin (i, col) of this strip
+  auto fp_bin = [&](int i, int col) -> float2 {
+    if (fp_tma) {
+      if (fp.dtype == kF32) return reinterpret_cast<const float2*>(fpsm)[i * NC + (col - c0)];
+      return __half22float2(reinterpret_cast<const __half2*>(fpsm)[i * NC + (col - c0)]);
+    }
+    return load_spec(fp.spec, fp.dtype, (size_t)i * Wh + col);
+  };
+  // the fingerprint bins (j + r*NS, col0) and (j + r*NS, col0 + 1) from the TMA'd strip
+  auto fp_pair = [&](int j, int r, float2& s0, float2& s1) {
+    if (fp.dtype == kF32) {
+      split2(reinterpret_cast<const float4*>(fpsm)[(j + r * FL::NS) * NP + cp], s0, s1);
+    } else {
+      const float2 u = reinterpret_cast<const float2*>(fpsm)[(j + r * FL::NS) * NP + cp];   // two __half2
+      s0 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+      s1 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    }
+  };
+  if constexpr (PART == 2 && FPSEP) {
+    // The strip holds the last forward stage's outputs in natural order and
+    // the fingerprint strip has its own region: each bin is multiplied as it
+    // is loaded, and column 0's mirror bins H - i are read from the strip.
+    if (fp_tma) {
+      const bool ok = mbar_wait_bounded(fbar, 0, kTmaWaitPolls);
+      if (__syncthreads_or(!ok)) {
+        if (t == 0) {
+          if (a.err) atomicExch(a.err, 1);
+          mbar_wait_bounded(fbar, 0, kTmaWaitPolls);
+        }
+        __syncthreads();
+        return false;
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int j = j0 + it * TJ;
+      if (FL::NB % TJ != 0 && j >= FL::NB) continue;
+      const float4* src = sm4 + j * NP + cp;
+      float2 sf[2][FL::R];
+      if (!fp_tma) load_fp_pair<FL::R, FL::NS, Wh>(fp, j, col0, sf);
+#pragma unroll
+      for (int r = 0; r < FL::R; ++r) {
+        float2 F0, F1, s0, s1;
+        split2(src[r * FL::NB * NP], F0, F1);
+        if (fp_tma) fp_pair(j, r, s0, s1);
+        else {
+          s0 = sf[0][r];
+          s1 = sf[1][r];
+        }
+        if (col0 == 0) {
+          const int i = j + r * FL::NS, im = i == 0 ? 0 : H - i;
+          v[it][0][r] = packed_col0_product(F0, sm[im * NC], fp_bin(i, 0), fp_bin(im, 0));
+        } else {
+          v[it][0][r] = c_conj_mul(F0, s0);
+        }
+        v[it][1][r] = c_conj_mul(F1, s1);
+      }
+    }
+    __syncthreads();   // every strip value read before the first inverse stage rewrites the strip
+    hook();
+  } else {
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
     const int j = j0 + it * TJ;
@@ -270,10 +358,7 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
   }
   __syncthreads();
   hook();
-  // The fingerprint strip: by TMA into the strip buffer, which is free now
-  // (every thread holds its inputs), else by per-thread loads.
-  const bool fp_tma = FPT && fp_tma_ok && fp.tmaps != nullptr && NC * (fp.dtype == kF32 ? 8 : 4) >= 16;
-  if constexpr (FPT) {
+  if constexpr (FPT && !FPSEP) {
     if (fp_tma && t == 0) {
       const CUtensorMap* fm = reinterpret_cast<const CUtensorMap*>(fp.tmaps) + fp_tmap_index(NC);
       const int es = fp.dtype == kF32 ? 8 : 4, fbr = tma_box_rows(H, NC, es);
@@ -309,27 +394,20 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
   }
   if constexpr (FPT) {
     if (fp_tma) {
-      const int ph = bar_uses & 1;
-      ++bar_uses;
-      const bool ok = mbar_wait_bounded(bar, ph, kTmaWaitPolls);
+      uint64_t* const wb = FPSEP ? fbar : bar;
+      const int ph = FPSEP ? 0 : bar_uses & 1;
+      if (!FPSEP) ++bar_uses;
+      const bool ok = mbar_wait_bounded(wb, ph, kTmaWaitPolls);
       if (__syncthreads_or(!ok)) {
         if (t == 0) {
           if (a.err) atomicExch(a.err, 1);
-          mbar_wait_bounded(bar, ph, kTmaWaitPolls);
+          mbar_wait_bounded(wb, ph, kTmaWaitPolls);
         }
         __syncthreads();
         return false;
       }
     }
   }
-  // fingerprint bin (i, col) of this strip
-  auto fp_bin = [&](int i, int col) -> float2 {
-    if (fp_tma) {
-      if (fp.dtype == kF32) return sm[i * NC + (col - c0)];
-      return __half22float2(reinterpret_cast<const __half2*>(sm)[i * NC + (col - c0)]);
-    }
-    return load_spec(fp.spec, fp.dtype, (size_t)i * Wh + col);
-  };
   // thread holds bins i = j + r*NS of columns col0 and col0 + 1
   if (c0 == 0) {
     // packed column 0 (DC + i*Nyquist): the product needs bin H - i as well
@@ -352,14 +430,7 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
         for (int r = 0; r < FL::R; ++r) {
           const int i = j + r * FL::NS;
           const int im = i == 0 ? 0 : H - i;
-          const float2 F = v[it][0][r], Fm = X0[im];
-          const float2 S = fp_bin(i, 0), Sm = fp_bin(im, 0);
-          const float2 Aa = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
-          const float2 Bb = make_float2(0.5f * (F.y + Fm.y), 0.5f * (Fm.x - F.x));
-          const float2 Ka = make_float2(0.5f * (S.x + Sm.x), 0.5f * (S.y - Sm.y));
-          const float2 Kb = make_float2(0.5f * (S.y + Sm.y), 0.5f * (Sm.x - S.x));
-          const float2 p1 = c_conj_mul(Aa, Ka), p2 = c_conj_mul(Bb, Kb);
-          v[it][0][r] = make_float2(p1.x - p2.y, p1.y + p2.x);
+          v[it][0][r] = packed_col0_product(v[it][0][r], X0[im], fp_bin(i, 0), fp_bin(im, 0));
         }
       }
     }
@@ -371,18 +442,10 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
     const int j = j0 + it * TJ;
     if (FL::NB % TJ != 0 && j >= FL::NB) continue;
     if (fp_tma) {
-      const float4* s4 = reinterpret_cast<const float4*>(sm) + j * NP + cp;
-      const float2* s2 = reinterpret_cast<const float2*>(sm) + j * NP + cp;   // two __half2
 #pragma unroll
       for (int r = 0; r < FL::R; ++r) {
         float2 s0, s1;
-        if (fp.dtype == kF32) {
-          split2(s4[r * FL::NS * NP], s0, s1);
-        } else {
-          const float2 u = s2[r * FL::NS * NP];
-          s0 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-          s1 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-        }
+        fp_pair(j, r, s0, s1);
         if (!col0_done) v[it][0][r] = c_conj_mul(v[it][0][r], s0);
         v[it][1][r] = c_conj_mul(v[it][1][r], s1);
       }
@@ -396,7 +459,8 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
       }
     }
   }
-  if (fp_tma) __syncthreads();   // every fingerprint bin read before the strip buffer is rewritten
+  if (!FPSEP && fp_tma) __syncthreads();   // every fingerprint bin read before the strip buffer is rewritten
+  }
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
     const int j = j0 + it * TJ;
@@ -447,8 +511,11 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
 // workspace spectra as a [slots*H][W] float tensor) and leaves the same way.
 // MODE 2: the fingerprint strip too comes by TMA, into the strip buffer once
 // the last forward stage has taken its inputs (the packed column-0 scratch then
-// sits after the strip).  A TMA wait that runs out raises a.err and abandons
-// the candidate.
+// sits after the strip).  MODE 3 and 4: the fingerprint strip comes by TMA
+// into its own region after the strip buffer, copied from the start together
+// with the strip (MODE 4 sizes the region for FP16 bins: FP32 fingerprints
+// are then loaded per thread).  A TMA wait that runs out raises a.err and
+// abandons the candidate.
 // PART splits the pass for forward units (candidates that share a frame and
 // a grid node): PART 1 runs the forward column FFT only and stores its
 // output, in natural order, back to slot ws; PART 2 loads that output from
@@ -459,7 +526,7 @@ __device__ __forceinline__ bool col_tail(const PassArgs& a, const FpDesc& fp, in
 template <class SP, int W, int NC, int T, bool CG = false, int MODE = 0, int PART = 0>
 __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int bx, float2* sm,
                                          const CUtensorMap* map = nullptr, int src_ws = -1) {
-  constexpr bool TMA = MODE >= 1, FPT = MODE == 2 && PART != 1;
+  constexpr bool TMA = MODE >= 1, FPT = MODE >= 2 && PART != 1, FPSEP = MODE >= 3 && PART != 1;
   static_assert(PART == 0 || TMA, "the split column pass moves its strips by TMA");
   if (src_ws < 0) src_ws = ws;
   constexpr int H = SP::N, Wh = W / 2;
@@ -477,11 +544,17 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   const FpDesc fp = a.fps[wi.fp];
 
   constexpr int BR = tma_box_rows(H, NC);
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_fbar;
+  // MODE 3/4: the fingerprint strip's copy goes out with the strip's (a
+  // region sized for its bins, boxes of at least 16 bytes)
+  const int fes = fp.dtype == kF32 ? 8 : 4;
+  const bool fp_sep = FPSEP && fp.tmaps != nullptr && fes <= fp_region_bin(MODE) && NC * fes >= 16;
   if constexpr (TMA) {
     static_assert(BR > 0, "no TMA box for this strip");
+    static_assert(!FPSEP || (H * NC * sizeof(float2)) % 128 == 0, "the fingerprint region starts 128-byte aligned");
     if (t == 0) {
       mbar_init(&s_bar, 1);
+      if (FPSEP) mbar_init(&s_fbar, 1);
       fence_mbar_init();
     }
     __syncthreads();
@@ -489,12 +562,23 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
       mbar_expect_tx(&s_bar, H * NC * 8 + (a.stall ? 16 : 0));   // the test hook waits for bytes that never come
 #pragma unroll 1
       for (int b = 0; b < H / BR; ++b) tma_load_2d(sm + b * BR * NC, map, 2 * c0, src_ws * H + b * BR, &s_bar);
+      if (fp_sep) {
+        const CUtensorMap* fm = reinterpret_cast<const CUtensorMap*>(fp.tmaps) + fp_tmap_index(NC);
+        const int fbr = tma_box_rows(H, NC, fes);
+        char* dst = reinterpret_cast<char*>(sm) + (size_t)H * NC * sizeof(float2);
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(fm))
+                     : "memory");
+        mbar_expect_tx(&s_fbar, H * NC * fes);
+#pragma unroll 1
+        for (int b = 0; b < H / fbr; ++b) tma_load_2d(dst + (size_t)b * fbr * NC * fes, fm, 2 * c0, b * fbr, &s_fbar);
+      }
     }
     const bool ok = mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         if (a.err) atomicExch(a.err, 1);
-        mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);   // let the copy land before the block leaves
+        mbar_wait_bounded(&s_bar, 0, kTmaWaitPolls);   // let the copies land before the block leaves
+        if (fp_sep) mbar_wait_bounded(&s_fbar, 0, kTmaWaitPolls);
       }
       __syncthreads();
       return;
@@ -522,9 +606,11 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int is, int ws, int 
   }
 
   // the rest of the pass (PART 1 leaves its outputs in the strip buffer)
-  float2* X0 = FPT ? sm + H * NC : sm;   // with MODE 2 the strip buffer holds the fingerprint
-  int bar_uses = 1;                       // s_bar completed once (the strip)
-  if (!col_tail<SP, W, NC, T, MODE, PART>(a, fp, c0, sm, Z, &s_bar, bar_uses, true, X0, [] {}, t)) return;
+  float2* X0 = FPT && !FPSEP ? sm + H * NC : sm;   // with MODE 2 the strip buffer holds the fingerprint
+  int bar_uses = 1;                                  // s_bar completed once (the strip)
+  if (!col_tail<SP, W, NC, T, MODE, PART>(a, fp, c0, sm, Z, &s_bar, bar_uses, FPSEP ? fp_sep : true, X0, [] {}, t,
+                                          &s_fbar))
+    return;
   if constexpr (TMA) {
     fence_proxy_async_smem();
     __syncthreads();
@@ -687,12 +773,12 @@ __global__ void __launch_bounds__(T, MINB) k_col_fwd_fx(PassArgs a, const __grid
   col_body<SP, W, NC, T, false, 1, 1>(a, unit_first(a, u), a.nitems + u, blockIdx.x,
                                       reinterpret_cast<float2*>(smem4f), &map);
 }
-template <class SP, int W, int NC, int T, int MINB>
+template <class SP, int W, int NC, int T, int MINB, int MODE>
 __global__ void __launch_bounds__(T, MINB) k_col_inv_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(1024) float4 smem4i[];
   const int s = blockIdx.y;
-  col_body<SP, W, NC, T, false, 2, 2>(a, s, s, blockIdx.x, reinterpret_cast<float2*>(smem4i), &map,
-                                      a.nitems + unit_of_slot(a, s));
+  col_body<SP, W, NC, T, false, MODE, 2>(a, s, s, blockIdx.x, reinterpret_cast<float2*>(smem4i), &map,
+                                         a.nitems + unit_of_slot(a, s));
 }
 
 template <class SP, int T, int PPB>
@@ -950,24 +1036,27 @@ struct ShapeDef {
   static constexpr int W = RS::N, H = CS::N;
   // NC columns per block, CT threads, at least MINB resident blocks per SM
   // MODE: 0 plain loads and stores, 1 strip by TMA, 2 strip and fingerprint by TMA
-  static FixedCol col_entry(void* fn, int nc, int ct, size_t smem, bool tma) {
+  static FixedCol col_entry(void* fn, int nc, int ct, size_t smem, int mode) {
     allow_max_dynamic_smem(fn);
-    FixedCol c{nc, ct, smem, fn, tma, tma_box_rows(H, nc)};
+    FixedCol c{nc, ct, smem, fn, mode != 0, tma_box_rows(H, nc), mode};
     return c;
+  }
+  static constexpr size_t col_smem(int nc, int mode) {
+    return mode >= 3 ? col_fx_smem_sep(H, nc, mode) : mode == 2 ? col_fx_smem_fpt(H, nc) : col_fx_smem(H, nc);
   }
   template <int NC, int CT, int MINB, int MODE>
   static FixedCol col() {
     void* fn = MODE ? (void*)k_col_tma_fx<CS, W, NC, CT, MINB, MODE> : (void*)k_col_fx<CS, W, NC, CT, MINB>;
-    return col_entry(fn, NC, CT, MODE == 2 ? col_fx_smem_fpt(H, NC) : col_fx_smem(H, NC), MODE != 0);
+    return col_entry(fn, NC, CT, col_smem(NC, MODE), MODE);
   }
   // the split column pass of forward units (NC columns, CT threads, MINB blocks)
   template <int NC, int CT, int MINB>
   static FixedCol col_fwd() {
-    return col_entry((void*)k_col_fwd_fx<CS, W, NC, CT, MINB>, NC, CT, col_fx_smem(H, NC), true);
+    return col_entry((void*)k_col_fwd_fx<CS, W, NC, CT, MINB>, NC, CT, col_fx_smem(H, NC), 1);
   }
-  template <int NC, int CT, int MINB>
+  template <int NC, int CT, int MINB, int MODE = 2>
   static FixedCol col_inv() {
-    return col_entry((void*)k_col_inv_fx<CS, W, NC, CT, MINB>, NC, CT, col_fx_smem_fpt(H, NC), true);
+    return col_entry((void*)k_col_inv_fx<CS, W, NC, CT, MINB, MODE>, NC, CT, col_smem(NC, MODE), MODE);
   }
   template <int PPB>
   static FixedRow row() {
@@ -1017,15 +1106,18 @@ struct ShapeDef {
     }
     return f;
   }
-  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, std::pair<FixedCol, FixedCol> split,
+  // split: the forward half, the inverse half (mode 2) and, optionally, the
+  // inverse half with the fingerprint strip in its own region (mode 3/4)
+  static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, std::vector<FixedCol> split,
                          FixedPersist ps) {
     FixedShape s{};
     s.W = W;
     s.H = H;
     s.rows = std::move(rows);
     s.cols = std::move(cols);
-    s.col_fwd = split.first;
-    s.col_inv = split.second;
+    s.col_fwd = split.at(0);
+    s.col_inv = split.at(1);
+    if (split.size() > 2) s.col_inv_sep = split[2];
     s.persist = ps;
     return s;
   }
@@ -1036,31 +1128,32 @@ std::vector<FixedShape> build_registry() {
   {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>, 160>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(), D::col<4, 240, 3, 0>(),
-                         D::col<8, 480, 1, 1>()},
-                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>()},
+                        {D::col<4, 240, 3, 3>(), D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(),
+                         D::col<4, 240, 3, 0>(), D::col<8, 480, 1, 1>()},
+                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>(), D::col_inv<4, 240, 3, 3>()},
                         D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(), D::col<8, 360, 2, 0>(),
-                         D::col<4, 180, 4, 2>()},
-                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>()},
+                        {D::col<8, 360, 2, 3>(), D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(),
+                         D::col<8, 360, 2, 0>(), D::col<4, 180, 4, 2>()},
+                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>(), D::col_inv<4, 180, 4, 3>()},
                         D::persist<160, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
-                        {D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(), D::col<4, 360, 2, 0>()},
-                        {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>()},
+                        {D::col<4, 360, 2, 4>(), D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(),
+                         D::col<4, 360, 2, 0>()},
+                        {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>(), D::col_inv<4, 360, 2, 4>()},
                         D::persist<256, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<256, 16, 16>, 32, Spec<256, 16, 16>>;
     v.push_back(D::make({D::row<4>(), D::row<2>()},
-                        {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>()},
-                        {D::col_fwd<16, 128, 4>(), D::col_inv<16, 128, 4>()},
+                        {D::col<16, 128, 4, 2>(), D::col<16, 128, 4, 0>(), D::col<16, 128, 4, 3>()},
+                        {D::col_fwd<16, 128, 4>(), D::col_inv<16, 128, 4>(), D::col_inv<16, 128, 4, 3>()},
                         D::persist<32, 8, 16>()));
   }
   cudaGetLastError();
@@ -1150,9 +1243,19 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   // and the inverse column FFT per candidate
   const bool units = a.units != nullptr || a.share > 1;
   const int nunits = units ? a.nunits : a.nitems;
-  const FixedCol& fv = fs.cols[std::max(0, std::min(col_variant, (int)fs.cols.size() - 1))];
-  // forward units take the split pass
-  const FixedCol& fc = units ? fs.col_inv : fv;
+  int v = std::max(0, std::min(col_variant, (int)fs.cols.size() - 1));
+  // a variant whose fingerprint region holds FP16 bins only (mode 4) steps
+  // aside for FP32 fingerprints: the first variant that copies FP32 bins by TMA
+  if (fs.cols[v].mode == 4 && a.fp_f32)
+    for (int k = 0; k < (int)fs.cols.size(); ++k)
+      if (fs.cols[k].mode == 2 || fs.cols[k].mode == 3) {
+        v = k;
+        break;
+      }
+  const FixedCol& fv = fs.cols[v];
+  // forward units take the split pass (its inverse half in the variant's fingerprint mode)
+  const bool sep = fv.mode >= 3 && fs.col_inv_sep.fn && (fs.col_inv_sep.mode == 3 || !a.fp_f32);
+  const FixedCol& fc = units ? (sep ? fs.col_inv_sep : fs.col_inv) : fv;
   const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};

@@ -17,6 +17,7 @@ struct FixedCol {
   void* fn;
   bool tma;
   int br;
+  int mode;   // 0 plain loads, 1 strip by TMA, 2 fingerprint by TMA into the strip buffer, 3/4 into its own region
 };
 
 // one instantiated pair of row kernels: row pairs per block, threads per pair
@@ -60,6 +61,8 @@ struct FixedShape {
   std::vector<FixedRow> rows;
   std::vector<FixedCol> cols;
   FixedCol col_fwd, col_inv; // the column pass split for forward units (k_col_fwd_fx, k_col_inv_fx)
+  FixedCol col_inv_sep;      // k_col_inv_fx with the fingerprint strip in its own region (mode 3/4), taken
+                             // with a column variant of that mode; fn null where none is instantiated
   FixedPersist persist;
   // the row kernels with `ppb` pairs per block, else the first variant
   const FixedRow& row_for(int ppb) const {

@@ -499,7 +499,7 @@ struct Server::Impl {
     int* hu = reinterpret_cast<int*>(slot.h_tab + 2 * kMaxWave);   // forward units' first slots
     int* hs = hu + kMaxWave + 1;                                      // unit of each slot
     int count = 0, nunits = 0;
-    bool grouped = false;
+    bool grouped = false, fp_f32 = false;
     std::vector<Query*> finished;
     for (auto& qp : best->second) {
       if (count >= wave) break;
@@ -524,6 +524,7 @@ struct Server::Impl {
         hu[nunits++] = count + u * S;
       }
       grouped = grouped || S > 1;
+      for (auto& f : q.fps) fp_f32 = fp_f32 || f->dtype == kF32;
       count += take;
       q.next += take;
       if (q.next == n) finished.push_back(&q);
@@ -558,6 +559,7 @@ struct Server::Impl {
     // forward units of several items: the unit table; else one item per unit
     a.units = grouped ? reinterpret_cast<const int*>(slot.d_tab + 2 * kMaxWave) : nullptr;
     a.unit_of = grouped ? a.units + kMaxWave + 1 : nullptr;
+    a.fp_f32 = fp_f32 ? 1 : 0;
     a.nunits = grouped ? nunits : count;
     a.share = 1;
     const FixedShape* fs = tn.variant >= 0 ? find_fixed(H, W) : nullptr;
