@@ -1107,7 +1107,8 @@ struct ShapeDef {
     return f;
   }
   // split: the forward half, the inverse half (mode 2) and, optionally, the
-  // inverse half with the fingerprint strip in its own region (mode 3/4)
+  // inverse half with the fingerprint strip in its own region (mode 3/4) and
+  // the one for FP16 fingerprints only (mode 4, more blocks per SM)
   static FixedShape make(std::vector<FixedRow> rows, std::vector<FixedCol> cols, std::vector<FixedCol> split,
                          FixedPersist ps) {
     FixedShape s{};
@@ -1118,6 +1119,7 @@ struct ShapeDef {
     s.col_fwd = split.at(0);
     s.col_inv = split.at(1);
     if (split.size() > 2) s.col_inv_sep = split[2];
+    if (split.size() > 3) s.col_inv_h = split[3];
     s.persist = ps;
     return s;
   }
@@ -1130,15 +1132,17 @@ std::vector<FixedShape> build_registry() {
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<4, 240, 3, 3>(), D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(),
                          D::col<4, 240, 3, 0>(), D::col<8, 480, 1, 1>()},
-                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>(), D::col_inv<4, 240, 3, 3>()},
+                        {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>(), D::col_inv<4, 240, 3, 3>(),
+                         D::col_inv<4, 240, 4, 4>()},
                         D::persist<192, 2, 4>()));
   }
   {
     using D = ShapeDef<Spec<1280, 16, 10, 8>, 160, Spec<720, 9, 10, 8>>;
     v.push_back(D::make({D::row<2>(), D::row<1>()},
                         {D::col<8, 360, 2, 3>(), D::col<8, 360, 2, 1>(), D::col<8, 360, 2, 2>(),
-                         D::col<8, 360, 2, 0>(), D::col<4, 180, 4, 2>()},
-                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>(), D::col_inv<4, 180, 4, 3>()},
+                         D::col<8, 360, 2, 0>(), D::col<4, 180, 4, 2>(), D::col<8, 360, 3, 4>()},
+                        {D::col_fwd<4, 180, 4>(), D::col_inv<4, 180, 4>(), D::col_inv<4, 180, 4, 3>(),
+                         D::col_inv<4, 180, 5, 4>()},
                         D::persist<160, 2, 4>()));
   }
   {
@@ -1255,7 +1259,8 @@ void launch_fixed_wave(const PassArgs& a, const FixedShape& fs, int col_variant,
   const FixedCol& fv = fs.cols[v];
   // forward units take the split pass (its inverse half in the variant's fingerprint mode)
   const bool sep = fv.mode >= 3 && fs.col_inv_sep.fn && (fs.col_inv_sep.mode == 3 || !a.fp_f32);
-  const FixedCol& fc = units ? (sep ? fs.col_inv_sep : fs.col_inv) : fv;
+  const bool sep_h = fv.mode >= 3 && fs.col_inv_h.fn && !a.fp_f32;
+  const FixedCol& fc = units ? (sep_h ? fs.col_inv_h : sep ? fs.col_inv_sep : fs.col_inv) : fv;
   const FixedRow& fr = fs.row_for(a.pairs_per_block);
   const int Wh = a.W / 2;
   void* args[] = {const_cast<PassArgs*>(&a)};

@@ -63,6 +63,8 @@ struct FixedShape {
   FixedCol col_fwd, col_inv; // the column pass split for forward units (k_col_fwd_fx, k_col_inv_fx)
   FixedCol col_inv_sep;      // k_col_inv_fx with the fingerprint strip in its own region (mode 3/4), taken
                              // with a column variant of that mode; fn null where none is instantiated
+  FixedCol col_inv_h;        // the same with a region for FP16 bins (mode 4) and more blocks per SM, taken
+                             // instead when every fingerprint of the wave is FP16; fn null where none
   FixedPersist persist;
   // the row kernels with `ppb` pairs per block, else the first variant
   const FixedRow& row_for(int ppb) const {

@@ -9,7 +9,10 @@ from is a launch choice only:
 * mode 4 does the same with a region sized for FP16 bins.  A wave with an FP32
   fingerprint then takes the first mode-2/3 variant.
 
-Each bin's arithmetic is the same in all three, so every PCE, arg-max node
+With the shared forward pass and FP16 fingerprints only, the split inverse
+half runs a mode-4 kernel with more blocks per SM at 720p and 1080p.
+
+Each bin's arithmetic is the same in all of them, so every PCE, arg-max node
 and shift must match bit for bit.  The test covers every planned frame size,
 FP32 and FP16 fingerprints, and the shared forward pass on and off."""
 import numpy as np
