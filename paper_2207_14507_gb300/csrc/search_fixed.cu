@@ -786,6 +786,14 @@ __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
   row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
+// the same with registers allocated for MINB resident blocks per SM (a
+// separate kernel: an explicit bound of 1 changes the allocation of the
+// unbounded one)
+template <class SP, int T, int PPB, int MINB>
+__global__ void __launch_bounds__(T * PPB, MINB) k_row_inverse_mb(PassArgs a) {
+  extern __shared__ float4 smem4[];
+  row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
+}
 
 // ---------------------------------------------------------------- persistent kernel
 
@@ -1058,7 +1066,8 @@ struct ShapeDef {
   static FixedCol col_inv() {
     return col_entry((void*)k_col_inv_fx<CS, W, NC, CT, MINB, MODE>, NC, CT, col_smem(NC, MODE), MODE);
   }
-  template <int PPB>
+  // RIMB: resident row-inverse blocks per SM to allocate registers for (0: no bound)
+  template <int PPB, int RIMB = 0>
   static FixedRow row() {
     FixedRow r{};
     r.ppb = PPB;
@@ -1070,7 +1079,8 @@ struct ShapeDef {
     r.fwd[kBF16] = (void*)k_row_forward_fx<kBF16, RS, RT, PPB>;
     r.fwd[kF16P] = (void*)k_row_forward_fx<kF16P, RS, RT, PPB>;
     r.fwd[kBF16P] = (void*)k_row_forward_fx<kBF16P, RS, RT, PPB>;
-    r.inv = (void*)k_row_inverse_fx<RS, RTI, PPB>;
+    if constexpr (RIMB > 0) r.inv = (void*)k_row_inverse_mb<RS, RTI, PPB, RIMB>;
+    else r.inv = (void*)k_row_inverse_fx<RS, RTI, PPB>;
     r.fin = (void*)k_finalize_fx<RS, RTI, kFinPairs>;
     r.fin_threads = RTI * kFinPairs;
     r.fin_smem = row_fx_smem<W>(kFinPairs);
@@ -1080,7 +1090,7 @@ struct ShapeDef {
     allow(k_row_forward_fx<kBF16, RS, RT, PPB>);
     allow(k_row_forward_fx<kF16P, RS, RT, PPB>);
     allow(k_row_forward_fx<kBF16P, RS, RT, PPB>);
-    allow(k_row_inverse_fx<RS, RTI, PPB>);
+    allow_max_dynamic_smem(r.inv);
     return r;
   }
   // PRT threads per row pair (PRT * PPB per block, also the column task's
@@ -1129,7 +1139,7 @@ std::vector<FixedShape> build_registry() {
   std::vector<FixedShape> v;
   {
     using D = ShapeDef<Spec<1920, 16, 12, 10>, 192, Spec<1080, 9, 12, 10>, 160>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()},
+    v.push_back(D::make({D::row<2>(), D::row<1, 8>()},
                         {D::col<4, 240, 3, 3>(), D::col<4, 240, 3, 2>(), D::col<4, 240, 3, 1>(),
                          D::col<4, 240, 3, 0>(), D::col<8, 480, 1, 1>()},
                         {D::col_fwd<4, 240, 3>(), D::col_inv<4, 240, 3>(), D::col_inv<4, 240, 3, 3>(),
@@ -1147,7 +1157,7 @@ std::vector<FixedShape> build_registry() {
   }
   {
     using D = ShapeDef<Spec<3840, 16, 16, 15>, 256, Spec<2160, 15, 12, 12>>;
-    v.push_back(D::make({D::row<2>(), D::row<1>()},
+    v.push_back(D::make({D::row<2>(), D::row<1, 5>()},
                         {D::col<4, 360, 2, 4>(), D::col<4, 360, 2, 2>(), D::col<4, 360, 2, 1>(),
                          D::col<4, 360, 2, 0>()},
                         {D::col_fwd<4, 360, 2>(), D::col_inv<4, 360, 2>(), D::col_inv<4, 360, 2, 4>()},
