@@ -384,8 +384,30 @@ int query_poll(prnu_ctx* ctx, uint64_t qid, prnu_result* out, int64_t timeout_us
  * host memory (total_ms), in milliseconds.  Errors: PRNU_ENOTFOUND. */
 int query_latency(prnu_ctx* ctx, uint64_t qid, double* queued_ms, double* total_ms);
 
+/* Request loop of the server.  PRNU_LOOP_HOST: a host thread forms every
+ * wave (its candidate, result and frame tables) and launches its kernels.
+ * PRNU_LOOP_DEVICE: for frame sizes with compile-time-planned kernels, the
+ * loop runs on the GPU.  One CUDA graph per frame size and storage type
+ * repeats, in a WHILE node:
+ *  - a scheduler kernel takes the next candidates of the admitted queries
+ *    (whole forward units, in admission order) from a host-mapped ring and
+ *    builds the wave's tables on the device;
+ *  - the wave kernels run, in the shared-forward or plain branch of an
+ *    IF/ELSE node;
+ *  - a completion kernel writes the arg-max of each query the wave finished
+ *    into host-mapped memory and raises its done flag.
+ * The host thread only admits queries (device memory, ingest, one ring entry
+ * each).  It relaunches a size's graph when it has drained or used its
+ * budget of 32 waves, so sizes take turns.  Other sizes take host waves.
+ * Results are bit-identical in both modes.  Set the mode before the
+ * context's first query_submit: PRNU_EINVAL afterwards (unless unchanged) or
+ * for an unknown mode. */
+enum { PRNU_LOOP_HOST = 0, PRNU_LOOP_DEVICE = 1 };
+int prnu_server_set_loop(prnu_ctx* ctx, int mode);
+
 /* Serving statistics since creation: completed queries, candidates scored,
- * launches issued by the server, and the peak device bytes admitted. */
+ * launches issued by the server (with the device loop: graph launches, plus
+ * the ingest kernels), and the peak device bytes admitted. */
 typedef struct {
     uint64_t queries_done, candidates_done, server_launches;
     uint64_t admitted_bytes_peak, admitted_bytes_now;

@@ -19,6 +19,7 @@ PRNU_OK, PRNU_EINVAL, PRNU_ENOMEM, PRNU_ECUDA, PRNU_EAGAIN, PRNU_ETIMEOUT, PRNU_
 PRNU_F32, PRNU_F16, PRNU_BF16 = 0, 1, 2
 PRNU_WEIGHT_BY_INTENSITY, PRNU_NORMALISE = 1, 2
 PRNU_DEBUG_STALL_DEVICE_WAITS = 1
+PRNU_LOOP_HOST, PRNU_LOOP_DEVICE = 0, 1
 STATUS_NAMES = {0: "PRNU_OK", 1: "PRNU_EINVAL", 2: "PRNU_ENOMEM", 3: "PRNU_ECUDA", 4: "PRNU_EAGAIN",
                 5: "PRNU_ETIMEOUT", 6: "PRNU_ENOTFOUND", 7: "PRNU_EDEVICE_ABORT"}
 
@@ -102,6 +103,7 @@ _SIGNATURES = {
     "query_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
     "query_latency": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "prnu_server_stats_get": (C.c_int, [_P, C.POINTER(prnu_server_stats)]),
+    "prnu_server_set_loop": (C.c_int, [_P, C.c_int]),
     "prnu_get_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
     "prnu_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(prnu_tuning)]),
     "prnu_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(prnu_tuning), _P]),
@@ -410,6 +412,10 @@ class Context:
         qm, tm = C.c_double(), C.c_double()
         _check(lib().query_latency(self.h, qid, C.byref(qm), C.byref(tm)), "query_latency")
         return dict(queued_ms=qm.value, total_ms=tm.value)
+
+    def prnu_server_set_loop(self, mode):
+        """PRNU_LOOP_HOST or PRNU_LOOP_DEVICE; before the first query_submit."""
+        _check(lib().prnu_server_set_loop(self.h, int(mode)), "prnu_server_set_loop")
 
     def prnu_server_stats_get(self) -> dict:
         s = prnu_server_stats()

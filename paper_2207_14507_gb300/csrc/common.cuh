@@ -96,7 +96,18 @@ struct PassArgs {
   int share;
   // host-side: some fingerprint of the pass is stored FP32 (launch choices only)
   int fp_f32;
+  // Device-side counts of a launch whose grid was sized for nitems / nunits
+  // slots ahead of time (the query server's device-resident loop): [0] the
+  // wave's items, [1] its forward units; blocks past them return at once.
+  // nullptr: the grid is exact.
+  const int* d_counts;
 };
+
+// whether block `b` of a grid over the wave's items (k = 0) or forward units
+// (k = 1) lies past the wave's device-side count
+__device__ __forceinline__ bool past_count(const PassArgs& a, int b, int k) {
+  return a.d_counts != nullptr && b >= __ldcg(a.d_counts + k);
+}
 
 __device__ __forceinline__ int unit_first(const PassArgs& a, int u) { return a.units ? a.units[u] : u * a.share; }
 __device__ __forceinline__ int unit_of_slot(const PassArgs& a, int s) { return a.unit_of ? a.unit_of[s] : s / a.share; }

@@ -221,36 +221,8 @@ __global__ void k_argmax(const CandResult* __restrict__ res, const WorkItem* __r
                          const int* __restrict__ gstart, int ngroups, int share, prnu_result* __restrict__ out,
                          int H, int W) {
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   if (g >= ngroups) return;
-  const int f = g / share;
-  const int b = gstart[f] + (g - f * share), n = (gstart[f + 1] - gstart[f]) / share;
-  double bv = -INFINITY;
-  int bi = INT_MAX;
-  for (int k = lane; k < n; k += 32) {
-    const int i = b + k * share;
-    better_d(bv, bi, res[i].pce, i);
-  }
-  warp_maxarg_d(bv, bi);
-  if (lane == 0) {
-    prnu_result r;
-    if (bi == INT_MAX || n == 0) {
-      r.lam = 0.f; r.th_deg = 0.f; r.dy = 0; r.dx = 0; r.pce = 0.0; r.peak = 0.f; r.cand_idx = -1;
-    } else {
-      const CandResult c = res[bi];
-      const WorkItem it = items[bi];
-      r.lam = it.lam;
-      r.th_deg = it.th_deg;
-      r.dy = c.py < (H + 1) / 2 ? c.py : c.py - H;
-      r.dx = c.px < (W + 1) / 2 ? c.px : c.px - W;
-      if (2 * c.py == H) r.dy = -H / 2;
-      if (2 * c.px == W) r.dx = -W / 2;
-      r.pce = c.pce;
-      r.peak = c.peak;
-      r.cand_idx = c.cand;
-    }
-    out[g] = r;
-  }
+  argmax_group(res, items, gstart, share, out, H, W, g, threadIdx.x & 31);
 }
 
 __global__ void k_scatter_all(const CandResult* __restrict__ res, int n, int cmax, double* __restrict__ all) {

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "prnu.h"
 
 namespace prnu {
 
@@ -46,6 +47,43 @@ __device__ __forceinline__ void warp_maxarg_d(double& v, int& i) {
     double v2 = __shfl_xor_sync(0xffffffffu, v, o);
     int i2 = __shfl_xor_sync(0xffffffffu, i, o);
     better_d(v, i, v2, i2);
+  }
+}
+
+// The best candidate of group g (one frame and fingerprint), by one warp
+// (lane = its lane): the highest PCE, the lowest index among equal ones
+// (candidates gstart[f] + (g - f*share) + k*share of frame f = g / share),
+// its (lam, theta), cyclic peak as a signed shift, PCE and peak, into out[g].
+__device__ __forceinline__ void argmax_group(const CandResult* __restrict__ res, const WorkItem* __restrict__ items,
+                                             const int* __restrict__ gstart, int share, prnu_result* out, int H,
+                                             int W, int g, int lane) {
+  const int f = g / share;
+  const int b = gstart[f] + (g - f * share), n = (gstart[f + 1] - gstart[f]) / share;
+  double bv = -INFINITY;
+  int bi = INT_MAX;
+  for (int k = lane; k < n; k += 32) {
+    const int i = b + k * share;
+    better_d(bv, bi, res[i].pce, i);
+  }
+  warp_maxarg_d(bv, bi);
+  if (lane == 0) {
+    prnu_result r;
+    if (bi == INT_MAX || n == 0) {
+      r.lam = 0.f; r.th_deg = 0.f; r.dy = 0; r.dx = 0; r.pce = 0.0; r.peak = 0.f; r.cand_idx = -1;
+    } else {
+      const CandResult c = res[bi];
+      const WorkItem it = items[bi];
+      r.lam = it.lam;
+      r.th_deg = it.th_deg;
+      r.dy = c.py < (H + 1) / 2 ? c.py : c.py - H;
+      r.dx = c.px < (W + 1) / 2 ? c.px : c.px - W;
+      if (2 * c.py == H) r.dy = -H / 2;
+      if (2 * c.px == W) r.dx = -W / 2;
+      r.pce = c.pce;
+      r.peak = c.peak;
+      r.cand_idx = c.cand;
+    }
+    out[g] = r;
   }
 }
 __device__ __forceinline__ double warp_sum(double s) {

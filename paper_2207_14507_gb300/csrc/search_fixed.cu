@@ -745,6 +745,7 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
   const bool units = a.units || a.share > 1;
   const int u = blockIdx.y;
+  if (past_count(a, u, units ? 1 : 0)) return;
   row_forward_body<DT, SP, T, PPB>(a, units ? unit_first(a, u) : u, units ? a.nitems + u : u, blockIdx.x,
                                    reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
@@ -752,12 +753,14 @@ __global__ void __launch_bounds__(T * PPB) k_row_forward_fx(PassArgs a) {
 template <class SP, int W, int NC, int T, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_col_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
+  if (past_count(a, blockIdx.y, 0)) return;
   col_body<SP, W, NC, T>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4));
 }
 
 template <class SP, int W, int NC, int T, int MINB, int MODE>
 __global__ void __launch_bounds__(T, MINB) k_col_tma_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(1024) float4 smem4t[];
+  if (past_count(a, blockIdx.y, 0)) return;
   col_body<SP, W, NC, T, false, MODE>(a, blockIdx.y, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4t),
                                       &map);
 }
@@ -770,6 +773,7 @@ template <class SP, int W, int NC, int T, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_col_fwd_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(1024) float4 smem4f[];
   const int u = blockIdx.y;
+  if (past_count(a, u, 1)) return;
   col_body<SP, W, NC, T, false, 1, 1>(a, unit_first(a, u), a.nitems + u, blockIdx.x,
                                       reinterpret_cast<float2*>(smem4f), &map);
 }
@@ -777,6 +781,7 @@ template <class SP, int W, int NC, int T, int MINB, int MODE>
 __global__ void __launch_bounds__(T, MINB) k_col_inv_fx(PassArgs a, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(1024) float4 smem4i[];
   const int s = blockIdx.y;
+  if (past_count(a, s, 0)) return;
   col_body<SP, W, NC, T, false, MODE, 2>(a, s, s, blockIdx.x, reinterpret_cast<float2*>(smem4i), &map,
                                          a.nitems + unit_of_slot(a, s));
 }
@@ -784,6 +789,7 @@ __global__ void __launch_bounds__(T, MINB) k_col_inv_fx(PassArgs a, const __grid
 template <class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
   extern __shared__ float4 smem4[];
+  if (past_count(a, blockIdx.y, 0)) return;
   row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
 // the same with registers allocated for MINB resident blocks per SM (a
@@ -792,6 +798,7 @@ __global__ void __launch_bounds__(T * PPB) k_row_inverse_fx(PassArgs a) {
 template <class SP, int T, int PPB, int MINB>
 __global__ void __launch_bounds__(T * PPB, MINB) k_row_inverse_mb(PassArgs a) {
   extern __shared__ float4 smem4[];
+  if (past_count(a, blockIdx.y, 0)) return;
   row_inverse_body<SP, T, PPB>(a, blockIdx.y, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
 }
 
@@ -916,6 +923,7 @@ __device__ __forceinline__ void finalize_task(const PassArgs& a, int is, int ws,
 // window recomputed at a time.
 template <class SP, int T, int PPB>
 __global__ void __launch_bounds__(T * PPB) k_finalize_fx(PassArgs a) {
+  if (past_count(a, blockIdx.x, 0)) return;
   extern __shared__ float4 smem4[];
   finalize_task<SP, T, PPB>(a, blockIdx.x, blockIdx.x, reinterpret_cast<float2*>(smem4), threadIdx.x);
 }

@@ -17,10 +17,26 @@
 // tables (item, result, residual frame), so the kernels are those of
 // eis_grid_search and a query's results do not depend on what it was batched
 // with.
+//
+// Two request loops run the waves (prnu_server_set_loop):
+//  host   : the server thread forms each wave's tables and launches its
+//           kernels;
+//  device : for frame sizes with compile-time-planned kernels, one CUDA graph
+//           per size class holds the whole loop.  A WHILE node repeats a body:
+//           a scheduler kernel takes the next candidates of the ready queries
+//           from a host-mapped ring, builds the wave tables on the device and
+//           picks the shared-forward or plain branch of an IF/ELSE node that
+//           holds the wave kernels.  A completion kernel then writes the
+//           arg-max of every query the wave finished into host-mapped memory
+//           and raises its done flag.  The host thread only admits queries
+//           (memory, ingest, one ring entry each), relaunches a size class's
+//           graph when it has drained or used its wave budget, and reports
+//           queries whose done flag is up.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
 
+#include "search_common.cuh"
 #include "search_fixed.h"
 #include "server.h"
 
@@ -55,9 +71,127 @@ __global__ void k_set_frame_ptrs(const void** __restrict__ dst, const char* __re
 
 __global__ void k_set_fpdesc(FpDesc* __restrict__ dst, FpDesc v) { *dst = v; }
 
+// ---------------------------------------------------------------- device-resident loop
+
+constexpr int kRing = 1024;       // queries of one size class admitted and not yet reported
+constexpr int kLoopWaves = 32;    // waves per launch of a size class's loop
+
+// One admitted query as the device scheduler sees it (an entry of a
+// host-mapped ring; its ready and done flags are in host-mapped arrays indexed
+// like the ring).
+struct DevRun {
+  const WorkItem* items;    // device [n]
+  CandResult* results;      // device [n]
+  const int* groups;        // device group table (SearchCall::group_start)
+  prnu_result* out;         // host-mapped [ngroups]
+  int n;                    // candidates
+  int share;                // fingerprints per forward unit (1: none)
+  int ngroups;              // F * P
+  int pad;
+};
+
+// Device state of one size class's loop.
+struct DevSched {
+  int head;                 // ring position of the first query not fully scheduled
+  int next;                 // its next candidate
+  int waves;                // waves run by the current launch
+  int counts[2];            // the current wave's items and forward units (PassArgs::d_counts)
+  int ncomplete;            // queries whose last candidates are in the current wave
+  int complete[kMaxWave];   // their ring positions
+};
+
+__device__ __forceinline__ int ld_acquire_sys(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(int* p, int v) {
+  asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void k_loop_begin(DevSched* st) { st->waves = 0; }
+
+// the query's ingest (frames, residual, work list) is complete
+__global__ void k_mark_ready(int* ready) {
+  __threadfence_system();
+  st_release_sys(ready, 1);
+}
+
+// One wave: up to `wave` candidates of the ready queries in ring order, whole
+// forward units only, into the wave tables; the loop goes on while it found
+// candidates and the launch's wave budget lasts.  One thread.
+__global__ void k_sched(DevSched* st, const DevRun* ring, const int* tail_p, const int* ready, int wave,
+                        const WorkItem** item_ptrs, CandResult** result_ptrs, int* units, int* unit_of,
+                        cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_units) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int tail = ld_acquire_sys(tail_p);
+  int head = st->head, next = st->next, count = 0, nunits = 0, ncomp = 0;
+  bool grouped = false;
+  while (count < wave && ncomp < kMaxWave && head != tail) {
+    const int slot = head % kRing;
+    if (ld_acquire_sys(ready + slot) == 0) break;   // ingest still running: keep arrival order
+    const DevRun r = ring[slot];
+    if (r.n <= 0) {                                  // nothing to score: complete at once
+      st->complete[ncomp++] = head;
+      ++head;
+      next = 0;
+      continue;
+    }
+    const int S = max(r.share, 1);
+    const int take = min(wave - count, r.n - next) / S * S;
+    if (take == 0) break;
+    for (int k = 0; k < take; ++k) {
+      item_ptrs[count + k] = r.items + next + k;
+      result_ptrs[count + k] = r.results + next + k;
+    }
+    for (int u = 0; u < take / S; ++u) {
+      units[nunits] = count + u * S;
+      for (int k = 0; k < S; ++k) unit_of[count + u * S + k] = nunits;
+      ++nunits;
+    }
+    grouped = grouped || S > 1;
+    count += take;
+    next += take;
+    if (next == r.n) {
+      st->complete[ncomp++] = head;
+      ++head;
+      next = 0;
+    }
+  }
+  units[nunits] = count;
+  st->head = head;
+  st->next = next;
+  st->counts[0] = count;
+  st->counts[1] = grouped ? nunits : count;
+  st->ncomplete = ncomp;
+  const int waves = st->waves + 1;
+  st->waves = waves;
+  __threadfence();
+  cudaGraphSetConditional(h_units, grouped ? 1u : 0u);
+  cudaGraphSetConditional(h_loop, count > 0 && waves < kLoopWaves ? 1u : 0u);
+}
+
+// The arg-max of every query the wave finished, into its host-mapped results,
+// then its done flag.  One block per finished query.
+__global__ void k_complete(const DevSched* st, const DevRun* ring, int* done, int H, int W) {
+  const int c = blockIdx.x;
+  if (c >= st->ncomplete) return;
+  const int slot = st->complete[c] % kRing;
+  const DevRun r = ring[slot];
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int g = threadIdx.x >> 5; g < r.ngroups; g += nw)
+    argmax_group(r.results, r.items, r.groups, max(r.share, 1), r.out, H, W, g, lane);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    st_release_sys(done + slot, 1);
+  }
+}
+
 }  // namespace
 
 struct Server::Impl {
+  struct DevLoop;
   struct Query {
     uint64_t id = 0;
     int F = 0, H = 0, W = 0, P = 0, dtype = 0, flags = 0;
@@ -88,7 +222,9 @@ struct Server::Impl {
     prnu_result* h_out = nullptr;  // pinned
     int arena_block = -1;
     std::vector<prnu_result> results;
-    std::atomic<int> gpu_done{0};  // set by the stream callback
+    std::atomic<int> gpu_done{0};  // set by the stream callback (host loop) or on the done flag (device loop)
+    DevLoop* loop = nullptr;       // device loop of its size class, or nullptr (host waves)
+    long long ring_pos = -1;       // its position in that loop's ring
     bool reported = false;         // results copied out, resources released
     bool failed = false;
     int err = PRNU_OK;
@@ -138,6 +274,39 @@ struct Server::Impl {
   size_t ws_spec_bytes = 0, ws_stats_bytes = 0;
   prnu_server_stats st{};
 
+  // The device-resident loop of one size class: its graph, its scheduler
+  // state and wave tables (device), and the ring of admitted queries with
+  // their ready and done flags (host-mapped).
+  struct DevLoop {
+    SizeKey key{};
+    Tuning tn{};
+    const FixedShape* fs = nullptr;
+    int wave = 0;
+    char* dmem = nullptr;
+    size_t dbytes = 0;
+    DevSched* d_st = nullptr;
+    const WorkItem** d_items = nullptr;
+    CandResult** d_results = nullptr;
+    int* d_units = nullptr;
+    int* d_unit_of = nullptr;
+    DevRun* ring = nullptr;        // host pointer
+    DevRun* d_ring = nullptr;      // its device pointer
+    int* flags = nullptr;          // host pointer: tail, ready[kRing], done[kRing]
+    int* d_flags = nullptr;
+    long long appended = 0;
+    std::deque<std::shared_ptr<Query>> runs;   // appended, not yet reported (ring order)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t built_gen = ~(size_t)0;
+    bool dead = false;             // a launch failed: no further use
+  };
+  bool dev_mode = false;
+  std::map<SizeKey, std::unique_ptr<DevLoop>> loops;   // nullptr: no planned kernels, host waves
+  cudaStream_t s_cap = nullptr;
+  cudaEvent_t loop_ev = nullptr;
+  bool loop_running = false;
+  size_t ws_gen = 0;               // workspace generation (graphs hold its pointers)
+
   explicit Impl(prnu_ctx* c) : ctx(c) {
     PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_comp, cudaStreamNonBlocking));
     PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_copy, cudaStreamNonBlocking));
@@ -151,7 +320,13 @@ struct Server::Impl {
     d_frame_ptrs = reinterpret_cast<const void**>(ctx_alloc(ctx, sizeof(void*) * kMaxFrameSlots));
     d_scale = reinterpret_cast<float*>(ctx_alloc(ctx, sizeof(float) * kMaxFrameSlots));
     d_fpdesc = reinterpret_cast<FpDesc*>(ctx_alloc(ctx, sizeof(FpDesc) * kMaxFpSlots));
-    PRNU_CUDA_TRY(cudaHostAlloc((void**)&arena, kArenaBlock * kArenaBlocks, cudaHostAllocDefault));
+    // mapped: the device loop's completion kernel writes query results here
+    PRNU_CUDA_TRY(cudaHostAlloc((void**)&arena, kArenaBlock * kArenaBlocks, cudaHostAllocMapped));
+    dev_mode = ctx->server_loop == PRNU_LOOP_DEVICE;
+    if (dev_mode) {
+      PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_cap, cudaStreamNonBlocking));
+      PRNU_CUDA_TRY(cudaEventCreateWithFlags(&loop_ev, cudaEventDisableTiming));
+    }
     for (auto& w : waves) {
       PRNU_CUDA_TRY(cudaHostAlloc((void**)&w.h_tab, kWaveTabBytes, cudaHostAllocDefault));
       w.d_tab = reinterpret_cast<void**>(ctx_alloc(ctx, kWaveTabBytes));
@@ -172,6 +347,17 @@ struct Server::Impl {
     cudaStreamSynchronize(s_comp);
     for (auto& q : admitted) release(*q);
     cudaStreamSynchronize(s_comp);
+    for (auto& kv : loops) {
+      DevLoop* L = kv.second.get();
+      if (!L) continue;
+      if (L->exec) cudaGraphExecDestroy(L->exec);
+      if (L->graph) cudaGraphDestroy(L->graph);
+      if (L->dmem) ctx_free(ctx, L->dmem, L->dbytes);
+      if (L->ring) cudaFreeHost(L->ring);
+      if (L->flags) cudaFreeHost(L->flags);
+    }
+    if (s_cap) cudaStreamDestroy(s_cap);
+    if (loop_ev) cudaEventDestroy(loop_ev);
     for (auto& w : waves) {
       cudaFreeHost(w.h_tab);
       ctx_free(ctx, w.d_tab, kWaveTabBytes);
@@ -364,6 +550,7 @@ struct Server::Impl {
     if (ws_stats) ctx_free(ctx, ws_stats, ws_stats_bytes);
     ws_spec = nullptr;
     ws_stats = nullptr;
+    ++ws_gen;   // device loops rebuild their graphs before the next launch
     ws_spec_bytes = std::max(sb, ws_spec_bytes);
     ws_stats_bytes = std::max(tb, ws_stats_bytes);
     ws_spec = reinterpret_cast<float2*>(ctx_alloc(ctx, ws_spec_bytes));
@@ -373,8 +560,12 @@ struct Server::Impl {
   // Admit the head of the queue; false if it does not fit yet.
   bool admit(const std::shared_ptr<Query>& qp) {
     Query& q = *qp;
-    const int wave = std::max(1, std::min(q.tn.wave, kMaxWave));
-    ensure_workspace(q.H, q.W, (q.call.share > 1 ? 2 : 1) * wave, wave);
+    DevLoop* L = dev_mode ? loop_for(q) : nullptr;   // nullptr: host waves
+    if (L && (int)L->runs.size() >= kRing) return false;
+    const int wave = L ? L->wave : std::max(1, std::min(q.tn.wave, kMaxWave));
+    // spectra: the wave's candidates, then one slot per forward unit (the
+    // device loop's graph always holds the shared-forward branch)
+    ensure_workspace(q.H, q.W, (L || q.call.share > 1 ? 2 : 1) * wave, wave);
     if (ctx->used.load() + q.bytes > ctx->budget) return false;
     const int slot0 = alloc_frames(q.F);
     if (slot0 < 0) return false;
@@ -393,7 +584,7 @@ struct Server::Impl {
         return false;
       }
     } else {
-      PRNU_CUDA_TRY(cudaHostAlloc((void**)&q.h_out, outb, cudaHostAllocDefault));
+      PRNU_CUDA_TRY(cudaHostAlloc((void**)&q.h_out, outb, cudaHostAllocMapped));
     }
     for (auto& f : q.fps) {
       const int s = take_fp_slot(f);
@@ -465,8 +656,229 @@ struct Server::Impl {
     st.server_launches += 5;
     q.t_admit = Clock::now();
     admitted.push_back(qp);
-    active[SizeKey{q.H, q.W, q.dtype}].push_back(qp);
+    if (L) {
+      append_run(*L, qp);
+    } else {
+      active[SizeKey{q.H, q.W, q.dtype}].push_back(qp);
+    }
     return true;
+  }
+
+  // ---------------------------------------------------------------- device loop (holds mu)
+
+  // The device loop of q's size class; nullptr where the size has no planned
+  // kernels for q's tuning (its queries take host waves).
+  DevLoop* loop_for(const Query& q) {
+    const SizeKey key{q.H, q.W, q.dtype};
+    auto it = loops.find(key);
+    if (it != loops.end()) return it->second.get();
+    const FixedShape* fs = q.tn.variant >= 0 ? find_fixed(q.H, q.W) : nullptr;
+    if (!fs || !fixed_supports(*fs, q.H, q.tn.ppb)) {
+      loops[key] = nullptr;
+      return nullptr;
+    }
+    auto L = std::make_unique<DevLoop>();
+    L->key = key;
+    L->tn = q.tn;
+    L->fs = fs;
+    L->wave = std::max(1, std::min(q.tn.wave, kMaxWave));
+    const size_t o_items = align256(sizeof(DevSched));
+    const size_t o_results = o_items + align256(sizeof(void*) * kMaxWave);
+    const size_t o_units = o_results + align256(sizeof(void*) * kMaxWave);
+    const size_t o_unit_of = o_units + align256(sizeof(int) * (kMaxWave + 1));
+    L->dbytes = o_unit_of + align256(sizeof(int) * kMaxWave);
+    L->dmem = reinterpret_cast<char*>(ctx_alloc(ctx, L->dbytes));
+    PRNU_CUDA_TRY(cudaMemset(L->dmem, 0, L->dbytes));
+    L->d_st = reinterpret_cast<DevSched*>(L->dmem);
+    L->d_items = reinterpret_cast<const WorkItem**>(L->dmem + o_items);
+    L->d_results = reinterpret_cast<CandResult**>(L->dmem + o_results);
+    L->d_units = reinterpret_cast<int*>(L->dmem + o_units);
+    L->d_unit_of = reinterpret_cast<int*>(L->dmem + o_unit_of);
+    PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->ring, sizeof(DevRun) * kRing, cudaHostAllocMapped));
+    PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->flags, sizeof(int) * (1 + 2 * kRing), cudaHostAllocMapped));
+    memset(L->ring, 0, sizeof(DevRun) * kRing);
+    memset(L->flags, 0, sizeof(int) * (1 + 2 * kRing));
+    PRNU_CUDA_TRY(cudaHostGetDevicePointer((void**)&L->d_ring, L->ring, 0));
+    PRNU_CUDA_TRY(cudaHostGetDevicePointer((void**)&L->d_flags, L->flags, 0));
+    DevLoop* r = L.get();
+    loops[key] = std::move(L);
+    return r;
+  }
+
+  // Append an admitted query to its loop's ring: flags cleared, entry
+  // written, ready raised on the copy stream after its ingest, then the tail
+  // moved (the scheduler reads the tail, then the entry).
+  void append_run(DevLoop& L, const std::shared_ptr<Query>& qp) {
+    Query& q = *qp;
+    const int slot = (int)(L.appended % kRing);
+    volatile int* fl = L.flags;
+    fl[1 + slot] = 0;
+    fl[1 + kRing + slot] = 0;
+    DevRun r{};
+    r.items = q.d_items;
+    r.results = q.d_results;
+    r.groups = q.d_groups;
+    PRNU_CUDA_TRY(cudaHostGetDevicePointer((void**)&r.out, q.h_out, 0));
+    r.n = (int)q.call.items.size();
+    r.share = std::max(q.call.share, 1);
+    r.ngroups = q.F * q.P;
+    L.ring[slot] = r;
+    k_mark_ready<<<1, 1, 0, s_copy>>>(L.d_flags + 1 + slot);
+    PRNU_CUDA_TRY(cudaGetLastError());
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    q.loop = &L;
+    q.ring_pos = L.appended;
+    ++L.appended;
+    fl[0] = (int)L.appended;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    L.runs.push_back(qp);
+  }
+
+  // The wave kernels of one branch of the loop body, captured into `into`:
+  // grids sized for a full wave, the live counts read on the device.
+  void capture_wave(DevLoop& L, cudaGraph_t into, bool units) {
+    const int H = L.key.H, W = L.key.W;
+    const FftPlan prow = make_plan(W, ctx->tw_off), pcol = make_plan(H, ctx->tw_off);
+    int rowT, rowMB;
+    row_launch_shape(prow, &rowT, &rowMB);
+    PassArgs a{};
+    a.err = ctx->d_err;
+    a.rdtype = L.key.dtype;
+    const ResidLayout lay = padded_layout(H, W);
+    a.rpitch = lay.rpitch;
+    a.fpitch = lay.fpitch;
+    a.roff = lay.roff;
+    a.H = H;
+    a.W = W;
+    a.nitems = L.wave;
+    a.spec = ws_spec;
+    a.stats = ws_stats;
+    a.fps = d_fpdesc;
+    a.scale = d_scale;
+    a.tw = ctx->d_tw;
+    a.prow = prow;
+    a.pcol = pcol;
+    a.pairs_per_block = L.tn.ppb;
+    a.col_log2 = L.tn.col_log2;
+    a.row_threads = rowT;
+    a.item_ptrs = L.d_items;
+    a.result_ptrs = L.d_results;
+    a.frame_ptrs = d_frame_ptrs;
+    a.units = units ? L.d_units : nullptr;
+    a.unit_of = units ? L.d_unit_of : nullptr;
+    a.nunits = L.wave;
+    a.share = 1;
+    a.fp_f32 = L.key.dtype == kF32 ? 1 : 0;   // half residuals: FP16 fingerprints expected (FP32 ones still correct)
+    a.d_counts = L.d_st->counts;
+    LaunchCounter lc;
+    PRNU_CUDA_TRY(cudaStreamBeginCaptureToGraph(s_cap, into, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    try {
+      launch_fixed_wave(a, *L.fs, L.tn.variant, s_cap, lc);
+    } catch (...) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(s_cap, &g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g;
+    PRNU_CUDA_TRY(cudaStreamEndCapture(s_cap, &g));
+  }
+
+  // loop begin -> WHILE { scheduler -> IF/ELSE { shared-forward wave | plain wave } -> completion }
+  void build_loop(DevLoop& L) {
+    if (L.exec) cudaGraphExecDestroy(L.exec);
+    if (L.graph) cudaGraphDestroy(L.graph);
+    L.exec = nullptr;
+    L.graph = nullptr;
+    cudaGraph_t g;
+    PRNU_CUDA_TRY(cudaGraphCreate(&g, 0));
+    L.graph = g;
+    cudaGraphConditionalHandle h_loop, h_units;
+    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
+    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_units, g, 0, cudaGraphCondAssignDefault));
+    auto kernel_node = [](cudaGraphNode_t* n, cudaGraph_t gr, const cudaGraphNode_t* dep, void* fn, int grid,
+                          int block, void** args) {
+      cudaKernelNodeParams kp{};
+      kp.func = fn;
+      kp.gridDim = dim3(grid);
+      kp.blockDim = dim3(block);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = args;
+      PRNU_CUDA_TRY(cudaGraphAddKernelNode(n, gr, dep, dep ? 1 : 0, &kp));
+    };
+    cudaGraphNode_t n_begin, n_loop, n_sched, n_if, n_done;
+    DevSched* d_st = L.d_st;
+    void* bargs[] = {&d_st};
+    kernel_node(&n_begin, g, nullptr, (void*)k_loop_begin, 1, 1, bargs);
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    PRNU_CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_begin, nullptr, 1, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    const DevRun* d_ring = L.d_ring;
+    const int* d_tail = L.d_flags;
+    const int* d_ready = L.d_flags + 1;
+    int* d_done = L.d_flags + 1 + kRing;
+    int wave = L.wave, H = L.key.H, W = L.key.W;
+    const WorkItem** d_items = L.d_items;
+    CandResult** d_results = L.d_results;
+    int* d_units = L.d_units;
+    int* d_unit_of = L.d_unit_of;
+    void* sargs[] = {&d_st, &d_ring, &d_tail, &d_ready, &wave, &d_items, &d_results, &d_units, &d_unit_of,
+                     &h_loop, &h_units};
+    kernel_node(&n_sched, body, nullptr, (void*)k_sched, 1, 32, sargs);
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_units;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 2;
+    PRNU_CUDA_TRY(cudaGraphAddNode(&n_if, body, &n_sched, nullptr, 1, &ip));
+    capture_wave(L, ip.conditional.phGraph_out[0], true);
+    capture_wave(L, ip.conditional.phGraph_out[1], false);
+    const DevSched* d_stc = d_st;
+    void* cargs[] = {&d_stc, &d_ring, &d_done, &H, &W};
+    kernel_node(&n_done, body, &n_if, (void*)k_complete, kMaxWave, 256, cargs);
+    PRNU_CUDA_TRY(cudaGraphInstantiate(&L.exec, g, 0));
+    L.built_gen = ws_gen;
+  }
+
+  // One launch at a time on the compute stream: when the previous one has
+  // ended, the size class whose oldest unfinished query (ingest complete) was
+  // admitted first gets the next launch.
+  void launch_loops() {
+    if (loop_running) {
+      if (cudaEventQuery(loop_ev) == cudaErrorNotReady) return;
+      loop_running = false;
+    }
+    DevLoop* best = nullptr;
+    Clock::time_point oldest = Clock::time_point::max();
+    for (auto& kv : loops) {
+      DevLoop* L = kv.second.get();
+      if (!L || L->dead) continue;
+      for (auto& qp : L->runs) {
+        if (qp->gpu_done.load() || qp->failed) continue;
+        if (cudaEventQuery(qp->ingest) != cudaSuccess) break;
+        if (qp->t_admit < oldest) {
+          oldest = qp->t_admit;
+          best = L;
+        }
+        break;
+      }
+    }
+    if (!best) return;
+    try {
+      if (!best->exec || best->built_gen != ws_gen) build_loop(*best);
+      PRNU_CUDA_TRY(cudaGraphLaunch(best->exec, s_comp));
+      PRNU_CUDA_TRY(cudaEventRecord(loop_ev, s_comp));
+      loop_running = true;
+      st.server_launches += 1;
+    } catch (const Error& e) {
+      best->dead = true;   // its ring may still name these queries: never launch it again
+      for (auto& qp : best->runs)
+        if (!qp->reported) fail(*qp, e);
+    }
   }
 
   // The size class with the oldest unlaunched work, or active.end().
@@ -597,6 +1009,15 @@ struct Server::Impl {
     bool any = false;
     for (size_t i = 0; i < admitted.size();) {
       Query& q = *admitted[i];
+      if (q.loop && !q.failed && !q.gpu_done.load()) {
+        const volatile int* fl = q.loop->flags;
+        if (fl[1 + kRing + (int)(q.ring_pos % kRing)]) {
+          std::atomic_thread_fence(std::memory_order_acquire);
+          q.t_done = Clock::now();
+          q.gpu_done.store(1);
+          st.candidates_done += q.call.items.size();
+        }
+      }
       if (q.gpu_done.load() || q.failed) {
         if (!q.failed) {
           q.results.assign(q.h_out, q.h_out + (size_t)q.F * q.P);
@@ -613,6 +1034,9 @@ struct Server::Impl {
       }
     }
     while (latency.size() > 100000) latency.erase(latency.begin());
+    for (auto& kv : loops)
+      if (kv.second)
+        while (!kv.second->runs.empty() && kv.second->runs.front()->reported) kv.second->runs.pop_front();
     return any;
   }
 
@@ -638,6 +1062,7 @@ struct Server::Impl {
         progressed = true;
       }
       if (progressed) done_cv.notify_all();
+      if (dev_mode) launch_loops();
       auto best = pick();
       if (best != active.end()) {
         WaveSlot& slot = waves[wave_next];
@@ -735,6 +1160,25 @@ int query_latency(prnu_ctx* ctx, uint64_t qid, double* queued_ms, double* total_
       throw Error{PRNU_ENOTFOUND, "no finished query with this id"};
     return (int)PRNU_OK;
   });
+}
+
+int prnu_server_set_loop(prnu_ctx* ctx, int mode) {
+  if (!ctx) {
+    set_error("NULL context");
+    return PRNU_EINVAL;
+  }
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (mode != PRNU_LOOP_HOST && mode != PRNU_LOOP_DEVICE) {
+    set_error("unknown server loop mode");
+    return PRNU_EINVAL;
+  }
+  if (ctx->server && mode != ctx->server_loop) {
+    set_error("the server has started: set its loop before the first query_submit");
+    return PRNU_EINVAL;
+  }
+  ctx->server_loop = mode;
+  set_error("");
+  return PRNU_OK;
 }
 
 int prnu_server_stats_get(prnu_ctx* ctx, prnu_server_stats* out) {

@@ -1,0 +1,118 @@
+"""The query server's device-resident request loop (prnu_server_set_loop).
+
+With PRNU_LOOP_DEVICE the waves of frame sizes with compile-time-planned
+kernels are formed on the GPU.  A CUDA graph per size repeats a scheduler
+kernel, the wave kernels (shared-forward or plain branch) and a completion
+kernel that writes each finished query's arg-max to host-mapped memory.  The
+kernels are those of the host loop, fed the same candidates, so every query's
+results must equal the host loop's bit for bit.  That holds alone, in a mix
+of sizes, storage types and fingerprint counts, across several waves per
+query, with many queries finishing in one wave, and for a size without
+planned kernels (which takes host waves inside the device mode)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def prnu():
+    import paper_2207_14507_gb300 as p
+    p.build()
+    return p
+
+
+def _query(H, W, F, P, half, seed, full_grid=False):
+    if full_grid:
+        g = synth.Grid(0.97, 0.01, 11, -1.5, 0.3, 11)
+        wl = synth.make_workload(1, H=H, W=W, F=F, grid=g)
+        wins = None
+    else:
+        g = synth.Grid(0.97, 0.01, 7, -1.5, 0.5, 7)
+        wl = synth.make_workload(2, H=H, W=W, F=F, grid=g, on_grid=True, s_max=min(12, H // 8))
+        rng = np.random.default_rng(seed)
+        # windows around the planted node, of uneven half-widths 1-2
+        wins = synth.snap_windows(g, wl.planted[:, :2], rng.integers(1, 3, size=F))
+    rng = np.random.default_rng(1000 + seed)
+    fps = [wl.fingerprints[0]] + [synth.fingerprint_field(H, W, rng) for _ in range(P - 1)]
+    return dict(frames=torch.from_numpy(wl.frames).to(DEV), fps=fps, g=g, windows=wins, half=half, F=F, P=P)
+
+
+def _serve(prnu, mode, queries, order=None):
+    """Serve the queries (all submitted before the first poll) on a fresh
+    context with the given loop; returns their results in submission order."""
+    with prnu.Context(0) as ctx:
+        ctx.prnu_server_set_loop(mode)
+        ids = []
+        for q in (queries if order is None else [queries[i] for i in order]):
+            fpd = prnu.PRNU_F16 if q["half"] else prnu.PRNU_F32
+            hs = [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(DEV), fpd) for K in q["fps"]]
+            dt = prnu.PRNU_F16 if q["half"] else prnu.PRNU_F32
+            flags = prnu.PRNU_WEIGHT_BY_INTENSITY | (prnu.PRNU_NORMALISE if q["half"] else 0)
+            ids.append((ctx.query_submit(q["frames"], hs, q["g"], windows=q["windows"], dtype=dt, flags=flags), q))
+        out = [ctx.query_poll(i, q["F"], q["P"], timeout_us=300_000_000) for i, q in ids]
+        stats = ctx.prnu_server_stats_get()
+    return out, stats
+
+
+MIX = [(256, 256, 3, 2, False, 1, True),      # planned, FP32, several waves per query
+       (720, 1280, 2, 3, True, 2, False),     # planned, FP16, shared forward units
+       (1080, 1920, 2, 1, True, 3, False),    # planned, FP16, plain branch
+       (240, 320, 2, 2, False, 4, False),     # no planned kernels: host waves in device mode
+       (256, 256, 2, 3, True, 5, True)]       # planned, FP16, shared units, several waves
+
+
+def test_device_loop_equals_host_loop(prnu):
+    qs = [_query(*m) for m in MIX]
+    dev, st = _serve(prnu, prnu.PRNU_LOOP_DEVICE, qs)
+    host, _ = _serve(prnu, prnu.PRNU_LOOP_HOST, qs)
+    for d, h in zip(dev, host):
+        assert d.tobytes() == h.tobytes()
+    assert st["queries_done"] == len(qs) and st["server_launches"] > 0
+    # the matching fingerprint finds every planted node and shift (the windowed queries)
+    for q, d in zip(qs, dev):
+        if q["windows"] is None:
+            continue
+        assert np.all(d[:, 0]["pce"] > 60)
+
+
+def test_device_loop_alone_and_in_the_mix(prnu):
+    qs = [_query(*m) for m in MIX]
+    alone, _ = _serve(prnu, prnu.PRNU_LOOP_DEVICE, qs[1:2])
+    mixed, _ = _serve(prnu, prnu.PRNU_LOOP_DEVICE, qs, order=[4, 0, 3, 1, 2])
+    assert alone[0].tobytes() == mixed[3].tobytes()
+
+
+def test_device_loop_many_small_queries(prnu):
+    """48 one-frame 256x256 queries at once: many finish in the same wave and
+    the loop relaunches across its wave budget; each equals eis_grid_search."""
+    qs = [_query(256, 256, 1, 1 + (i % 3), bool(i % 2), 100 + i) for i in range(48)]
+    dev, st = _serve(prnu, prnu.PRNU_LOOP_DEVICE, qs)
+    host, _ = _serve(prnu, prnu.PRNU_LOOP_HOST, qs)
+    for d, h in zip(dev, host):
+        assert d.tobytes() == h.tobytes()
+    assert st["candidates_done"] == sum(q["P"] * int(np.prod(q["windows"][:, 1] - q["windows"][:, 0] + 1) *
+                                                     np.prod(q["windows"][:, 3] - q["windows"][:, 2] + 1))
+                                        for q in qs)
+
+
+def test_loop_mode_rules(prnu):
+    with prnu.Context(0) as ctx:
+        with pytest.raises(prnu.PrnuError) as e:
+            ctx.prnu_server_set_loop(7)
+        assert e.value.code == prnu.PRNU_EINVAL
+        ctx.prnu_server_set_loop(prnu.PRNU_LOOP_DEVICE)
+        q = _query(256, 256, 1, 1, False, 9)
+        h = ctx.prnu_fingerprint_term(torch.from_numpy(q["fps"][0]).to(DEV))
+        qid = ctx.query_submit(q["frames"], [h], q["g"], windows=q["windows"], dtype=prnu.PRNU_F32,
+                               flags=prnu.PRNU_WEIGHT_BY_INTENSITY)
+        ctx.query_poll(qid, 1, 1, timeout_us=60_000_000)
+        ctx.prnu_server_set_loop(prnu.PRNU_LOOP_DEVICE)        # unchanged: fine
+        with pytest.raises(prnu.PrnuError) as e:
+            ctx.prnu_server_set_loop(prnu.PRNU_LOOP_HOST)      # the server has started
+        assert e.value.code == prnu.PRNU_EINVAL
