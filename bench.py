@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=16, help="serving: queries of the capacity run")
     ap.add_argument("--steady-queries", type=int, default=100, help="serving: queries at 70%% of capacity")
     ap.add_argument("--overload-queries", type=int, default=200, help="serving: queries at 20 queries/s")
+    ap.add_argument("--loop", choices=("device", "host"), default="device",
+                    help="serving: the server's request loop (device-resident graphs or the host thread)")
     ap.add_argument("--oracle-queries", type=int, default=20, help="serving: served queries checked by the oracle")
     ap.add_argument("--wave", type=int, default=0,
                     help="plain workload: candidates per wave after tuning (0 = the tuned value); for small profiles")
@@ -965,7 +967,8 @@ def run_serving(args):
     include queueing).  The FP64 oracle checks sampled served results: for
     --oracle-queries queries of the steady run, one (frame, fingerprint) pair
     each, the PCE at the served node and at its grid neighbours inside the
-    window."""
+    window.  --loop picks the server's request loop: the device-resident
+    graphs (default) or the host thread."""
     import threading
     import torch
     import oracle
@@ -978,6 +981,7 @@ def run_serving(args):
     queries, banks, pools = synth.make_query_stream(n_cap + n_st + n_ov, rate_hz=20.0, pool_frames=8,
                                                     match_sources=1, materialise=False)
     ctx = prnu.Context(0, hbm_budget_bytes=120 << 30)
+    ctx.prnu_server_set_loop(prnu.PRNU_LOOP_DEVICE if args.loop == "device" else prnu.PRNU_LOOP_HOST)
     tunings = {}
     for (H, W) in banks:
         tunings[f"{H}x{W}"] = ctx.prnu_autotune(H, W, prnu.PRNU_F16, budget_ms=args.autotune_ms) \
@@ -1042,6 +1046,8 @@ def run_serving(args):
     rng = np.random.default_rng(5)
     for name, rate, idx in (("70pct_capacity", 0.7 * cap_q, list(range(n_cap, n_cap + n_st))),
                             ("20qps_overloaded", 20.0, list(range(n_cap + n_st, n_cap + n_st + n_ov)))):
+        if not idx:
+            continue
         arr = np.cumsum(rng.exponential(1.0 / rate, size=len(idx)))
         w2, l2 = run(idx, list(arr))
         out[name] = summary(name, rate, idx, w2, l2, cap_q)
@@ -1097,7 +1103,7 @@ def run_serving(args):
                     "checks": checks}
     mean_fp = float(np.mean([len(q.fp_ids) for q in queries]))
     print(json.dumps({"workload": "serving (config 5)", "metric": "served p50/p99 query latency",
-                      "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
+                      "loop": args.loop, "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
                       "mean_fingerprints_per_query": round(mean_fp, 2), "budget_gb": 120,
                       "admitted_bytes_peak": st["admitted_bytes_peak"], "server_launches": st["server_launches"],
                       "dtype": "f16", "oracle_check": oracle_check, "tuning": tunings}), flush=True)

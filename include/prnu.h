@@ -392,16 +392,16 @@ int query_latency(prnu_ctx* ctx, uint64_t qid, double* queued_ms, double* total_
  *  - a scheduler kernel takes the next candidates of the admitted queries
  *    (whole forward units, in admission order) from a host-mapped ring and
  *    builds the wave's tables on the device;
- *  - the wave kernels run, in the shared-forward or plain branch of an
- *    IF/ELSE node;
+ *  - the wave kernels run, in the branch of a SWITCH node whose grids are
+ *    the smallest that fit the wave (shared forward units or not);
  *  - a completion kernel writes the arg-max of each query the wave finished
  *    into host-mapped memory and raises its done flag.
  * The host thread only admits queries (device memory, ingest, one ring entry
  * each).  It relaunches a size's graph when it has drained or used its
  * budget of 32 waves, so sizes take turns.  Other sizes take host waves.
- * Results are bit-identical in both modes.  Set the mode before the
- * context's first query_submit: PRNU_EINVAL afterwards (unless unchanged) or
- * for an unknown mode. */
+ * Results are bit-identical in both modes; PRNU_LOOP_DEVICE is the default.
+ * Set the mode before the context's first query_submit: PRNU_EINVAL
+ * afterwards (unless unchanged) or for an unknown mode. */
 enum { PRNU_LOOP_HOST = 0, PRNU_LOOP_DEVICE = 1 };
 int prnu_server_set_loop(prnu_ctx* ctx, int mode);
 

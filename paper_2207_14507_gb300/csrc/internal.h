@@ -242,7 +242,7 @@ struct prnu_ctx {
   cudaEvent_t stage_free = nullptr;
   std::map<std::pair<int, int>, prnu::Tuning> tuning;
   std::unique_ptr<prnu::Server> server;
-  int server_loop = 0;            // PRNU_LOOP_HOST / PRNU_LOOP_DEVICE, read when the server starts
+  int server_loop = PRNU_LOOP_DEVICE;   // PRNU_LOOP_HOST / PRNU_LOOP_DEVICE, read when the server starts
 };
 
 namespace prnu {

@@ -18,17 +18,18 @@
 // eis_grid_search and a query's results do not depend on what it was batched
 // with.
 //
-// Two request loops run the waves (prnu_server_set_loop):
+// Two request loops run the waves (prnu_server_set_loop; device by default):
 //  host   : the server thread forms each wave's tables and launches its
 //           kernels;
 //  device : for frame sizes with compile-time-planned kernels, one CUDA graph
 //           per size class holds the whole loop.  A WHILE node repeats a body:
 //           a scheduler kernel takes the next candidates of the ready queries
 //           from a host-mapped ring, builds the wave tables on the device and
-//           picks the shared-forward or plain branch of an IF/ELSE node that
-//           holds the wave kernels.  A completion kernel then writes the
-//           arg-max of every query the wave finished into host-mapped memory
-//           and raises its done flag.  The host thread only admits queries
+//           picks the branch of a SWITCH node that holds the wave kernels
+//           in the smallest grids that fit the wave (shared forward units or
+//           not; 16, 32, ... candidates and units).  A completion kernel
+//           then writes the arg-max of every query the wave finished into
+//           host-mapped memory and raises its done flag.  The host thread only admits queries
 //           (memory, ingest, one ring entry each), relaunches a size class's
 //           graph when it has drained or used its wave budget, and reports
 //           queries whose done flag is up.
@@ -90,6 +91,17 @@ struct DevRun {
   int pad;
 };
 
+// The wave shapes a size class's loop body holds, one branch each of its
+// SWITCH node: shared forward units or not, and the grids' sizes (items, and
+// forward units), so that a wave runs in the smallest branch that fits it.
+constexpr int kMaxCases = 24;
+struct CaseTable {
+  int n;
+  int grouped[kMaxCases];
+  int items[kMaxCases];
+  int units[kMaxCases];
+};
+
 // Device state of one size class's loop.
 struct DevSched {
   int head;                 // ring position of the first query not fully scheduled
@@ -111,6 +123,13 @@ __device__ __forceinline__ void st_release_sys(int* p, int v) {
 
 __global__ void k_loop_begin(DevSched* st) { st->waves = 0; }
 
+// the first branch of the case table that holds a wave, or ct.n
+__device__ __forceinline__ int fit_case(const CaseTable& ct, int count, int nunits, bool grouped) {
+  for (int k = 0; k < ct.n; ++k)
+    if (ct.grouped[k] == (grouped ? 1 : 0) && ct.items[k] >= count && (!grouped || ct.units[k] >= nunits)) return k;
+  return ct.n;
+}
+
 // the query's ingest (frames, residual, work list) is complete
 __global__ void k_mark_ready(int* ready) {
   __threadfence_system();
@@ -118,11 +137,12 @@ __global__ void k_mark_ready(int* ready) {
 }
 
 // One wave: up to `wave` candidates of the ready queries in ring order, whole
-// forward units only, into the wave tables; the loop goes on while it found
-// candidates and the launch's wave budget lasts.  One thread.
+// forward units only, into the wave tables; the smallest branch of the case
+// table that holds it; the loop goes on while it found candidates and the
+// launch's wave budget lasts.  One thread.
 __global__ void k_sched(DevSched* st, const DevRun* ring, const int* tail_p, const int* ready, int wave,
                         const WorkItem** item_ptrs, CandResult** result_ptrs, int* units, int* unit_of,
-                        cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_units) {
+                        cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_case, CaseTable ct) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int tail = ld_acquire_sys(tail_p);
   int head = st->head, next = st->next, count = 0, nunits = 0, ncomp = 0;
@@ -138,7 +158,9 @@ __global__ void k_sched(DevSched* st, const DevRun* ring, const int* tail_p, con
       continue;
     }
     const int S = max(r.share, 1);
-    const int take = min(wave - count, r.n - next) / S * S;
+    int take = min(wave - count, r.n - next) / S * S;
+    // only as many whole units as a branch of the body can hold
+    while (take > 0 && fit_case(ct, count + take, nunits + take / S, grouped || S > 1) == ct.n) take -= S;
     if (take == 0) break;
     for (int k = 0; k < take; ++k) {
       item_ptrs[count + k] = r.items + next + k;
@@ -166,8 +188,9 @@ __global__ void k_sched(DevSched* st, const DevRun* ring, const int* tail_p, con
   st->ncomplete = ncomp;
   const int waves = st->waves + 1;
   st->waves = waves;
+  const int c = count > 0 ? fit_case(ct, count, nunits, grouped) : ct.n;   // ct.n: no branch runs
   __threadfence();
-  cudaGraphSetConditional(h_units, grouped ? 1u : 0u);
+  cudaGraphSetConditional(h_case, (unsigned)c);
   cudaGraphSetConditional(h_loop, count > 0 && waves < kLoopWaves ? 1u : 0u);
 }
 
@@ -563,9 +586,9 @@ struct Server::Impl {
     DevLoop* L = dev_mode ? loop_for(q) : nullptr;   // nullptr: host waves
     if (L && (int)L->runs.size() >= kRing) return false;
     const int wave = L ? L->wave : std::max(1, std::min(q.tn.wave, kMaxWave));
-    // spectra: the wave's candidates, then one slot per forward unit (the
-    // device loop's graph always holds the shared-forward branch)
-    ensure_workspace(q.H, q.W, (L || q.call.share > 1 ? 2 : 1) * wave, wave);
+    // spectra: the wave's candidates, then one slot per forward unit (a
+    // device loop's branches are rebuilt for the slots there are)
+    ensure_workspace(q.H, q.W, (q.call.share > 1 ? 2 : 1) * wave, wave);
     if (ctx->used.load() + q.bytes > ctx->budget) return false;
     const int slot0 = alloc_frames(q.F);
     if (slot0 < 0) return false;
@@ -735,8 +758,9 @@ struct Server::Impl {
   }
 
   // The wave kernels of one branch of the loop body, captured into `into`:
-  // grids sized for a full wave, the live counts read on the device.
-  void capture_wave(DevLoop& L, cudaGraph_t into, bool units) {
+  // grids sized for `items` candidates and `nunits` forward units (the unit
+  // slots follow the items' slots), the live counts read on the device.
+  void capture_wave(DevLoop& L, cudaGraph_t into, bool units, int items, int nunits) {
     const int H = L.key.H, W = L.key.W;
     const FftPlan prow = make_plan(W, ctx->tw_off), pcol = make_plan(H, ctx->tw_off);
     int rowT, rowMB;
@@ -750,7 +774,7 @@ struct Server::Impl {
     a.roff = lay.roff;
     a.H = H;
     a.W = W;
-    a.nitems = L.wave;
+    a.nitems = items;
     a.spec = ws_spec;
     a.stats = ws_stats;
     a.fps = d_fpdesc;
@@ -766,7 +790,7 @@ struct Server::Impl {
     a.frame_ptrs = d_frame_ptrs;
     a.units = units ? L.d_units : nullptr;
     a.unit_of = units ? L.d_unit_of : nullptr;
-    a.nunits = L.wave;
+    a.nunits = nunits;
     a.share = 1;
     a.fp_f32 = L.key.dtype == kF32 ? 1 : 0;   // half residuals: FP16 fingerprints expected (FP32 ones still correct)
     a.d_counts = L.d_st->counts;
@@ -784,7 +808,30 @@ struct Server::Impl {
     PRNU_CUDA_TRY(cudaStreamEndCapture(s_cap, &g));
   }
 
-  // loop begin -> WHILE { scheduler -> IF/ELSE { shared-forward wave | plain wave } -> completion }
+  // The branches of a loop body: plain and shared-forward waves with grids of
+  // 16, 32, ... up to `wave` items (and, shared, as many or fewer units),
+  // within `slots` workspace spectra (a shared wave takes items + units).
+  static CaseTable case_table(int wave, int slots) {
+    std::vector<int> caps;
+    for (int c = 16; c < wave; c *= 2) caps.push_back(c);
+    caps.push_back(wave);
+    CaseTable ct{};
+    auto add = [&](int g, int it, int un) {
+      if (ct.n >= kMaxCases) return;
+      ct.grouped[ct.n] = g;
+      ct.items[ct.n] = it;
+      ct.units[ct.n] = un;
+      ++ct.n;
+    };
+    for (int it : caps)
+      if (it <= slots) add(0, it, it);
+    for (int it : caps)
+      for (int un : caps)
+        if (un <= it && it + un <= slots) add(1, it, un);
+    return ct;
+  }
+
+  // loop begin -> WHILE { scheduler -> SWITCH { wave branches } -> completion }
   void build_loop(DevLoop& L) {
     if (L.exec) cudaGraphExecDestroy(L.exec);
     if (L.graph) cudaGraphDestroy(L.graph);
@@ -793,9 +840,12 @@ struct Server::Impl {
     cudaGraph_t g;
     PRNU_CUDA_TRY(cudaGraphCreate(&g, 0));
     L.graph = g;
-    cudaGraphConditionalHandle h_loop, h_units;
+    cudaGraphConditionalHandle h_loop, h_case;
     PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
-    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_units, g, 0, cudaGraphCondAssignDefault));
+    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_case, g, 0, cudaGraphCondAssignDefault));
+    const size_t spec_slot = (size_t)L.key.H * (L.key.W / 2) * sizeof(float2);
+    CaseTable ct = case_table(L.wave, (int)std::min<size_t>(ws_spec_bytes / spec_slot, 1 << 20));
+    if (ct.n == 0) throw Error{PRNU_ENOMEM, "no workspace for a wave of this frame size"};
     auto kernel_node = [](cudaGraphNode_t* n, cudaGraph_t gr, const cudaGraphNode_t* dep, void* fn, int grid,
                           int block, void** args) {
       cudaKernelNodeParams kp{};
@@ -827,16 +877,16 @@ struct Server::Impl {
     int* d_units = L.d_units;
     int* d_unit_of = L.d_unit_of;
     void* sargs[] = {&d_st, &d_ring, &d_tail, &d_ready, &wave, &d_items, &d_results, &d_units, &d_unit_of,
-                     &h_loop, &h_units};
+                     &h_loop, &h_case, &ct};
     kernel_node(&n_sched, body, nullptr, (void*)k_sched, 1, 32, sargs);
     cudaGraphNodeParams ip{};
     ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = h_units;
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 2;
+    ip.conditional.handle = h_case;
+    ip.conditional.type = cudaGraphCondTypeSwitch;
+    ip.conditional.size = (unsigned)ct.n;
     PRNU_CUDA_TRY(cudaGraphAddNode(&n_if, body, &n_sched, nullptr, 1, &ip));
-    capture_wave(L, ip.conditional.phGraph_out[0], true);
-    capture_wave(L, ip.conditional.phGraph_out[1], false);
+    for (int k = 0; k < ct.n; ++k)
+      capture_wave(L, ip.conditional.phGraph_out[k], ct.grouped[k] != 0, ct.items[k], ct.units[k]);
     const DevSched* d_stc = d_st;
     void* cargs[] = {&d_stc, &d_ring, &d_done, &H, &W};
     kernel_node(&n_done, body, &n_if, (void*)k_complete, kMaxWave, 256, cargs);
