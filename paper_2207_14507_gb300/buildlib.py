@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libprnu.so")
 SOURCES = ["api.cu", "search.cu", "search_fixed.cu", "residual.cu", "wavelet.cu", "serve.cu", "autotune.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "wave_loop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -10,6 +10,7 @@
 #include <functional>
 
 #include "internal.h"
+#include "wave_loop.h"
 #include "search_fixed.h"
 #include "server.h"
 
@@ -176,7 +177,7 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
 bool share_forward(prnu_ctx* c, int H, int W, int P, bool naive) {
   if (naive || P < 2) return false;
   const Tuning t = tuning_for(c, H, W);
-  if (!t.share || t.persistent || t.variant < 0 || P > t.wave) return false;
+  if (!t.share || t.persistent == 1 || t.variant < 0 || P > t.wave) return false;
   const FixedShape* fs = find_fixed(H, W);
   return fs && fixed_supports(*fs, H, t.ppb);
 }
@@ -301,16 +302,18 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   const int wave = naive ? 1 : std::max(share, std::min(tn.wave, n) / share * share);
   const FixedShape* fs = (!naive && tn.variant >= 0) ? find_fixed(H, W) : nullptr;
   if (fs && !fixed_supports(*fs, H, tn.ppb)) fs = nullptr;
-  PRNU_CHECK_ARG(share == 1 || (fs && !tn.persistent && n % share == 0),
+  PRNU_CHECK_ARG(share == 1 || (fs && tn.persistent != 1 && n % share == 0),
                  "shared forward units need the compile-time-planned wave kernels");
-  bool persistent = fs && tn.persistent && (H / 2) % fs->persist.ppb == 0;
+  bool persistent = fs && tn.persistent == 1 && (H / 2) % fs->persist.ppb == 0;
+  // the device-resident loop: every wave of the call in one graph launch
+  const bool graph = fs && tn.persistent == 2 && !naive && !call.prepadded;
   if (persistent) {   // tickets of one launch: (n + 3) steps of 2 row phases, the column phase and a finalisation
     const long long nrf = (H / 2) / fs->persist.ppb, ncol = (Wh + fs->persist.nc - 1) / fs->persist.nc;
     persistent = (long long)(n + 3) * (2 * nrf + ncol + 1) < (long long)INT_MAX;
   }
   // two-stream waves: alternate waves on s and the context's second stream,
   // each on its own half of the workspace
-  const bool two = fs && !persistent && !naive && tn.streams == 2 && n > wave && share == 1;
+  const bool two = fs && !persistent && !graph && !naive && tn.streams == 2 && n > wave && share == 1;
   // forward units compute in slots after the wave's candidates (one per unit)
   const int slots = persistent ? kPersistSlots : (two ? 2 * wave : wave + (share > 1 ? wave / share : 0));
 
@@ -372,7 +375,37 @@ void enqueue_search(prnu_ctx* c, const SearchCall& call, prnu_result* d_out, dou
   a.unit_of = nullptr;
   a.fp_f32 = std::any_of(fd.begin(), fd.end(), [](const FpDesc& d) { return d.dtype == kF32; }) ? 1 : 0;
 
-  if (persistent) {
+  if (graph) {
+    auto& bl = c->batch_loops[std::make_tuple(H, W, (int)a.rdtype)];
+    if (!bl) bl.reset(new BatchLoop(c));
+    WaveLoopConfig g;
+    g.fs = fs;
+    g.variant = tn.variant;
+    g.ppb = tn.ppb;
+    g.col_log2 = tn.col_log2;
+    g.H = H;
+    g.W = W;
+    g.rdtype = a.rdtype;
+    g.wave = std::min(wave, kLoopMaxWave / share * share);
+    g.fp_f32 = a.fp_f32;
+    g.spec = a.spec;
+    g.stats = a.stats;
+    g.spec_slots = slots;
+    g.resid = a.resid;
+    g.fps = a.fps;
+    g.scale = a.scale;
+    g.err = a.err;
+    g.stall = a.stall;
+    DevRun r{};
+    r.items = a.items;
+    r.results = a.results;
+    r.groups = reinterpret_cast<const int*>(c->ws_groups.p);
+    r.n = n;
+    r.share = share;
+    r.ngroups = 0;   // the arg-max runs after the loop, as for the other paths
+    bl->run(g, r, s);
+    PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else if (persistent) {
     int* st0 = reinterpret_cast<int*>(c->ws_persist.p);
     PersistArgs p{st0, st0 + 1, st0 + 2, st0 + 2 + n, st0 + 2 + 2 * (size_t)n, st0 + 2 + 3 * (size_t)n, n,
                   kPersistSlots};
@@ -798,6 +831,7 @@ int prnu_destroy(prnu_ctx* ctx) {
     DeviceGuard dg(ctx->device);
     ctx->server.reset();
     cudaDeviceSynchronize();
+    ctx->batch_loops.clear();
     for (auto& kv : ctx->fps) {
       auto& f = kv.second;
       if (f->refs > 0 && f.use_count() == 1) {
@@ -1389,7 +1423,7 @@ int prnu_set_tuning(prnu_ctx* ctx, int H, int W, const prnu_tuning* cfg) {
     const FixedShape* fs = find_fixed(H, W);
     PRNU_CHECK_ARG(cfg->variant >= -1 && cfg->variant < (fs ? (int)fs->cols.size() : 0),
                    "variant out of range for this frame size (-1 = generic kernels)");
-    PRNU_CHECK_ARG(cfg->persistent == 0 || cfg->persistent == 1, "persistent must be 0 or 1");
+    PRNU_CHECK_ARG(cfg->persistent >= 0 && cfg->persistent <= 2, "persistent must be 0, 1 or 2");
     PRNU_CHECK_ARG(cfg->streams >= 0 && cfg->streams <= 2, "streams must be 0, 1 or 2");
     PRNU_CHECK_ARG(cfg->share_forward == 0 || cfg->share_forward == 1, "share_forward must be 0 or 1");
     ctx->tuning[{H, W}] = Tuning{lg, cfg->pairs_per_block, cfg->wave, cfg->variant, cfg->persistent,

@@ -6,6 +6,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -215,6 +216,10 @@ struct Tuning {
 
 }  // namespace prnu
 
+namespace prnu {
+class BatchLoop;
+}  // namespace prnu
+
 struct prnu_ctx {
   int device = 0;
   int sm_count = 0;
@@ -242,6 +247,8 @@ struct prnu_ctx {
   cudaEvent_t stage_free = nullptr;
   std::map<std::pair<int, int>, prnu::Tuning> tuning;
   std::unique_ptr<prnu::Server> server;
+  // eis_grid_search's device-resident loops (prnu_tuning.persistent = 2), by (H, W, residual layout)
+  std::map<std::tuple<int, int, int>, std::unique_ptr<prnu::BatchLoop>> batch_loops;
   int server_loop = PRNU_LOOP_DEVICE;   // PRNU_LOOP_HOST / PRNU_LOOP_DEVICE, read when the server starts
 };
 

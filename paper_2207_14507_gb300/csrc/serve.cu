@@ -37,9 +37,9 @@
 #include <chrono>
 #include <cstring>
 
-#include "search_common.cuh"
 #include "search_fixed.h"
 #include "server.h"
+#include "wave_loop.h"
 
 namespace prnu {
 
@@ -76,140 +76,6 @@ __global__ void k_set_fpdesc(FpDesc* __restrict__ dst, FpDesc v) { *dst = v; }
 
 constexpr int kRing = 1024;       // queries of one size class admitted and not yet reported
 constexpr int kLoopWaves = 32;    // waves per launch of a size class's loop
-
-// One admitted query as the device scheduler sees it (an entry of a
-// host-mapped ring; its ready and done flags are in host-mapped arrays indexed
-// like the ring).
-struct DevRun {
-  const WorkItem* items;    // device [n]
-  CandResult* results;      // device [n]
-  const int* groups;        // device group table (SearchCall::group_start)
-  prnu_result* out;         // host-mapped [ngroups]
-  int n;                    // candidates
-  int share;                // fingerprints per forward unit (1: none)
-  int ngroups;              // F * P
-  int pad;
-};
-
-// The wave shapes a size class's loop body holds, one branch each of its
-// SWITCH node: shared forward units or not, and the grids' sizes (items, and
-// forward units), so that a wave runs in the smallest branch that fits it.
-constexpr int kMaxCases = 24;
-struct CaseTable {
-  int n;
-  int grouped[kMaxCases];
-  int items[kMaxCases];
-  int units[kMaxCases];
-};
-
-// Device state of one size class's loop.
-struct DevSched {
-  int head;                 // ring position of the first query not fully scheduled
-  int next;                 // its next candidate
-  int waves;                // waves run by the current launch
-  int counts[2];            // the current wave's items and forward units (PassArgs::d_counts)
-  int ncomplete;            // queries whose last candidates are in the current wave
-  int complete[kMaxWave];   // their ring positions
-};
-
-__device__ __forceinline__ int ld_acquire_sys(const int* p) {
-  int v;
-  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_sys(int* p, int v) {
-  asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__global__ void k_loop_begin(DevSched* st) { st->waves = 0; }
-
-// the first branch of the case table that holds a wave, or ct.n
-__device__ __forceinline__ int fit_case(const CaseTable& ct, int count, int nunits, bool grouped) {
-  for (int k = 0; k < ct.n; ++k)
-    if (ct.grouped[k] == (grouped ? 1 : 0) && ct.items[k] >= count && (!grouped || ct.units[k] >= nunits)) return k;
-  return ct.n;
-}
-
-// the query's ingest (frames, residual, work list) is complete
-__global__ void k_mark_ready(int* ready) {
-  __threadfence_system();
-  st_release_sys(ready, 1);
-}
-
-// One wave: up to `wave` candidates of the ready queries in ring order, whole
-// forward units only, into the wave tables; the smallest branch of the case
-// table that holds it; the loop goes on while it found candidates and the
-// launch's wave budget lasts.  One thread.
-__global__ void k_sched(DevSched* st, const DevRun* ring, const int* tail_p, const int* ready, int wave,
-                        const WorkItem** item_ptrs, CandResult** result_ptrs, int* units, int* unit_of,
-                        cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_case, CaseTable ct) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int tail = ld_acquire_sys(tail_p);
-  int head = st->head, next = st->next, count = 0, nunits = 0, ncomp = 0;
-  bool grouped = false;
-  while (count < wave && ncomp < kMaxWave && head != tail) {
-    const int slot = head % kRing;
-    if (ld_acquire_sys(ready + slot) == 0) break;   // ingest still running: keep arrival order
-    const DevRun r = ring[slot];
-    if (r.n <= 0) {                                  // nothing to score: complete at once
-      st->complete[ncomp++] = head;
-      ++head;
-      next = 0;
-      continue;
-    }
-    const int S = max(r.share, 1);
-    int take = min(wave - count, r.n - next) / S * S;
-    // only as many whole units as a branch of the body can hold
-    while (take > 0 && fit_case(ct, count + take, nunits + take / S, grouped || S > 1) == ct.n) take -= S;
-    if (take == 0) break;
-    for (int k = 0; k < take; ++k) {
-      item_ptrs[count + k] = r.items + next + k;
-      result_ptrs[count + k] = r.results + next + k;
-    }
-    for (int u = 0; u < take / S; ++u) {
-      units[nunits] = count + u * S;
-      for (int k = 0; k < S; ++k) unit_of[count + u * S + k] = nunits;
-      ++nunits;
-    }
-    grouped = grouped || S > 1;
-    count += take;
-    next += take;
-    if (next == r.n) {
-      st->complete[ncomp++] = head;
-      ++head;
-      next = 0;
-    }
-  }
-  units[nunits] = count;
-  st->head = head;
-  st->next = next;
-  st->counts[0] = count;
-  st->counts[1] = grouped ? nunits : count;
-  st->ncomplete = ncomp;
-  const int waves = st->waves + 1;
-  st->waves = waves;
-  const int c = count > 0 ? fit_case(ct, count, nunits, grouped) : ct.n;   // ct.n: no branch runs
-  __threadfence();
-  cudaGraphSetConditional(h_case, (unsigned)c);
-  cudaGraphSetConditional(h_loop, count > 0 && waves < kLoopWaves ? 1u : 0u);
-}
-
-// The arg-max of every query the wave finished, into its host-mapped results,
-// then its done flag.  One block per finished query.
-__global__ void k_complete(const DevSched* st, const DevRun* ring, int* done, int H, int W) {
-  const int c = blockIdx.x;
-  if (c >= st->ncomplete) return;
-  const int slot = st->complete[c] % kRing;
-  const DevRun r = ring[slot];
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int g = threadIdx.x >> 5; g < r.ngroups; g += nw)
-    argmax_group(r.results, r.items, r.groups, max(r.share, 1), r.out, H, W, g, lane);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence_system();
-    st_release_sys(done + slot, 1);
-  }
-}
 
 }  // namespace
 
@@ -297,38 +163,27 @@ struct Server::Impl {
   size_t ws_spec_bytes = 0, ws_stats_bytes = 0;
   prnu_server_stats st{};
 
-  // The device-resident loop of one size class: its graph, its scheduler
-  // state and wave tables (device), and the ring of admitted queries with
-  // their ready and done flags (host-mapped).
+  // The device-resident loop of one size class: its WaveLoop (graph,
+  // scheduler state, wave tables) and the ring of admitted queries with their
+  // ready and done flags (host-mapped).
   struct DevLoop {
     SizeKey key{};
     Tuning tn{};
     const FixedShape* fs = nullptr;
     int wave = 0;
-    char* dmem = nullptr;
-    size_t dbytes = 0;
-    DevSched* d_st = nullptr;
-    const WorkItem** d_items = nullptr;
-    CandResult** d_results = nullptr;
-    int* d_units = nullptr;
-    int* d_unit_of = nullptr;
+    std::unique_ptr<WaveLoop> wl;
     DevRun* ring = nullptr;        // host pointer
     DevRun* d_ring = nullptr;      // its device pointer
     int* flags = nullptr;          // host pointer: tail, ready[kRing], done[kRing]
     int* d_flags = nullptr;
     long long appended = 0;
     std::deque<std::shared_ptr<Query>> runs;   // appended, not yet reported (ring order)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    size_t built_gen = ~(size_t)0;
     bool dead = false;             // a launch failed: no further use
   };
   bool dev_mode = false;
   std::map<SizeKey, std::unique_ptr<DevLoop>> loops;   // nullptr: no planned kernels, host waves
-  cudaStream_t s_cap = nullptr;
   cudaEvent_t loop_ev = nullptr;
   bool loop_running = false;
-  size_t ws_gen = 0;               // workspace generation (graphs hold its pointers)
 
   explicit Impl(prnu_ctx* c) : ctx(c) {
     PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_comp, cudaStreamNonBlocking));
@@ -346,10 +201,7 @@ struct Server::Impl {
     // mapped: the device loop's completion kernel writes query results here
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&arena, kArenaBlock * kArenaBlocks, cudaHostAllocMapped));
     dev_mode = ctx->server_loop == PRNU_LOOP_DEVICE;
-    if (dev_mode) {
-      PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_cap, cudaStreamNonBlocking));
-      PRNU_CUDA_TRY(cudaEventCreateWithFlags(&loop_ev, cudaEventDisableTiming));
-    }
+    if (dev_mode) PRNU_CUDA_TRY(cudaEventCreateWithFlags(&loop_ev, cudaEventDisableTiming));
     for (auto& w : waves) {
       PRNU_CUDA_TRY(cudaHostAlloc((void**)&w.h_tab, kWaveTabBytes, cudaHostAllocDefault));
       w.d_tab = reinterpret_cast<void**>(ctx_alloc(ctx, kWaveTabBytes));
@@ -373,13 +225,10 @@ struct Server::Impl {
     for (auto& kv : loops) {
       DevLoop* L = kv.second.get();
       if (!L) continue;
-      if (L->exec) cudaGraphExecDestroy(L->exec);
-      if (L->graph) cudaGraphDestroy(L->graph);
-      if (L->dmem) ctx_free(ctx, L->dmem, L->dbytes);
+      L->wl.reset();
       if (L->ring) cudaFreeHost(L->ring);
       if (L->flags) cudaFreeHost(L->flags);
     }
-    if (s_cap) cudaStreamDestroy(s_cap);
     if (loop_ev) cudaEventDestroy(loop_ev);
     for (auto& w : waves) {
       cudaFreeHost(w.h_tab);
@@ -572,8 +421,7 @@ struct Server::Impl {
     if (ws_spec) ctx_free(ctx, ws_spec, ws_spec_bytes);
     if (ws_stats) ctx_free(ctx, ws_stats, ws_stats_bytes);
     ws_spec = nullptr;
-    ws_stats = nullptr;
-    ++ws_gen;   // device loops rebuild their graphs before the next launch
+    ws_stats = nullptr;   // device loops rebuild their graphs for the new pointers before their next launch
     ws_spec_bytes = std::max(sb, ws_spec_bytes);
     ws_stats_bytes = std::max(tb, ws_stats_bytes);
     ws_spec = reinterpret_cast<float2*>(ctx_alloc(ctx, ws_spec_bytes));
@@ -705,18 +553,7 @@ struct Server::Impl {
     L->tn = q.tn;
     L->fs = fs;
     L->wave = std::max(1, std::min(q.tn.wave, kMaxWave));
-    const size_t o_items = align256(sizeof(DevSched));
-    const size_t o_results = o_items + align256(sizeof(void*) * kMaxWave);
-    const size_t o_units = o_results + align256(sizeof(void*) * kMaxWave);
-    const size_t o_unit_of = o_units + align256(sizeof(int) * (kMaxWave + 1));
-    L->dbytes = o_unit_of + align256(sizeof(int) * kMaxWave);
-    L->dmem = reinterpret_cast<char*>(ctx_alloc(ctx, L->dbytes));
-    PRNU_CUDA_TRY(cudaMemset(L->dmem, 0, L->dbytes));
-    L->d_st = reinterpret_cast<DevSched*>(L->dmem);
-    L->d_items = reinterpret_cast<const WorkItem**>(L->dmem + o_items);
-    L->d_results = reinterpret_cast<CandResult**>(L->dmem + o_results);
-    L->d_units = reinterpret_cast<int*>(L->dmem + o_units);
-    L->d_unit_of = reinterpret_cast<int*>(L->dmem + o_unit_of);
+    L->wl.reset(new WaveLoop(ctx));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->ring, sizeof(DevRun) * kRing, cudaHostAllocMapped));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->flags, sizeof(int) * (1 + 2 * kRing), cudaHostAllocMapped));
     memset(L->ring, 0, sizeof(DevRun) * kRing);
@@ -746,8 +583,7 @@ struct Server::Impl {
     r.share = std::max(q.call.share, 1);
     r.ngroups = q.F * q.P;
     L.ring[slot] = r;
-    k_mark_ready<<<1, 1, 0, s_copy>>>(L.d_flags + 1 + slot);
-    PRNU_CUDA_TRY(cudaGetLastError());
+    launch_mark_ready(L.d_flags + 1 + slot, s_copy);
     std::atomic_thread_fence(std::memory_order_seq_cst);
     q.loop = &L;
     q.ring_pos = L.appended;
@@ -757,141 +593,34 @@ struct Server::Impl {
     L.runs.push_back(qp);
   }
 
-  // The wave kernels of one branch of the loop body, captured into `into`:
-  // grids sized for `items` candidates and `nunits` forward units (the unit
-  // slots follow the items' slots), the live counts read on the device.
-  void capture_wave(DevLoop& L, cudaGraph_t into, bool units, int items, int nunits) {
-    const int H = L.key.H, W = L.key.W;
-    const FftPlan prow = make_plan(W, ctx->tw_off), pcol = make_plan(H, ctx->tw_off);
-    int rowT, rowMB;
-    row_launch_shape(prow, &rowT, &rowMB);
-    PassArgs a{};
-    a.err = ctx->d_err;
-    a.rdtype = L.key.dtype;
-    const ResidLayout lay = padded_layout(H, W);
-    a.rpitch = lay.rpitch;
-    a.fpitch = lay.fpitch;
-    a.roff = lay.roff;
-    a.H = H;
-    a.W = W;
-    a.nitems = items;
-    a.spec = ws_spec;
-    a.stats = ws_stats;
-    a.fps = d_fpdesc;
-    a.scale = d_scale;
-    a.tw = ctx->d_tw;
-    a.prow = prow;
-    a.pcol = pcol;
-    a.pairs_per_block = L.tn.ppb;
-    a.col_log2 = L.tn.col_log2;
-    a.row_threads = rowT;
-    a.item_ptrs = L.d_items;
-    a.result_ptrs = L.d_results;
-    a.frame_ptrs = d_frame_ptrs;
-    a.units = units ? L.d_units : nullptr;
-    a.unit_of = units ? L.d_unit_of : nullptr;
-    a.nunits = nunits;
-    a.share = 1;
-    a.fp_f32 = L.key.dtype == kF32 ? 1 : 0;   // half residuals: FP16 fingerprints expected (FP32 ones still correct)
-    a.d_counts = L.d_st->counts;
-    LaunchCounter lc;
-    PRNU_CUDA_TRY(cudaStreamBeginCaptureToGraph(s_cap, into, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    try {
-      launch_fixed_wave(a, *L.fs, L.tn.variant, s_cap, lc);
-    } catch (...) {
-      cudaGraph_t g;
-      cudaStreamEndCapture(s_cap, &g);
-      cudaGetLastError();
-      throw;
-    }
-    cudaGraph_t g;
-    PRNU_CUDA_TRY(cudaStreamEndCapture(s_cap, &g));
-  }
-
-  // The branches of a loop body: plain and shared-forward waves with grids of
-  // 16, 32, ... up to `wave` items (and, shared, as many or fewer units),
-  // within `slots` workspace spectra (a shared wave takes items + units).
-  static CaseTable case_table(int wave, int slots) {
-    std::vector<int> caps;
-    for (int c = 16; c < wave; c *= 2) caps.push_back(c);
-    caps.push_back(wave);
-    CaseTable ct{};
-    auto add = [&](int g, int it, int un) {
-      if (ct.n >= kMaxCases) return;
-      ct.grouped[ct.n] = g;
-      ct.items[ct.n] = it;
-      ct.units[ct.n] = un;
-      ++ct.n;
-    };
-    for (int it : caps)
-      if (it <= slots) add(0, it, it);
-    for (int it : caps)
-      for (int un : caps)
-        if (un <= it && it + un <= slots) add(1, it, un);
-    return ct;
-  }
-
-  // loop begin -> WHILE { scheduler -> SWITCH { wave branches } -> completion }
-  void build_loop(DevLoop& L) {
-    if (L.exec) cudaGraphExecDestroy(L.exec);
-    if (L.graph) cudaGraphDestroy(L.graph);
-    L.exec = nullptr;
-    L.graph = nullptr;
-    cudaGraph_t g;
-    PRNU_CUDA_TRY(cudaGraphCreate(&g, 0));
-    L.graph = g;
-    cudaGraphConditionalHandle h_loop, h_case;
-    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
-    PRNU_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_case, g, 0, cudaGraphCondAssignDefault));
-    const size_t spec_slot = (size_t)L.key.H * (L.key.W / 2) * sizeof(float2);
-    CaseTable ct = case_table(L.wave, (int)std::min<size_t>(ws_spec_bytes / spec_slot, 1 << 20));
-    if (ct.n == 0) throw Error{PRNU_ENOMEM, "no workspace for a wave of this frame size"};
-    auto kernel_node = [](cudaGraphNode_t* n, cudaGraph_t gr, const cudaGraphNode_t* dep, void* fn, int grid,
-                          int block, void** args) {
-      cudaKernelNodeParams kp{};
-      kp.func = fn;
-      kp.gridDim = dim3(grid);
-      kp.blockDim = dim3(block);
-      kp.sharedMemBytes = 0;
-      kp.kernelParams = args;
-      PRNU_CUDA_TRY(cudaGraphAddKernelNode(n, gr, dep, dep ? 1 : 0, &kp));
-    };
-    cudaGraphNode_t n_begin, n_loop, n_sched, n_if, n_done;
-    DevSched* d_st = L.d_st;
-    void* bargs[] = {&d_st};
-    kernel_node(&n_begin, g, nullptr, (void*)k_loop_begin, 1, 1, bargs);
-    cudaGraphNodeParams wp{};
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = h_loop;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    PRNU_CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_begin, nullptr, 1, &wp));
-    cudaGraph_t body = wp.conditional.phGraph_out[0];
-    const DevRun* d_ring = L.d_ring;
-    const int* d_tail = L.d_flags;
-    const int* d_ready = L.d_flags + 1;
-    int* d_done = L.d_flags + 1 + kRing;
-    int wave = L.wave, H = L.key.H, W = L.key.W;
-    const WorkItem** d_items = L.d_items;
-    CandResult** d_results = L.d_results;
-    int* d_units = L.d_units;
-    int* d_unit_of = L.d_unit_of;
-    void* sargs[] = {&d_st, &d_ring, &d_tail, &d_ready, &wave, &d_items, &d_results, &d_units, &d_unit_of,
-                     &h_loop, &h_case, &ct};
-    kernel_node(&n_sched, body, nullptr, (void*)k_sched, 1, 32, sargs);
-    cudaGraphNodeParams ip{};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = h_case;
-    ip.conditional.type = cudaGraphCondTypeSwitch;
-    ip.conditional.size = (unsigned)ct.n;
-    PRNU_CUDA_TRY(cudaGraphAddNode(&n_if, body, &n_sched, nullptr, 1, &ip));
-    for (int k = 0; k < ct.n; ++k)
-      capture_wave(L, ip.conditional.phGraph_out[k], ct.grouped[k] != 0, ct.items[k], ct.units[k]);
-    const DevSched* d_stc = d_st;
-    void* cargs[] = {&d_stc, &d_ring, &d_done, &H, &W};
-    kernel_node(&n_done, body, &n_if, (void*)k_complete, kMaxWave, 256, cargs);
-    PRNU_CUDA_TRY(cudaGraphInstantiate(&L.exec, g, 0));
-    L.built_gen = ws_gen;
+  // What the size class's graph holds fixed: the shared tables, the current
+  // workspace, the ring and its flags.
+  WaveLoopConfig loop_config(const DevLoop& L) const {
+    WaveLoopConfig c;
+    c.fs = L.fs;
+    c.variant = L.tn.variant;
+    c.ppb = L.tn.ppb;
+    c.col_log2 = L.tn.col_log2;
+    c.H = L.key.H;
+    c.W = L.key.W;
+    c.rdtype = L.key.dtype;
+    c.wave = L.wave;
+    c.budget = kLoopWaves;
+    c.fp_f32 = L.key.dtype == kF32 ? 1 : 0;   // half residuals: FP16 fingerprints expected (FP32 ones still correct)
+    c.spec = ws_spec;
+    c.stats = ws_stats;
+    const size_t slot = (size_t)L.key.H * (L.key.W / 2) * sizeof(float2);
+    c.spec_slots = (int)std::min<size_t>(ws_spec_bytes / slot, 1 << 20);
+    c.frame_ptrs = d_frame_ptrs;
+    c.fps = d_fpdesc;
+    c.scale = d_scale;
+    c.err = ctx->d_err;
+    c.ring = L.d_ring;
+    c.tail = L.d_flags;
+    c.ready = L.d_flags + 1;
+    c.done = L.d_flags + 1 + kRing;
+    c.ring_size = kRing;
+    return c;
   }
 
   // One launch at a time on the compute stream: when the previous one has
@@ -919,8 +648,8 @@ struct Server::Impl {
     }
     if (!best) return;
     try {
-      if (!best->exec || best->built_gen != ws_gen) build_loop(*best);
-      PRNU_CUDA_TRY(cudaGraphLaunch(best->exec, s_comp));
+      best->wl->ensure(loop_config(*best));
+      best->wl->launch(s_comp);
       PRNU_CUDA_TRY(cudaEventRecord(loop_ev, s_comp));
       loop_running = true;
       st.server_launches += 1;

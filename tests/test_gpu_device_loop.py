@@ -116,3 +116,58 @@ def test_loop_mode_rules(prnu):
         with pytest.raises(prnu.PrnuError) as e:
             ctx.prnu_server_set_loop(prnu.PRNU_LOOP_HOST)      # the server has started
         assert e.value.code == prnu.PRNU_EINVAL
+
+
+# ------------------------------------------------------------------ eis_grid_search in one graph launch
+
+def _grid_search(ctx, prnu, wl, fps, windows, dtype, persistent, wave=64):
+    H, W = wl.frames.shape[1:]
+    half = dtype != torch.float32
+    frames = torch.from_numpy(wl.frames).to(DEV)
+    R = torch.empty(frames.shape, dtype=dtype, device=DEV)
+    sc = torch.empty(frames.shape[0], device=DEV)
+    ctx.prnu_residual(frames, R, scale=sc,
+                      flags=prnu.PRNU_WEIGHT_BY_INTENSITY | (prnu.PRNU_NORMALISE if half else 0))
+    hs = [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(DEV), prnu.PRNU_F16 if half else prnu.PRNU_F32)
+          for K in fps]
+    t0 = ctx.prnu_get_tuning(H, W)
+    try:
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], wave, t0["variant"], persistent, 1,
+                            t0["share_forward"])
+        out = []
+        for _ in range(2):   # the second call replays the graph built by the first
+            allp = torch.empty((len(wl.frames), len(hs), wl.grid.size), dtype=torch.float64, device=DEV)
+            res = ctx.eis_grid_search(R, hs, wl.grid, windows=windows, scale=sc, all_pce=allp)
+            torch.cuda.synchronize()
+            out.append((res.tobytes(), allp.cpu().numpy()))
+    finally:
+        ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                            t0["persistent"], t0["streams"], t0["share_forward"])
+        for h in hs:
+            ctx.prnu_fingerprint_release(h)
+    assert out[0][0] == out[1][0]
+    return out[0]
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float16"])
+@pytest.mark.parametrize("H,W", [(256, 256), (720, 1280), (1080, 1920), (2160, 3840)])
+def test_grid_search_in_one_graph_launch_equals_waves(prnu, H, W, dtype):
+    """prnu_tuning.persistent = 2 runs every wave of an eis_grid_search call in
+    one graph launch (the device-resident loop over the call's work list):
+    the same results as the wave launches, bit for bit, with one fingerprint
+    (full grid at 256x256, several waves) and with three sharing forward units
+    (windows)."""
+    dt = getattr(torch, dtype)
+    with prnu.Context(0) as ctx:
+        if H == 256:
+            wl = synth.make_workload(1, F=2)
+            fps, win = [wl.fingerprints[0]], None
+        else:
+            wl = synth.make_workload(2, H=H, W=W, F=2, on_grid=True, s_max=min(16, H // 8))
+            fps = [wl.fingerprints[0], synth.fingerprint_field(H, W, np.random.default_rng(3)),
+                   synth.fingerprint_field(H, W, np.random.default_rng(4))]
+            win = synth.snap_windows(wl.grid, wl.planted[:, :2], np.array([1, 2]))
+        g_res, g_all = _grid_search(ctx, prnu, wl, fps, win, dt, 2)
+        w_res, w_all = _grid_search(ctx, prnu, wl, fps, win, dt, 0)
+    assert g_res == w_res
+    np.testing.assert_array_equal(g_all, w_all)
