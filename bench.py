@@ -558,8 +558,10 @@ def batched_leg(ctx, prnu, dev, F, dtype, steps, warmup, autotune_ms=0.0, persis
 
     peak, kind = hbm_peak()
     pb = path_bytes(H, W, s_in, s_k)
-    paths = {}
-    for pers in ((0, 1) if persistent else (0,)):
+    paths, outs = {}, {}
+    names = {0: "waves", 1: "persistent", 2: "graph"}
+    # 0: a launch sequence per wave; 1: the persistent kernel; 2: every wave in one graph launch
+    for pers in ((0, 1, 2) if persistent else (0,)):
         t = dict(tuning, persistent=pers)
         ctx.prnu_set_tuning(H, W, t["col_width"], t["pairs_per_block"], t["wave"], t["variant"], pers, t["streams"])
         ms, prof = _timed_steps(step, steps, warmup, dev, ctx)
@@ -568,7 +570,8 @@ def batched_leg(ctx, prnu, dev, F, dtype, steps, warmup, autotune_ms=0.0, persis
         hits = int(sum(abs(float(res[f]["lam"]) - wl.planted[f, 0]) <= wl.grid.dlam / 2 + 1e-6 and
                        abs(float(res[f]["th_deg"]) - wl.planted[f, 1]) <= wl.grid.dth_deg / 2 + 1e-6
                        for f in range(F)))
-        paths["persistent" if pers else "waves"] = {
+        outs[pers] = out_d.cpu().numpy().tobytes()
+        paths[names[pers]] = {
             "value": round(value, 1), "ms_per_step": round(ms, 2),
             "path_roofline": {"bytes_per_candidate": pb, "achieved": round(pb * value / 1e9, 1),
                               "frac": round(pb * value / 1e9 / peak, 4)},
@@ -582,6 +585,7 @@ def batched_leg(ctx, prnu, dev, F, dtype, steps, warmup, autotune_ms=0.0, persis
                steps=steps, warmup=warmup, peak=f"{peak} GB/s {kind}", tuning=tuning)
     if persistent:
         out["persistent"] = paths["persistent"]
+        out["graph"] = dict(paths["graph"], results_identical_to_waves=outs[2] == outs[0])
     if naive:
         # the plain per-candidate FP32 path on the first 4 frames' windows (same inputs)
         R32 = torch.empty((4, H, W), device=dev)
@@ -605,9 +609,11 @@ def batched_leg(ctx, prnu, dev, F, dtype, steps, warmup, autotune_ms=0.0, persis
 
 def run_batched(args):
     """Config 3: 256 full-HD frames in one call, +-k warm-start windows; FP32
-    (the configuration) or, with --dtype f16/bf16, FP16/BF16 storage.  Both the
-    wave launches and the single persistent launch are timed; the plain
-    per-candidate FP32 path runs on a sample of the same inputs."""
+    (the configuration) or, with --dtype f16/bf16, FP16/BF16 storage.  Three
+    launch modes are timed: a launch sequence per wave, the single persistent
+    kernel, and every wave in one CUDA graph launch (the device-resident loop,
+    whose results must equal the waves').  The plain per-candidate FP32 path
+    runs on a sample of the same inputs."""
     import torch
     import paper_2207_14507_gb300 as prnu
     prnu.build()

@@ -427,9 +427,15 @@ typedef struct {
     int wave;             /* candidates in flight, >= 1 */
     int variant;          /* compile-time-planned column kernel variant for this size
                              (0.. n-1), or -1 for the generic runtime-plan kernels */
-    int persistent;       /* 1: sizes with compile-time-planned kernels run a whole call
+    int persistent;       /* 0: waves, one launch sequence each (default).
+                             1: sizes with compile-time-planned kernels run a whole call
                              as one persistent launch that schedules every phase of every
-                             candidate as tasks (spectra stay in L2); 0: waves */
+                             candidate as tasks (spectra stay in L2).
+                             2: sizes with compile-time-planned kernels run every wave of a
+                             call in one CUDA graph launch: a scheduler kernel forms each
+                             wave on the device and picks the branch of the graph whose
+                             grids fit it (the device-resident loop of the query server,
+                             over one run).  Results equal those of 0 bit for bit. */
     int streams;          /* 1 or 2: waves of compile-time-planned sizes alternate between
                              the call's stream and a second stream of the context, each
                              with its own half of the workspace, so that one wave's

@@ -54,75 +54,95 @@ __device__ __forceinline__ int fit_case(const CaseTable& ct, int count, int nuni
 // One wave: up to `wave` candidates of the ready runs in ring order, whole
 // forward units only (as many as a branch of the body holds), into the wave
 // tables; the smallest branch that holds it; the loop goes on while it found
-// candidates and the launch's wave budget (0: none) lasts.  One thread.
-__global__ void k_sched(DevSched* st, const DevRun* ring, int ring_size, const int* tail_p, const int* ready,
-                        int wave, int budget, const WorkItem** item_ptrs, CandResult** result_ptrs, int* units,
-                        int* unit_of, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_case,
-                        CaseTable ct) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int tail = ld_acquire_sys(tail_p);
-  int head = st->head, next = st->next, count = 0, nunits = 0, ncomp = 0;
-  bool grouped = false;
-  while (count < wave && ncomp < kLoopMaxWave && head != tail) {
-    const int slot = head % ring_size;
-    if (ld_acquire_sys(ready + slot) == 0) break;   // ingest still running: keep arrival order
-    const DevRun r = ring[slot];
-    if (r.n <= 0) {                                  // nothing to score: complete at once
-      st->complete[ncomp++] = head;
-      ++head;
-      next = 0;
-      continue;
+// candidates and the launch's wave budget (0: none) lasts.  One warp: lane 0
+// plans the wave as segments (a run's next candidates), all lanes write the
+// tables.
+struct Segment {
+  const WorkItem* items;
+  CandResult* results;
+  int count0, nunits0, take, S;
+};
+
+__global__ void __launch_bounds__(32) k_sched(DevSched* st, const DevRun* ring, int ring_size, const int* tail_p,
+                                              const int* ready, int wave, int budget, const WorkItem** item_ptrs,
+                                              CandResult** result_ptrs, int* units, int* unit_of,
+                                              cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_case,
+                                              CaseTable ct) {
+  __shared__ Segment seg[kLoopMaxWave];
+  __shared__ int s_nseg;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    const int tail = ld_acquire_sys(tail_p);
+    int head = st->head, next = st->next, count = 0, nunits = 0, ncomp = 0, nseg = 0;
+    bool grouped = false;
+    while (count < wave && ncomp < kLoopMaxWave && head != tail) {
+      const int slot = head % ring_size;
+      if (ld_acquire_sys(ready + slot) == 0) break;   // ingest still running: keep arrival order
+      const DevRun r = ring[slot];
+      if (r.n <= 0) {                                  // nothing to score: complete at once
+        st->complete[ncomp++] = head;
+        ++head;
+        next = 0;
+        continue;
+      }
+      const int S = max(r.share, 1);
+      int take = min(wave - count, r.n - next) / S * S;
+      while (take > 0 && fit_case(ct, count + take, nunits + take / S, grouped || S > 1) == ct.n) take -= S;
+      if (take == 0) break;
+      seg[nseg++] = Segment{r.items + next, r.results + next, count, nunits, take, S};
+      grouped = grouped || S > 1;
+      count += take;
+      nunits += take / S;
+      next += take;
+      if (next == r.n) {
+        st->complete[ncomp++] = head;
+        ++head;
+        next = 0;
+      }
     }
-    const int S = max(r.share, 1);
-    int take = min(wave - count, r.n - next) / S * S;
-    while (take > 0 && fit_case(ct, count + take, nunits + take / S, grouped || S > 1) == ct.n) take -= S;
-    if (take == 0) break;
-    for (int k = 0; k < take; ++k) {
-      item_ptrs[count + k] = r.items + next + k;
-      result_ptrs[count + k] = r.results + next + k;
-    }
-    for (int u = 0; u < take / S; ++u) {
-      units[nunits] = count + u * S;
-      for (int k = 0; k < S; ++k) unit_of[count + u * S + k] = nunits;
-      ++nunits;
-    }
-    grouped = grouped || S > 1;
-    count += take;
-    next += take;
-    if (next == r.n) {
-      st->complete[ncomp++] = head;
-      ++head;
-      next = 0;
-    }
+    units[nunits] = count;
+    st->head = head;
+    st->next = next;
+    st->counts[0] = count;
+    st->counts[1] = grouped ? nunits : count;
+    st->ncomplete = ncomp;
+    const int waves = st->waves + 1;
+    st->waves = waves;
+    s_nseg = nseg;
+    const int c = count > 0 ? fit_case(ct, count, nunits, grouped) : ct.n;   // ct.n: no branch runs
+    cudaGraphSetConditional(h_case, (unsigned)c);
+    cudaGraphSetConditional(h_loop, count > 0 && (budget == 0 || waves < budget) ? 1u : 0u);
   }
-  units[nunits] = count;
-  st->head = head;
-  st->next = next;
-  st->counts[0] = count;
-  st->counts[1] = grouped ? nunits : count;
-  st->ncomplete = ncomp;
-  const int waves = st->waves + 1;
-  st->waves = waves;
-  const int c = count > 0 ? fit_case(ct, count, nunits, grouped) : ct.n;   // ct.n: no branch runs
+  __syncwarp();
+  const int nseg = s_nseg;
+  for (int q = 0; q < nseg; ++q) {
+    const Segment g = seg[q];
+    for (int k = lane; k < g.take; k += 32) {
+      item_ptrs[g.count0 + k] = g.items + k;
+      result_ptrs[g.count0 + k] = g.results + k;
+      unit_of[g.count0 + k] = g.nunits0 + k / g.S;
+    }
+    for (int u = lane; u < g.take / g.S; u += 32) units[g.nunits0 + u] = g.count0 + u * g.S;
+  }
   __threadfence();
-  cudaGraphSetConditional(h_case, (unsigned)c);
-  cudaGraphSetConditional(h_loop, count > 0 && (budget == 0 || waves < budget) ? 1u : 0u);
 }
 
 // The arg-max of every run the wave finished, into its result buffer, then
-// its done flag.  One block per finished run.
+// its done flag.  Block b takes finished runs b, b + gridDim.x, ...
 __global__ void k_complete(const DevSched* st, const DevRun* ring, int ring_size, int* done, int H, int W) {
-  const int c = blockIdx.x;
-  if (c >= st->ncomplete) return;
-  const int slot = st->complete[c] % ring_size;
-  const DevRun r = ring[slot];
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int g = threadIdx.x >> 5; g < r.ngroups; g += nw)
-    argmax_group(r.results, r.items, r.groups, max(r.share, 1), r.out, H, W, g, lane);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence_system();
-    st_release_sys(done + slot, 1);
+  const int ncomp = st->ncomplete;
+  for (int c = blockIdx.x; c < ncomp; c += gridDim.x) {
+    const int slot = st->complete[c] % ring_size;
+    const DevRun r = ring[slot];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int g = threadIdx.x >> 5; g < r.ngroups; g += nw)
+      argmax_group(r.results, r.items, r.groups, max(r.share, 1), r.out, H, W, g, lane);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      st_release_sys(done + slot, 1);
+    }
+    __syncthreads();
   }
 }
 
@@ -312,7 +332,7 @@ void WaveLoop::build() {
   for (int k = 0; k < ct.n; ++k) capture(sp.conditional.phGraph_out[k], ct.grouped[k] != 0, ct.items[k], ct.units[k]);
   const DevSched* d_stc = d_st;
   void* cargs[] = {&d_stc, &ring, &ring_size, &done, &H, &W};
-  kernel_node(&n_done, body, &n_switch, (void*)k_complete, kLoopMaxWave, 256, cargs);
+  kernel_node(&n_done, body, &n_switch, (void*)k_complete, 64, 256, cargs);
   PRNU_CUDA_TRY(cudaGraphInstantiate(&exec_, g, 0));
   built_ = true;
 }
