@@ -182,8 +182,11 @@ struct Server::Impl {
   };
   bool dev_mode = false;
   std::map<SizeKey, std::unique_ptr<DevLoop>> loops;   // nullptr: no planned kernels, host waves
+  std::vector<std::unique_ptr<DevLoop>> retired;      // loops a device error retired
   cudaEvent_t loop_ev = nullptr;
   bool loop_running = false;
+  DevLoop* loop_last = nullptr;    // the loop of the last launch
+  int* h_loop_err = nullptr;       // pinned: the device flag after the last launch
 
   explicit Impl(prnu_ctx* c) : ctx(c) {
     PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&s_comp, cudaStreamNonBlocking));
@@ -201,7 +204,11 @@ struct Server::Impl {
     // mapped: the device loop's completion kernel writes query results here
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&arena, kArenaBlock * kArenaBlocks, cudaHostAllocMapped));
     dev_mode = ctx->server_loop == PRNU_LOOP_DEVICE;
-    if (dev_mode) PRNU_CUDA_TRY(cudaEventCreateWithFlags(&loop_ev, cudaEventDisableTiming));
+    if (dev_mode) {
+      PRNU_CUDA_TRY(cudaEventCreateWithFlags(&loop_ev, cudaEventDisableTiming));
+      PRNU_CUDA_TRY(cudaHostAlloc((void**)&h_loop_err, sizeof(int), cudaHostAllocDefault));
+      *h_loop_err = 0;
+    }
     for (auto& w : waves) {
       PRNU_CUDA_TRY(cudaHostAlloc((void**)&w.h_tab, kWaveTabBytes, cudaHostAllocDefault));
       w.d_tab = reinterpret_cast<void**>(ctx_alloc(ctx, kWaveTabBytes));
@@ -222,14 +229,15 @@ struct Server::Impl {
     cudaStreamSynchronize(s_comp);
     for (auto& q : admitted) release(*q);
     cudaStreamSynchronize(s_comp);
-    for (auto& kv : loops) {
-      DevLoop* L = kv.second.get();
+    for (auto& kv : loops) retired.push_back(std::move(kv.second));
+    for (auto& L : retired) {
       if (!L) continue;
       L->wl.reset();
       if (L->ring) cudaFreeHost(L->ring);
       if (L->flags) cudaFreeHost(L->flags);
     }
     if (loop_ev) cudaEventDestroy(loop_ev);
+    if (h_loop_err) cudaFreeHost(h_loop_err);
     for (auto& w : waves) {
       cudaFreeHost(w.h_tab);
       ctx_free(ctx, w.d_tab, kWaveTabBytes);
@@ -542,6 +550,11 @@ struct Server::Impl {
   DevLoop* loop_for(const Query& q) {
     const SizeKey key{q.H, q.W, q.dtype};
     auto it = loops.find(key);
+    if (it != loops.end() && it->second && it->second->dead) {
+      retired.push_back(std::move(it->second));   // kept until its queries are reported
+      loops.erase(it);
+      it = loops.end();
+    }
     if (it != loops.end()) return it->second.get();
     const FixedShape* fs = q.tn.variant >= 0 ? find_fixed(q.H, q.W) : nullptr;
     if (!fs || !fixed_supports(*fs, q.H, q.tn.ppb)) {
@@ -615,6 +628,7 @@ struct Server::Impl {
     c.fps = d_fpdesc;
     c.scale = d_scale;
     c.err = ctx->d_err;
+    c.stall = ctx->debug_stall;
     c.ring = L.d_ring;
     c.tail = L.d_flags;
     c.ready = L.d_flags + 1;
@@ -630,6 +644,16 @@ struct Server::Impl {
     if (loop_running) {
       if (cudaEventQuery(loop_ev) == cudaErrorNotReady) return;
       loop_running = false;
+      if (*h_loop_err && loop_last) {
+        // a bounded device-side wait gave up in that launch: its size class's
+        // unreported queries fail, and the loop is not used again
+        *h_loop_err = 0;
+        PRNU_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s_comp));
+        loop_last->dead = true;
+        const Error e{PRNU_EDEVICE_ABORT, "a bounded device-side wait timed out in the server's loop"};
+        for (auto& qp : loop_last->runs)
+          if (!qp->reported && !qp->gpu_done.load()) fail(*qp, e);
+      }
     }
     DevLoop* best = nullptr;
     Clock::time_point oldest = Clock::time_point::max();
@@ -650,7 +674,9 @@ struct Server::Impl {
     try {
       best->wl->ensure(loop_config(*best));
       best->wl->launch(s_comp);
+      PRNU_CUDA_TRY(cudaMemcpyAsync(h_loop_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s_comp));
       PRNU_CUDA_TRY(cudaEventRecord(loop_ev, s_comp));
+      loop_last = best;
       loop_running = true;
       st.server_launches += 1;
     } catch (const Error& e) {
@@ -790,7 +816,10 @@ struct Server::Impl {
       Query& q = *admitted[i];
       if (q.loop && !q.failed && !q.gpu_done.load()) {
         const volatile int* fl = q.loop->flags;
-        if (fl[1 + kRing + (int)(q.ring_pos % kRing)]) {
+        const int dv = fl[1 + kRing + (int)(q.ring_pos % kRing)];
+        if (dv == 2) {
+          fail(q, Error{PRNU_EDEVICE_ABORT, "a bounded device-side wait timed out in the server's loop"});
+        } else if (dv) {
           std::atomic_thread_fence(std::memory_order_acquire);
           q.t_done = Clock::now();
           q.gpu_done.store(1);

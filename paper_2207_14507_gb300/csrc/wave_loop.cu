@@ -128,8 +128,11 @@ __global__ void __launch_bounds__(32) k_sched(DevSched* st, const DevRun* ring, 
 }
 
 // The arg-max of every run the wave finished, into its result buffer, then
-// its done flag.  Block b takes finished runs b, b + gridDim.x, ...
-__global__ void k_complete(const DevSched* st, const DevRun* ring, int ring_size, int* done, int H, int W) {
+// its done flag: 1, or 2 if a bounded device-side wait has given up (the
+// context's error flag err is raised: the results are not to be trusted).
+// Block b takes finished runs b, b + gridDim.x, ...
+__global__ void k_complete(const DevSched* st, const DevRun* ring, int ring_size, int* done, const int* err, int H,
+                           int W) {
   const int ncomp = st->ncomplete;
   for (int c = blockIdx.x; c < ncomp; c += gridDim.x) {
     const int slot = st->complete[c] % ring_size;
@@ -139,8 +142,9 @@ __global__ void k_complete(const DevSched* st, const DevRun* ring, int ring_size
       argmax_group(r.results, r.items, r.groups, max(r.share, 1), r.out, H, W, g, lane);
     __syncthreads();
     if (threadIdx.x == 0) {
+      const int bad = err != nullptr && ld_acquire_sys(err) != 0;
       __threadfence_system();
-      st_release_sys(done + slot, 1);
+      st_release_sys(done + slot, bad ? 2 : 1);
     }
     __syncthreads();
   }
@@ -331,7 +335,8 @@ void WaveLoop::build() {
   PRNU_CUDA_TRY(cudaGraphAddNode(&n_switch, body, &n_sched, nullptr, 1, &sp));
   for (int k = 0; k < ct.n; ++k) capture(sp.conditional.phGraph_out[k], ct.grouped[k] != 0, ct.items[k], ct.units[k]);
   const DevSched* d_stc = d_st;
-  void* cargs[] = {&d_stc, &ring, &ring_size, &done, &H, &W};
+  const int* err = c.err;
+  void* cargs[] = {&d_stc, &ring, &ring_size, &done, &err, &H, &W};
   kernel_node(&n_done, body, &n_switch, (void*)k_complete, 64, 256, cargs);
   PRNU_CUDA_TRY(cudaGraphInstantiate(&exec_, g, 0));
   built_ = true;

@@ -61,7 +61,7 @@ struct WaveLoopConfig {
   const DevRun* ring = nullptr;             // ring_size runs, device-accessible
   const int* tail = nullptr;                // runs appended so far
   const int* ready = nullptr;               // [ring_size] ingest complete
-  int* done = nullptr;                      // [ring_size] completion flags
+  int* done = nullptr;                      // [ring_size] completion flags (2: an error was raised)
   int ring_size = 1;
   bool same(const WaveLoopConfig& o) const;
 };

@@ -7,7 +7,11 @@ kernel's dependency counts).  Each wait gives up after about a second, the
 kernel raises the context's error flag and abandons its candidate.  A call
 that returns its results to the host fails with PRNU_EDEVICE_ABORT itself; a
 call that leaves them on the device returns, and the next call fails.  Either
-way the context then works again and gives the same results as before."""
+way the context then works again and gives the same results as before.  This
+holds for the wave launches, the persistent kernel and the one-graph launch
+(persistent = 0, 1, 2).  In the query server's device-resident loop, a query
+whose wave saw the flag fails at query_poll, and the next queries of that
+size run in a fresh loop."""
 import numpy as np
 import pytest
 
@@ -35,7 +39,7 @@ def _setup(ctx, prnu):
     return g, R, h
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_bounded_device_wait_runs_out_and_is_reported(prnu, persistent):
     with prnu.Context(0) as ctx:
         g, R, h = _setup(ctx, prnu)
@@ -65,3 +69,24 @@ def test_bounded_device_wait_runs_out_and_is_reported(prnu, persistent):
         with pytest.raises(prnu.PrnuError) as e:
             ctx.prnu_debug_set(99, 1)
         assert e.value.code == prnu.PRNU_EINVAL
+
+
+def test_server_device_loop_wait_runs_out_and_is_reported(prnu):
+    with prnu.Context(0) as ctx:
+        g, R, h = _setup(ctx, prnu)
+        wl = synth.make_workload(1, F=1, grid=g)
+        frames = torch.from_numpy(wl.frames).to(DEV)
+        flags = prnu.PRNU_WEIGHT_BY_INTENSITY
+
+        def serve():
+            qid = ctx.query_submit(frames, [h], g, dtype=prnu.PRNU_F32, flags=flags)
+            return ctx.query_poll(qid, 1, 1, timeout_us=120_000_000)
+
+        good = serve()
+        ctx.prnu_debug_set(prnu.PRNU_DEBUG_STALL_DEVICE_WAITS, 1)
+        with pytest.raises(prnu.PrnuError) as e:
+            serve()
+        assert e.value.code == prnu.PRNU_EDEVICE_ABORT
+        ctx.prnu_debug_set(prnu.PRNU_DEBUG_STALL_DEVICE_WAITS, 0)
+        again = serve()                                      # a fresh loop for this size
+        assert again.tobytes() == good.tobytes()
