@@ -498,7 +498,19 @@ def run_ours(args):
                                                                              "decisions_agree",
                                                                              "decisions_robust")}}
                      for n, v in pr["legs"].items()}}
-    ctx.close()
+        # the served mix (config 5's stream) through the device-resident loop:
+        # 8 queries at once, the oracle on 4 of them
+        ctx.close()
+        ctx = None
+        sv = serving_leg(prnu, dev, 8, 0, 0, 4, "device")
+        oc = sv["oracle_check"]
+        line["serving"] = {"workload": "served mix: the first 8 queries of the config-5 stream at once "
+                                       "(720p/1080p/4K, 8-64 frames, 1-16 fingerprints), FP16, device-resident loop",
+                           "loop": sv["loop"], "capacity": sv["runs"]["capacity"],
+                           "mean_fingerprints_per_query": sv["mean_fingerprints_per_query"],
+                           "oracle_check": {k: oc[k] for k in ("queries", "max_pce_rel_err", "local_argmax_ok")}}
+    if ctx is not None:
+        ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     job.close()
@@ -963,7 +975,7 @@ def run_precision(args):
     ctx.close()
 
 
-def run_serving(args):
+def serving_leg(prnu, dev, n_cap, n_st, n_ov, oracle_queries, loop="device", autotune_ms=0.0):
     """Config 5: Poisson query stream (720p/1080p/4K, 8-64 frames, 1-16
     fingerprints, one matching with probability 0.5, +-k windows, FP16
     storage, 120 GB admission budget).  Three runs through query_submit /
@@ -980,18 +992,14 @@ def run_serving(args):
     import oracle
     import synth
     from oracle.parallel import ScorePool, available_cores
-    import paper_2207_14507_gb300 as prnu
-    prnu.build()
-    dev = torch.device("cuda", 0)
-    n_cap, n_st, n_ov = args.queries, args.steady_queries, args.overload_queries
     queries, banks, pools = synth.make_query_stream(n_cap + n_st + n_ov, rate_hz=20.0, pool_frames=8,
                                                     match_sources=1, materialise=False)
     ctx = prnu.Context(0, hbm_budget_bytes=120 << 30)
-    ctx.prnu_server_set_loop(prnu.PRNU_LOOP_DEVICE if args.loop == "device" else prnu.PRNU_LOOP_HOST)
+    ctx.prnu_server_set_loop(prnu.PRNU_LOOP_DEVICE if loop == "device" else prnu.PRNU_LOOP_HOST)
     tunings = {}
     for (H, W) in banks:
-        tunings[f"{H}x{W}"] = ctx.prnu_autotune(H, W, prnu.PRNU_F16, budget_ms=args.autotune_ms) \
-            if args.autotune_ms > 0 else ctx.prnu_get_tuning(H, W)
+        tunings[f"{H}x{W}"] = ctx.prnu_autotune(H, W, prnu.PRNU_F16, budget_ms=autotune_ms) \
+            if autotune_ms > 0 else ctx.prnu_get_tuning(H, W)
     handles = {k: [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(dev), prnu.PRNU_F16) for K in bank]
                for k, bank in banks.items()}
     dpools = {k: torch.from_numpy(v).to(dev) for k, v in pools.items()}
@@ -1063,7 +1071,7 @@ def run_serving(args):
     # that node inside the window; one process pool per resolution
     t0 = time.perf_counter()
     g = synth.GRID_FULL
-    sample = list(range(n_cap, n_cap + n_st))[:args.oracle_queries]
+    sample = (list(range(n_cap, n_cap + n_st)) if n_st else list(range(n_cap)))[:oracle_queries]
     picks = []
     for i in sample:
         q = queries[i]
@@ -1108,12 +1116,24 @@ def run_serving(args):
                             "score highest within 2e-2, with the oracle's shift)",
                     "checks": checks}
     mean_fp = float(np.mean([len(q.fp_ids) for q in queries]))
-    print(json.dumps({"workload": "serving (config 5)", "metric": "served p50/p99 query latency",
-                      "loop": args.loop, "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
-                      "mean_fingerprints_per_query": round(mean_fp, 2), "budget_gb": 120,
-                      "admitted_bytes_peak": st["admitted_bytes_peak"], "server_launches": st["server_launches"],
-                      "dtype": "f16", "oracle_check": oracle_check, "tuning": tunings}), flush=True)
     ctx.close()
+    return {"workload": "serving (config 5)", "metric": "served p50/p99 query latency",
+            "loop": loop, "runs": out, "mean_candidates_per_query": round(float(np.mean(ncand)), 1),
+            "mean_fingerprints_per_query": round(mean_fp, 2), "budget_gb": 120,
+            "admitted_bytes_peak": st["admitted_bytes_peak"], "server_launches": st["server_launches"],
+            "dtype": "f16", "oracle_check": oracle_check, "tuning": tunings}
+
+
+def run_serving(args):
+    """Config 5 through the query server (serving_leg): --queries at once,
+    --steady-queries at 70% of capacity, --overload-queries at 20 queries/s,
+    the oracle on --oracle-queries served queries, --loop device|host."""
+    import torch
+    import paper_2207_14507_gb300 as prnu
+    prnu.build()
+    dev = torch.device("cuda", 0)
+    print(json.dumps(serving_leg(prnu, dev, args.queries, args.steady_queries, args.overload_queries,
+                                 args.oracle_queries, args.loop, args.autotune_ms)), flush=True)
 
 
 def main():
