@@ -199,9 +199,14 @@ WaveLoop::WaveLoop(prnu_ctx* ctx) : ctx_(ctx) {
   units_ = reinterpret_cast<int*>(dmem_ + o_units);
   unit_of_ = reinterpret_cast<int*>(dmem_ + o_unit_of);
   PRNU_CUDA_TRY(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+  PRNU_CUDA_TRY(cudaEventCreateWithFlags(&ev_, cudaEventDisableTiming));
 }
 
 WaveLoop::~WaveLoop() {
+  if (ev_) {
+    cudaEventSynchronize(ev_);
+    cudaEventDestroy(ev_);
+  }
   if (exec_) cudaGraphExecDestroy(exec_);
   if (graph_) cudaGraphDestroy(graph_);
   if (cap_) cudaStreamDestroy(cap_);
@@ -216,6 +221,7 @@ void WaveLoop::ensure(const WaveLoopConfig& c) {
 
 void WaveLoop::launch(cudaStream_t s) {
   PRNU_CUDA_TRY(cudaGraphLaunch(exec_, s));
+  PRNU_CUDA_TRY(cudaEventRecord(ev_, s));
   ctx_->launches.n++;
 }
 
@@ -279,6 +285,7 @@ void WaveLoop::capture(cudaGraph_t into, bool units, int items, int nunits) {
 
 // loop begin -> WHILE { scheduler -> SWITCH { wave branches } -> completion }
 void WaveLoop::build() {
+  if (exec_) PRNU_CUDA_TRY(cudaEventSynchronize(ev_));   // the last launch of the old graph has ended
   if (exec_) cudaGraphExecDestroy(exec_);
   if (graph_) cudaGraphDestroy(graph_);
   exec_ = nullptr;

@@ -89,6 +89,7 @@ class WaveLoop {
   int* units_ = nullptr;
   int* unit_of_ = nullptr;
   cudaStream_t cap_ = nullptr;
+  cudaEvent_t ev_ = nullptr;       // recorded after each launch: the graph is not destroyed before it
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t exec_ = nullptr;
   WaveLoopConfig cfg_{};

@@ -171,3 +171,33 @@ def test_grid_search_in_one_graph_launch_equals_waves(prnu, H, W, dtype):
         w_res, w_all = _grid_search(ctx, prnu, wl, fps, win, dt, 0)
     assert g_res == w_res
     np.testing.assert_array_equal(g_all, w_all)
+
+
+def test_graph_launch_rebuilt_between_asynchronous_calls(prnu):
+    """Two eis_grid_search calls with persistent = 2 and device outputs, back
+    to back without a synchronisation, whose scale tensors differ: the second
+    call rebuilds the graph while the first may still run (the old graph is
+    destroyed only after its last launch).  Both equal the wave launches."""
+    wl = synth.make_workload(1, F=2)
+    with prnu.Context(0) as ctx:
+        frames = torch.from_numpy(wl.frames).to(DEV)
+        R = torch.empty((2, 256, 256), device=DEV)
+        sc1 = torch.empty(2, device=DEV)
+        ctx.prnu_residual(frames, R, scale=sc1, flags=prnu.PRNU_WEIGHT_BY_INTENSITY)
+        sc2 = sc1.clone()
+        h = ctx.prnu_fingerprint_term(torch.from_numpy(wl.fingerprints[0]).to(DEV))
+        ref = ctx.eis_grid_search(R, [h], wl.grid, scale=sc1)
+        t0 = ctx.prnu_get_tuning(256, 256)
+        try:
+            ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], 16, t0["variant"], 2)
+            o1 = torch.empty((2, 32), dtype=torch.uint8, device=DEV)
+            o2 = torch.empty((2, 32), dtype=torch.uint8, device=DEV)
+            ctx.eis_grid_search(R, [h], wl.grid, scale=sc1, out=o1)
+            ctx.eis_grid_search(R, [h], wl.grid, scale=sc2, out=o2)
+            torch.cuda.synchronize()
+        finally:
+            ctx.prnu_set_tuning(256, 256, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                                t0["persistent"], t0["streams"], t0["share_forward"])
+            ctx.prnu_fingerprint_release(h)
+        for o in (o1, o2):
+            assert o.cpu().numpy().tobytes() == ref.tobytes()
