@@ -201,3 +201,36 @@ def test_graph_launch_rebuilt_between_asynchronous_calls(prnu):
             ctx.prnu_fingerprint_release(h)
         for o in (o1, o2):
             assert o.cpu().numpy().tobytes() == ref.tobytes()
+
+
+def test_correction_in_graph_launches_equals_waves(prnu):
+    """The iterative correction (Sec. 3.2) calls the search once per
+    iteration with a new work list (each pair's window around its last
+    estimate, pairs dropping out as they converge): with persistent = 2 each
+    of those calls is one graph launch, and the results and iteration counts
+    equal the wave launches' bit for bit."""
+    H, W = 720, 1280
+    wl = synth.make_workload(2, H=H, W=W, F=3)
+    fps = [wl.fingerprints[0], synth.fingerprint_field(H, W, np.random.default_rng(8))]
+    lam0 = np.round(wl.planted[:, 0] / 0.02) * 0.02
+    th0 = np.round(wl.planted[:, 1] / 0.5) * 0.5
+    init_l = np.repeat(lam0, 2).astype(np.float32)
+    init_t = np.repeat(th0, 2).astype(np.float32)
+    out = {}
+    with prnu.Context(0) as ctx:
+        frames = torch.from_numpy(wl.frames).to(DEV)
+        R = torch.empty(frames.shape, device=DEV)
+        ctx.prnu_residual(frames, R)
+        hs = [ctx.prnu_fingerprint_term(torch.from_numpy(K).to(DEV)) for K in fps]
+        t0 = ctx.prnu_get_tuning(H, W)
+        try:
+            for pers in (0, 2):
+                ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"], pers)
+                res, its = ctx.eis_correction(R, hs, init_l, init_t, max_iter=3, th_half1=20)
+                out[pers] = (res.tobytes(), its.tobytes())
+        finally:
+            ctx.prnu_set_tuning(H, W, t0["col_width"], t0["pairs_per_block"], t0["wave"], t0["variant"],
+                                t0["persistent"], t0["streams"], t0["share_forward"])
+            for h in hs:
+                ctx.prnu_fingerprint_release(h)
+    assert out[2] == out[0]
