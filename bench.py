@@ -642,8 +642,9 @@ def run_correction(args):
     with continuous planted transforms, started from a coarse estimate: 3
     iterations at most, the text's dense first angle grid (11 scales x 101
     angles, then 11 x 11 twice).  Reports
-    frames/s and candidates/s (nodes scored), the iterations used, and the FP64
-    oracle's candidates/s on a bounded sample of the first iteration's nodes."""
+    frames/s and candidates/s (nodes scored), the iterations used, the same
+    with the loop on the device (persistent = 2), and the FP64 oracle's
+    candidates/s on a bounded sample of the first iteration's nodes."""
     import torch
     import oracle
     import synth
@@ -672,6 +673,19 @@ def run_correction(args):
                                                         th_half1=50)
 
     ms = _timed_steps(step, args.steps, max(args.warmup, 1), dev)
+    host_out, host_its = state["out"].copy(), state["its"].copy()
+    # the same with the loop on the device (prnu_tuning.persistent = 2): the
+    # work lists written, scored (one graph launch each) and updated on the GPU
+    t_ = ctx.prnu_get_tuning(H, W)
+    ctx.prnu_set_tuning(H, W, t_["col_width"], t_["pairs_per_block"], t_["wave"], t_["variant"], 2, t_["streams"],
+                        t_["share_forward"])
+    ms_dev = _timed_steps(step, args.steps, max(args.warmup, 1), dev)
+    ctx.prnu_set_tuning(H, W, t_["col_width"], t_["pairs_per_block"], t_["wave"], t_["variant"], t_["persistent"],
+                        t_["streams"], t_["share_forward"])
+    same_nodes = bool(np.array_equal(host_its, state["its"]) and
+                      np.array_equal(host_out["lam"], state["out"]["lam"]) and
+                      np.array_equal(host_out["th_deg"], state["out"]["th_deg"]))
+    state["out"], state["its"] = host_out, host_its
     its = state["its"][:, 0]
     nodes = int(sum(11 * 101 + 121 * (int(k) - 1) for k in its))
     out = state["out"][:, 0]
@@ -697,6 +711,9 @@ def run_correction(args):
         "workload": "correction-1080p (Sec. 3.2 iterative search)", "metric": "frames/s",
         "value": round(F / (ms / 1e3), 3), "frames": F, "ms_per_step": round(ms, 2), "steps": args.steps,
         "candidates_per_s": round(nodes / (ms / 1e3), 1), "nodes_per_step": nodes,
+        "device_loop": {"value": round(F / (ms_dev / 1e3), 3), "ms_per_step": round(ms_dev, 2),
+                        "candidates_per_s": round(nodes / (ms_dev / 1e3), 1),
+                        "same_nodes_and_iterations_as_host_loop": same_nodes},
         "iterations": [int(k) for k in its], "max_abs_error_vs_planted": {"lam": err_l, "th_deg": err_t},
         "path_roofline_frac": round(path_bytes(H, W, 4, 8) * nodes / (ms / 1e3) / 1e9 / peak, 4),
         "peak": f"{peak} GB/s {kind}", "tuning": tuning, "cpu_baseline": cpu, "dtype": "f32",

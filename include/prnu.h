@@ -435,7 +435,10 @@ typedef struct {
                              call in one CUDA graph launch: a scheduler kernel forms each
                              wave on the device and picks the branch of the graph whose
                              grids fit it (the device-resident loop of the query server,
-                             over one run).  Results equal those of 0 bit for bit. */
+                             over one run).  Results equal those of 0 bit for bit.
+                             eis_correction then runs its whole iteration loop on the
+                             device: work lists written, scored (one graph launch each)
+                             and updated by kernels, one synchronisation at the end. */
     int streams;          /* 1 or 2: waves of compile-time-planned sizes alternate between
                              the call's stream and a second stream of the context, each
                              with its own half of the workspace, so that one wave's

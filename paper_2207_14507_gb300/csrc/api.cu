@@ -570,6 +570,206 @@ static void add_pair_items(SearchCall& call, int f, int p, int group, const std:
   }
 }
 
+// ---------------------------------------------------------------- the correction as a device-side loop
+
+namespace {
+
+constexpr int kCorrHalfLam = 5;   // lambda nodes either side of the estimate (11 in all)
+
+// Iteration work list on the device: for every active (frame, fingerprint)
+// pair, in pair order, the 11 x (2 hb + 1) nodes around its estimate (the
+// same float nodes and warp coefficients as add_pair_items); the pairs'
+// order (who), their group table and the one-graph search's run descriptor
+// (its arg-max per pair into out).  One block.
+__global__ void k_corr_gen(int G, int P, const int* __restrict__ active, const float* __restrict__ cl,
+                           const float* __restrict__ ct, float sl, float st, int hb, WorkItem* __restrict__ items,
+                           CandResult* results, int* __restrict__ group_start, int* __restrict__ who,
+                           prnu_result* out, DevRun* run) {
+  __shared__ int s_nact;
+  const int nb = 2 * hb + 1, per = (2 * kCorrHalfLam + 1) * nb;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int g = 0; g < G; ++g)
+      if (active[g]) {
+        who[k] = g;
+        group_start[k] = k * per;
+        ++k;
+      }
+    group_start[k] = k * per;
+    s_nact = k;
+    DevRun r{};
+    r.items = items;
+    r.results = results;
+    r.groups = group_start;
+    r.out = out;
+    r.n = k * per;
+    r.share = 1;
+    r.ngroups = k;
+    *run = r;
+  }
+  __syncthreads();
+  const int n = s_nact * per;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int k = i / per, c = i - k * per, g = who[k];
+    const int a = c / nb, b = c - a * nb;
+    const float lam = (float)((double)cl[g] + (double)(a - kCorrHalfLam) * (double)sl);
+    const float th = (float)((double)ct[g] + (double)(b - hb) * (double)st);
+    const double L = (double)lam;
+    const double t = (double)th * 3.14159265358979323846 / 180.0;
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    WorkItem it;
+    it.frame = g / P;
+    it.fp = g % P;
+    it.cand = c;
+    it.group = k;
+    it.a11 = (float)(cs / L);
+    it.a12 = (float)(sn / L);
+    it.a21 = (float)(-sn / L);
+    it.a22 = (float)(cs / L);
+    it.lam = lam;
+    it.th_deg = th;
+    items[i] = it;
+  }
+}
+
+// After the iteration's search: per active pair, the best result so far, and
+// the next estimate, or the pair leaves the loop (its arg-max is the centre
+// node, or it found none).
+__global__ void k_corr_update(const DevRun* run, const int* __restrict__ who, const prnu_result* __restrict__ out,
+                              int centre, prnu_result* __restrict__ best, int* __restrict__ have,
+                              int* __restrict__ active, float* __restrict__ cl, float* __restrict__ ct,
+                              int* __restrict__ runs) {
+  const int nact = run->ngroups;
+  for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+    const int g = who[k];
+    const prnu_result r = out[k];
+    ++runs[g];
+    if (!have[g] || r.pce > best[g].pce) {
+      best[g] = r;
+      have[g] = 1;
+    }
+    if (r.cand_idx == centre || r.cand_idx < 0) {
+      active[g] = 0;
+    } else {
+      cl[g] = r.lam;
+      ct[g] = r.th_deg;
+    }
+  }
+}
+
+}  // namespace
+
+// The correction with its loop on the device (prnu_tuning.persistent = 2 on a
+// size with compile-time-planned kernels; false otherwise): per iteration a
+// kernel writes the work list of the active pairs, one graph launch scores it
+// (the wave loop over one run, its arg-max per pair in the completion
+// kernel), and a kernel updates the estimates.  max_iter iterations are
+// enqueued at once; an iteration with no active pair has no candidates and
+// its launch ends at once.  One synchronisation, at the end.
+static bool run_correction_device(prnu_ctx* c, const void* d_resid, int dtype, const float* d_scale, int F, int H,
+                                  int W, const std::vector<std::shared_ptr<Fingerprint>>& fps,
+                                  const std::vector<float>& cl, const std::vector<float>& ct, int max_iter,
+                                  int th_half1, prnu_result* out, int* iters, cudaStream_t s) {
+  const Tuning tn = tuning_for(c, H, W);
+  if (tn.persistent != 2 || tn.variant < 0) return false;
+  const FixedShape* fs = find_fixed(H, W);
+  if (!fs || !fixed_supports(*fs, H, tn.ppb)) return false;
+  const int P = (int)fps.size(), G = F * P, Wh = W / 2;
+  const int hb1 = th_half1 ? th_half1 : 50;
+  const size_t per_max = (size_t)(2 * kCorrHalfLam + 1) * (2 * std::max(hb1, kCorrHalfLam) + 1);
+  const size_t nmax = (size_t)G * per_max;
+  PRNU_CHECK_ARG(nmax < (size_t)INT_MAX, "too many correction nodes");
+  const int wave = std::max(1, std::min(tn.wave, kLoopMaxWave));
+
+  if (*c->h_err)
+    report_device_abort(c, s, "a bounded device-side wait of an earlier call timed out; its results are invalid");
+  PRNU_CUDA_TRY(cudaStreamWaitEvent(s, c->last_done, 0));
+  for (auto& f : fps) PRNU_CUDA_TRY(cudaStreamWaitEvent(s, f->ready, 0));
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t o_ct = al(sizeof(float) * G), o_act = o_ct + al(sizeof(float) * G), o_have = o_act + al(sizeof(int) * G),
+               o_runs = o_have + al(sizeof(int) * G), o_who = o_runs + al(sizeof(int) * G),
+               o_best = o_who + al(sizeof(int) * G), corr_bytes = o_best + al(sizeof(prnu_result) * G);
+  ensure_buf(c, c->ws_items, sizeof(WorkItem) * nmax);
+  ensure_buf(c, c->ws_results, sizeof(CandResult) * nmax);
+  ensure_buf(c, c->ws_groups, sizeof(int) * (G + 1));
+  ensure_buf(c, c->ws_fpdesc, sizeof(FpDesc) * std::max(P, 1));
+  ensure_buf(c, c->ws_spec, (size_t)wave * H * Wh * sizeof(float2));
+  ensure_buf(c, c->ws_stats, (size_t)wave * H * sizeof(RowStat));
+  ensure_buf(c, c->ws_out, sizeof(prnu_result) * G);
+  ensure_buf(c, c->ws_corr, corr_bytes);
+  const ResidLayout lay = padded_layout(H, W);
+  const bool pairs = dtype != kF32;
+  ensure_buf(c, c->ws_pad, (size_t)F * lay.fpitch * (dtype == kF32 || pairs ? 4 : 2));
+  char* cb = reinterpret_cast<char*>(c->ws_corr.p);
+  float* d_cl = reinterpret_cast<float*>(cb);
+  float* d_ct = reinterpret_cast<float*>(cb + o_ct);
+  int* d_act = reinterpret_cast<int*>(cb + o_act);
+  int* d_have = reinterpret_cast<int*>(cb + o_have);
+  int* d_runs = reinterpret_cast<int*>(cb + o_runs);
+  int* d_who = reinterpret_cast<int*>(cb + o_who);
+  prnu_result* d_best = reinterpret_cast<prnu_result*>(cb + o_best);
+  std::vector<FpDesc> fd;
+  for (auto& f : fps) fd.push_back(fp_desc(*f));
+  const std::vector<int> ones(G, 1);
+  Stager stg(c);
+  stg.add(c->ws_fpdesc.p, fd.data(), fd.size());
+  stg.add(d_cl, cl.data(), cl.size());
+  stg.add(d_ct, ct.data(), ct.size());
+  stg.add(d_act, ones.data(), ones.size());
+  stg.flush(s);
+  PRNU_CUDA_TRY(cudaMemsetAsync(d_have, 0, 2 * al(sizeof(int) * G), s));   // have, runs
+  launch_pad_frames(d_resid, dtype, F, H, W, c->ws_pad.p, s, c->launches, pairs ? 1 : 0);
+
+  auto& bl = c->batch_loops[std::make_tuple(H, W, pairs ? (dtype == kF16 ? (int)kF16P : (int)kBF16P) : dtype)];
+  if (!bl) bl.reset(new BatchLoop(c));
+  WaveLoopConfig g;
+  g.fs = fs;
+  g.variant = tn.variant;
+  g.ppb = tn.ppb;
+  g.col_log2 = tn.col_log2;
+  g.H = H;
+  g.W = W;
+  g.rdtype = pairs ? (dtype == kF16 ? kF16P : kBF16P) : dtype;
+  g.wave = wave;
+  g.fp_f32 = std::any_of(fd.begin(), fd.end(), [](const FpDesc& d) { return d.dtype == kF32; }) ? 1 : 0;
+  g.spec = reinterpret_cast<float2*>(c->ws_spec.p);
+  g.stats = reinterpret_cast<RowStat*>(c->ws_stats.p);
+  g.spec_slots = wave;
+  g.resid = c->ws_pad.p;
+  g.fps = reinterpret_cast<const FpDesc*>(c->ws_fpdesc.p);
+  g.scale = d_scale;
+  g.err = c->d_err;
+  g.stall = c->debug_stall;
+  for (int n = 1; n <= max_iter; ++n) {
+    // float32 steps 0.01 * 10^-(n-1) and 0.1 * 10^-(n-1) degrees, as the host loop takes them
+    const float sl = (float)(0.01 * std::pow(10.0, -(n - 1))), st = (float)(0.1 * std::pow(10.0, -(n - 1)));
+    const int hb = n == 1 ? hb1 : kCorrHalfLam;
+    k_corr_gen<<<1, 1024, 0, s>>>(G, P, d_act, d_cl, d_ct, sl, st, hb,
+                                  reinterpret_cast<WorkItem*>(c->ws_items.p),
+                                  reinterpret_cast<CandResult*>(c->ws_results.p),
+                                  reinterpret_cast<int*>(c->ws_groups.p), d_who,
+                                  reinterpret_cast<prnu_result*>(c->ws_out.p), bl->ring_entry());
+    PRNU_CUDA_TRY(cudaGetLastError());
+    bl->run_written(g, s);
+    const int nb = 2 * hb + 1;
+    k_corr_update<<<1, 256, 0, s>>>(bl->ring_entry(), d_who, reinterpret_cast<const prnu_result*>(c->ws_out.p),
+                                    kCorrHalfLam * nb + hb, d_best, d_have, d_act, d_cl, d_ct, d_runs);
+    PRNU_CUDA_TRY(cudaGetLastError());
+    c->launches.n += 2;
+  }
+  std::vector<int> runs(G);
+  PRNU_CUDA_TRY(cudaMemcpyAsync(out, d_best, sizeof(prnu_result) * G, cudaMemcpyDeviceToHost, s));
+  PRNU_CUDA_TRY(cudaMemcpyAsync(runs.data(), d_runs, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
+  PRNU_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRNU_CUDA_TRY(cudaEventRecord(c->last_done, s));
+  PRNU_CUDA_TRY(cudaStreamSynchronize(s));
+  if (*c->h_err) report_device_abort(c, s, "a bounded device-side wait timed out; the results are invalid");
+  if (iters)
+    for (int k = 0; k < G; ++k) iters[k] = runs[k];
+  return true;
+}
+
 }  // namespace prnu
 
 using namespace prnu;
@@ -586,6 +786,8 @@ static void run_correction(prnu_ctx* ctx, const void* d_resid, int dtype, const 
                            int W, const std::vector<std::shared_ptr<Fingerprint>>& fps, std::vector<float> cl,
                            std::vector<float> ct, int max_iter, int th_half1, prnu_result* out, int* iters,
                            cudaStream_t s) {
+  if (run_correction_device(ctx, d_resid, dtype, d_scale, F, H, W, fps, cl, ct, max_iter, th_half1, out, iters, s))
+    return;
   constexpr int kHalf = 5;
   const int P = (int)fps.size();
   const int hb1 = th_half1 ? th_half1 : 50;
@@ -844,7 +1046,7 @@ int prnu_destroy(prnu_ctx* ctx) {
     for (DeviceBuf* b : {&ctx->ws_spec, &ctx->ws_stats, &ctx->ws_items, &ctx->ws_results, &ctx->ws_groups,
                          &ctx->ws_out, &ctx->ws_fpdesc, &ctx->ws_misc, &ctx->ws_resid, &ctx->ws_persist, &ctx->ws_pad, &ctx->ws_fpest,
                          &ctx->ws_lit, &ctx->ws_litx, &ctx->ws_litpart, &ctx->ws_renders, &ctx->ws_resize,
-                         &ctx->ws_wav})
+                         &ctx->ws_wav, &ctx->ws_corr})
       ctx_free(ctx, b->p, b->bytes);
     ctx_free(ctx, ctx->d_tw, ctx->tw_bytes);
     ctx_free(ctx, ctx->d_err, sizeof(int));

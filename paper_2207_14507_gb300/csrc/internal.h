@@ -234,7 +234,7 @@ struct prnu_ctx {
   cudaEvent_t last_done = nullptr;
   // call workspace
   prnu::DeviceBuf ws_spec, ws_stats, ws_items, ws_results, ws_groups, ws_out, ws_fpdesc, ws_misc, ws_resid,
-      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders, ws_resize, ws_wav;
+      ws_persist, ws_pad, ws_fpest, ws_lit, ws_litx, ws_litpart, ws_renders, ws_resize, ws_wav, ws_corr;
   size_t tw_bytes = 0;
   int* h_err = nullptr;           // pinned: error flag of the last persistent launch or TMA wait
   int* d_err = nullptr;           // device flag the wave kernels raise when a bounded wait gives up

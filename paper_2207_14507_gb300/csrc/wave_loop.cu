@@ -362,6 +362,12 @@ BatchLoop::~BatchLoop() {
 }
 
 void BatchLoop::run(WaveLoopConfig c, const DevRun& r, cudaStream_t s) {
+  k_set_run<<<1, 1, 0, s>>>(ring_entry(), r);
+  PRNU_CUDA_TRY(cudaGetLastError());
+  run_written(c, s);
+}
+
+void BatchLoop::run_written(WaveLoopConfig c, cudaStream_t s) {
   int* flags = reinterpret_cast<int*>(mem_ + 256);
   c.ring = reinterpret_cast<const DevRun*>(mem_);
   c.tail = flags;
@@ -370,8 +376,6 @@ void BatchLoop::run(WaveLoopConfig c, const DevRun& r, cudaStream_t s) {
   c.ring_size = 1;
   c.budget = 0;
   wl_.ensure(c);
-  k_set_run<<<1, 1, 0, s>>>(reinterpret_cast<DevRun*>(mem_), r);
-  PRNU_CUDA_TRY(cudaGetLastError());
   wl_.rewind(s);
   wl_.launch(s);
 }

@@ -108,6 +108,9 @@ class BatchLoop {
   BatchLoop& operator=(const BatchLoop&) = delete;
   // every wave of run r on s, in one graph launch (c: all but the ring fields)
   void run(WaveLoopConfig c, const DevRun& r, cudaStream_t s);
+  // the same for the run a kernel earlier on s wrote into ring_entry()
+  void run_written(WaveLoopConfig c, cudaStream_t s);
+  DevRun* ring_entry() const { return reinterpret_cast<DevRun*>(mem_); }
 
  private:
   prnu_ctx* ctx_;
