@@ -60,9 +60,15 @@ extern "C" int prnu_autotune(prnu_ctx* ctx, int H, int W, int dtype, double budg
     Tuning base = tuning_for(ctx, H, W);
     const FixedShape* fs = find_fixed(H, W);
     const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
+    // waves: a few small ones, then the size's default (up to 1024 candidates,
+    // 16 GB of spectra).  The timed search below has 512 candidates, so larger
+    // waves cannot be told apart there; the default is taken for them
     std::vector<int> waves;
-    for (int w : {16, 64, 128, 256, 512})
-      if ((size_t)w * per_item < ctx->budget / 4) waves.push_back(w);
+    const int def_wave = default_wave(H, W);
+    for (int w : {16, 64, 128, 256, def_wave})
+      if (w <= def_wave && (size_t)w * per_item < ctx->budget / 4 &&
+          std::find(waves.begin(), waves.end(), w) == waves.end())
+        waves.push_back(w);
     if (waves.empty()) waves.push_back(1);
     // candidate configurations: generic kernels and every compile-time column
     // variant and row-pair count, each over the wave sizes, and the persistent launch

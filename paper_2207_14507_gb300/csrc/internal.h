@@ -257,6 +257,8 @@ namespace prnu {
 void* ctx_alloc(prnu_ctx* c, size_t bytes);
 void ctx_free(prnu_ctx* c, void* p, size_t bytes);
 void ensure_buf(prnu_ctx* c, DeviceBuf& b, size_t bytes);
+// candidates per wave by default for frames of H x W: up to 1024, and up to 16 GB of spectra
+int default_wave(int H, int W);
 Tuning tuning_for(prnu_ctx* c, int H, int W);
 
 // The search engine: enqueue the fused path for a prepared item list.

@@ -12,7 +12,7 @@ namespace {
 // The wave shapes a loop body holds, one branch each of its SWITCH node:
 // shared forward units or not, and the grids' sizes (items, and forward
 // units), so that a wave runs in the smallest branch that fits it.
-constexpr int kMaxCases = 32;
+constexpr int kMaxCases = 40;
 struct CaseTable {
   int n;
   int grouped[kMaxCases];

@@ -16,7 +16,7 @@
 
 namespace prnu {
 
-constexpr int kLoopMaxWave = 512;   // wave table capacity
+constexpr int kLoopMaxWave = 1024;  // wave table capacity
 
 // One run of candidates: a query of the server, or one call's work list.
 struct DevRun {
