@@ -324,7 +324,8 @@ struct Server::Impl {
     q->call.H = q->H;
     q->call.W = q->W;
     q->bytes = query_bytes(*q);
-    if (q->bytes + workspace_bytes(q->H, q->W, std::max(1, std::min(q->tn.wave, kMaxWave)), unit_major) > ctx->budget)
+    const int wmax = dev_mode ? kLoopMaxWave : kMaxWave;   // the device loop's waves may be larger
+    if (q->bytes + workspace_bytes(q->H, q->W, std::max(1, std::min(q->tn.wave, wmax)), unit_major) > ctx->budget)
       throw Error{PRNU_ENOMEM, "the query alone exceeds the HBM budget"};
     std::lock_guard<std::mutex> lk(mu);
     if (queued.size() >= kMaxQueued) throw Error{PRNU_EAGAIN, "query queue full"};
@@ -565,7 +566,7 @@ struct Server::Impl {
     L->key = key;
     L->tn = q.tn;
     L->fs = fs;
-    L->wave = std::max(1, std::min(q.tn.wave, kMaxWave));
+    L->wave = std::max(1, std::min(q.tn.wave, kLoopMaxWave));   // the device tables hold up to 1024
     L->wl.reset(new WaveLoop(ctx));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->ring, sizeof(DevRun) * kRing, cudaHostAllocMapped));
     PRNU_CUDA_TRY(cudaHostAlloc((void**)&L->flags, sizeof(int) * (1 + 2 * kRing), cudaHostAllocMapped));
