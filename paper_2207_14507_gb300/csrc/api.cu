@@ -172,7 +172,9 @@ Tuning tuning_for(prnu_ctx* c, int H, int W) {
   // sizes without compile-time-planned kernels run the generic ones (-1), so
   // that what prnu_get_tuning reports is accepted by prnu_set_tuning
   t.variant = find_fixed(H, W) ? 0 : -1;
-  t.wave = default_wave(H, W);
+  // within a quarter of the context's HBM budget (spectra and row statistics)
+  const size_t per_item = (size_t)H * (W / 2) * sizeof(float2) + (size_t)H * sizeof(RowStat);
+  t.wave = (int)std::max<size_t>(1, std::min<size_t>((size_t)default_wave(H, W), c->budget / 4 / per_item));
   // one stream: two-stream waves gain under 1% at 1080p and make the
   // per-launch event times overlap (prnu_set_tuning selects them)
   t.streams = 1;

@@ -149,7 +149,9 @@ def test_poll_and_submit_errors(prnu):
             ctx.query_submit(bad, hs, q["g"])
         assert e.value.code == prnu.PRNU_EINVAL
     with prnu.Context(0, hbm_budget_bytes=64 << 20) as small:
-        big = torch.zeros((8, 1080, 1920), dtype=torch.uint8, device=DEV)
+        # 16 full-HD frames: their residuals alone (66 MB) exceed the budget,
+        # whatever wave the budget leaves room for
+        big = torch.zeros((16, 1080, 1920), dtype=torch.uint8, device=DEV)
         K = torch.zeros((1080, 1920), device=DEV)
         h = small.prnu_fingerprint_term(K)
         with pytest.raises(prnu.PrnuError) as e:
