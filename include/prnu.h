@@ -424,7 +424,8 @@ int prnu_server_stats_get(prnu_ctx* ctx, prnu_server_stats* out);
 typedef struct {
     int col_width;        /* 4, 8 or 16 */
     int pairs_per_block;  /* 1, 2 or 4 */
-    int wave;             /* candidates in flight, >= 1 */
+    int wave;             /* candidates in flight, >= 1 (default: up to 1024, with at most
+                             16 GB of spectra and a quarter of the context's HBM budget) */
     int variant;          /* compile-time-planned column kernel variant for this size
                              (0.. n-1), or -1 for the generic runtime-plan kernels */
     int persistent;       /* 0: waves, one launch sequence each (default).
