@@ -992,6 +992,12 @@ def run_precision(args):
     ctx.close()
 
 
+def oracle_sample_queries(n_cap, n_st, k):
+    """Indices of the served queries the oracle checks: the first k of the
+    steady run (queries n_cap .. n_cap + n_st - 1), else of the capacity run."""
+    return (list(range(n_cap, n_cap + n_st)) if n_st else list(range(n_cap)))[:k]
+
+
 def serving_leg(prnu, dev, n_cap, n_st, n_ov, oracle_queries, loop="device", autotune_ms=0.0):
     """Config 5: Poisson query stream (720p/1080p/4K, 8-64 frames, 1-16
     fingerprints, one matching with probability 0.5, +-k windows, FP16
@@ -1088,7 +1094,7 @@ def serving_leg(prnu, dev, n_cap, n_st, n_ov, oracle_queries, loop="device", aut
     # that node inside the window; one process pool per resolution
     t0 = time.perf_counter()
     g = synth.GRID_FULL
-    sample = (list(range(n_cap, n_cap + n_st)) if n_st else list(range(n_cap)))[:oracle_queries]
+    sample = oracle_sample_queries(n_cap, n_st, oracle_queries)
     picks = []
     for i in sample:
         q = queries[i]

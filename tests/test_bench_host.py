@@ -91,3 +91,10 @@ def test_shared_byte_model_reduces_to_the_path_model():
     H, W, s_in, s_k = 1080, 1920, 2, 4
     shared = (s_in + 12) * H * W / 1 + (12 + s_k / 2) * H * W
     assert shared == bench.path_bytes(H, W, s_in, s_k) + 8 * H * W
+
+
+def test_oracle_samples_the_steady_run_else_the_capacity_run():
+    assert bench.oracle_sample_queries(16, 100, 20) == list(range(16, 36))
+    assert bench.oracle_sample_queries(8, 0, 4) == [0, 1, 2, 3]
+    assert bench.oracle_sample_queries(3, 0, 4) == [0, 1, 2]
+    assert bench.oracle_sample_queries(16, 5, 20) == list(range(16, 21))
